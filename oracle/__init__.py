@@ -1,0 +1,194 @@
+"""FP64 CPU oracle of the dimensionally split MHD grid update (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never does, and this
+package imports nothing from it.
+
+The arithmetic lives in ``mhd_oracle.c`` (plain loops, FP64, periodic
+indexing); this module compiles it with gcc, loads it with ctypes and adds the
+FP64 diagnostics (exactly rounded sums with ``math.fsum``) and the coarse-grid
+restriction, both written from their plain definitions.
+
+State arrays are numpy float64 of shape (8, nz, ny, nx): fields rho, m_x, m_y,
+m_z, e, b_x, b_y, b_z; b_d[k, j, i] lives on the low face of cell (i, j, k)
+along d.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mhd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+# -ffp-contract=off: no fused multiply-add, so x86 and Arm hosts give the
+# same FP64 results; no -march flags for the same reason.
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+
+
+def build(force: bool = False) -> str:
+    """Compile mhd_oracle.c into _build/liboracle.so (if stale) and return its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            i3 = ctypes.c_int * 3
+            lib.orc_fluid_sweep.argtypes = [i3, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_int, ctypes.c_double]
+            lib.orc_mag_sweep.argtypes = [i3, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+            lib.orc_cfl_rate.argtypes = [i3, ctypes.c_double, ctypes.c_void_p]
+            lib.orc_cfl_rate.restype = ctypes.c_double
+            lib.orc_step.argtypes = [i3, ctypes.c_double, ctypes.c_void_p, ctypes.c_double]
+            lib.orc_run.argtypes = [i3, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_double, dp]
+            lib.orc_run.restype = ctypes.c_double
+            lib.orc_threads.restype = ctypes.c_int
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _dims(state: np.ndarray):
+    if state.dtype != np.float64 or state.ndim != 4 or state.shape[0] != 8:
+        raise ValueError("state must be float64 of shape (8, nz, ny, nx)")
+    if not state.flags.c_contiguous:
+        raise ValueError("state must be C-contiguous")
+    nz, ny, nx = state.shape[1:]
+    return (ctypes.c_int * 3)(nx, ny, nz)
+
+
+def _ptrs(state: np.ndarray):
+    base = state.ctypes.data
+    stride = state.strides[0]
+    arr = (ctypes.c_void_p * 8)(*[base + q * stride for q in range(8)])
+    return arr
+
+
+def threads() -> int:
+    """Number of OpenMP threads the oracle uses."""
+    return _load().orc_threads()
+
+
+def set_threads(t: int) -> None:
+    _load().orc_set_threads(int(t))
+
+
+def fluid_sweep(state: np.ndarray, d: int, tau: float, gamma: float) -> None:
+    """In place: relaxing-TVD fluid sweep along axis d (0=x, 1=y, 2=z), step tau."""
+    _load().orc_fluid_sweep(_dims(state), gamma, _ptrs(state), int(d), float(tau))
+
+
+def mag_sweep(state: np.ndarray, d: int, tau: float) -> None:
+    """In place: magnetic advection-constraint sweep along axis d, step tau."""
+    _load().orc_mag_sweep(_dims(state), _ptrs(state), int(d), float(tau))
+
+
+def cfl_rate(state: np.ndarray, gamma: float) -> float:
+    """max over cells and axes of (|v_d| + c_f*) / h_d."""
+    return _load().orc_cfl_rate(_dims(state), gamma, _ptrs(state))
+
+
+def cfl_dt(state: np.ndarray, gamma: float, cfl: float) -> float:
+    """Full-step CFL timestep 2 * cfl / rate (each of the 6 sweeps uses dt/2)."""
+    return 2.0 * cfl / cfl_rate(state, gamma)
+
+
+def step(state: np.ndarray, dt: float, gamma: float) -> None:
+    """In place: one full step (x, y, z then z, y, x; each sweep tau = dt/2)."""
+    _load().orc_step(_dims(state), gamma, _ptrs(state), float(dt))
+
+
+def run(state: np.ndarray, nsteps: int, cfl: float, gamma: float):
+    """In place: nsteps full steps with per-step CFL dt. Returns (t, dts)."""
+    dts = np.zeros(max(nsteps, 1), dtype=np.float64)
+    t = _load().orc_run(_dims(state), gamma, _ptrs(state), int(nsteps), float(cfl),
+                        dts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return t, dts[:nsteps]
+
+
+# --------------------------------------------------------------------------
+# FP64 diagnostics, from their plain definitions.
+
+def diagnostics(state: np.ndarray, gamma: float) -> np.ndarray:
+    """Ten numbers: exactly rounded sums of rho, m_x, m_y, m_z, e, b_x, b_y, b_z
+    over all cells/faces; max over cells of |div b| * h_min; and the minimum
+    gas pressure.
+
+    div b of a cell is its discrete flux balance sum_d (b_d(high face) -
+    b_d(low face)) / h_d (constrained transport keeps it at roundoff); it is
+    multiplied by the smallest spacing h_min = 1/max(n) so it has the units of b.
+    """
+    _dims(state)
+    nz, ny, nx = state.shape[1:]
+    out = np.zeros(10, dtype=np.float64)
+    for q in range(8):
+        out[q] = math.fsum(state[q].ravel().tolist())
+    n = (nx, ny, nz)
+    div = np.zeros(state.shape[1:], dtype=np.float64)
+    for d in range(3):
+        b = state[5 + d]
+        axis = 2 - d  # numpy axis of spatial axis d
+        div += (np.roll(b, -1, axis=axis) - b) * n[d]
+    out[8] = float(np.max(np.abs(div))) / max(n)
+    out[9] = float(np.min(pressure(state, gamma)))
+    return out
+
+
+def pressure(state: np.ndarray, gamma: float) -> np.ndarray:
+    """Gas pressure per cell, p = (gamma-1)(e - |m|^2/(2 rho) - |b_c|^2/2) (Eq. 3),
+    b_c the mean of each cell's two faces."""
+    rho = state[0]
+    kin = 0.5 * (state[1] ** 2 + state[2] ** 2 + state[3] ** 2) / rho
+    b2 = np.zeros_like(rho)
+    for d in range(3):
+        b = state[5 + d]
+        bc = 0.5 * (b + np.roll(b, -1, axis=2 - d))
+        b2 += bc * bc
+    return (gamma - 1.0) * (state[4] - kin - 0.5 * b2)
+
+
+def restrict(state: np.ndarray, r: int) -> np.ndarray:
+    """Coarse-grid restriction by an integer factor r along every axis.
+
+    Conserved cell quantities: mean over the r^3 fine cells of a coarse cell.
+    Face field b_d: mean over the r^2 fine faces that tile the coarse face
+    (the fine faces at fine index r*I along d).  The coarse face flux equals
+    the sum of the fine fluxes, so a divergence-free fine field restricts to a
+    divergence-free coarse field.
+    """
+    _dims(state)
+    nz, ny, nx = state.shape[1:]
+    if nx % r or ny % r or nz % r:
+        raise ValueError("dims must be divisible by r")
+    Z, Y, X = nz // r, ny // r, nx // r
+    out = np.empty((8, Z, Y, X), dtype=np.float64)
+    for q in range(5):
+        out[q] = state[q].reshape(Z, r, Y, r, X, r).mean(axis=(1, 3, 5))
+    bx = state[5][:, :, ::r]                      # faces on coarse x-faces
+    out[5] = bx.reshape(Z, r, Y, r, X).mean(axis=(1, 3))
+    by = state[6][:, ::r, :]
+    out[6] = by.reshape(Z, r, Y, X, r).mean(axis=(1, 4))
+    bz = state[7][::r, :, :]
+    out[7] = bz.reshape(Z, Y, r, X, r).mean(axis=(2, 4))
+    return out

@@ -1,0 +1,383 @@
+/*
+ * FP64 CPU oracle for the dimensionally split ideal-MHD grid update of
+ * "Magnetohydrodynamics on Heterogeneous architectures: a performance
+ * comparison" (Pang, Pen & Perrone), Section II.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * restatement of the method that the CUDA path is checked against.  Only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header or constant with the CUDA library.
+ *
+ * What it computes (restated from the equations, not from any code):
+ *   - state: cell-centred conserved U = (rho, m_x, m_y, m_z, e) and a
+ *     face-centred magnetic field b_x, b_y, b_z (constrained transport,
+ *     Section II.B); b is in units where the 4*pi is absorbed (Section II.A),
+ *     e = rho v^2/2 + p/(gamma-1) + b^2/2 and P* = p + b^2/2 (Eq. 1-3).
+ *   - a fluid sweep along axis d: the 1-D conservation law du/dt + dF/dx = 0
+ *     (Eq. 6) with the flux of Eq. 2-3 projected on d, discretised by a
+ *     relaxing TVD scheme: per-cell freezing speed c, right/left movers
+ *     F^R = (cU+F)/2, F^L = (cU-F)/2, a first-order upwind half step and a
+ *     full step with van Leer limited second-order fluxes (2-stage
+ *     Runge-Kutta), Section II.B.  b is held fixed during the sweep.
+ *   - a magnetic sweep along d: for each transverse axis t, the component b_t
+ *     is advected along d by the same upwind + van Leer, 2-stage scheme, and
+ *     the edge flux it produces is applied to b_d so that div b is unchanged
+ *     (advection-constraint step of Section II.B, Eq. 4-5).
+ *   - the timestep: CFL rate, then sweeps x, y, z followed by z, y, x.
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - freezing speed per cell c = |v_d| + sqrt((gamma p + |b_c|^2)/rho),
+ *     recomputed from each Runge-Kutta stage's state;
+ *   - cell-centred b_c is the mean of the two faces of the cell;
+ *   - b_d[i] sits on the low face of cell i along d;
+ *   - advection velocity of b_t: v_d averaged to the b_t face (cells j, j-1
+ *     along t), then to the edge (cells i, i+1 along d);
+ *   - second-order magnetic flux: ubar * (q_up + s * phi(dq-, dq+) / 2), with
+ *     s = +1 for ubar >= 0 (upwind cell i) and -1 otherwise (upwind cell i+1);
+ *   - schedule: forward half [fluid_d, magnetic_d] for d = x, y, z, reverse
+ *     half [magnetic_d, fluid_d] for d = z, y, x, every sweep with tau = dt/2;
+ *   - CFL: dt = 2 * cfl / max_cells max_d (|v_d| + c_f*) / h_d;
+ *   - domain is the periodic unit cube, h_d = 1 / n_d.
+ *
+ * Layout: 8 arrays (rho, m_x, m_y, m_z, e, b_x, b_y, b_z), each nx*ny*nz
+ * doubles, flat index i + nx*(j + ny*k).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
+
+/* periodic wrap of an index */
+static int wrap(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* flat index of cell c[0..2], wrapped periodically */
+static long at(const int n[3], const int c[3]) {
+    return (long)wrap(c[0], n[0]) +
+           (long)n[0] * ((long)wrap(c[1], n[1]) + (long)n[1] * (long)wrap(c[2], n[2]));
+}
+
+/* van Leer limiter of Section II.B: harmonic mean of two slopes of equal sign */
+static double vanleer(double a, double b) {
+    return (a * b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+/*
+ * Flux of Eq. 2-3 projected on the sweep axis, in the sweep's local frame
+ * (component 0 = along d, 1 and 2 = the two transverse axes), and the
+ * freezing speed c of the relaxation scheme.
+ *   u = (rho, m_d, m_t1, m_t2, e), b = cell-centred (b_d, b_t1, b_t2).
+ */
+static void flux_and_speed(const double u[5], const double b[3], double gamma,
+                           double F[5], double *c) {
+    double rho = u[0];
+    double vd = u[1] / rho, v1 = u[2] / rho, v2 = u[3] / rho;
+    double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    double kinetic = 0.5 * (u[1] * vd + u[2] * v1 + u[3] * v2);
+    double p = (gamma - 1.0) * (u[4] - kinetic - 0.5 * b2);
+    double pstar = p + 0.5 * b2;
+    double bv = b[0] * vd + b[1] * v1 + b[2] * v2;
+    F[0] = u[1];
+    F[1] = u[1] * vd + pstar - b[0] * b[0];
+    F[2] = u[2] * vd - b[0] * b[1];
+    F[3] = u[3] * vd - b[0] * b[2];
+    F[4] = (u[4] + pstar) * vd - b[0] * bv;
+    *c = fabs(vd) + sqrt((gamma * p + b2) / rho);
+}
+
+/*
+ * One relaxing-TVD fluid update of a periodic pencil of n cells with step tau
+ * and spacing h (Section II.B).  U[q][i] is updated in place; B[q][i] is the
+ * frozen cell-centred field.  w is workspace of at least 25*n doubles.
+ */
+static void fluid_pencil(int n, double h, double tau, double gamma,
+                         double *U[5], double *B[3], double *w) {
+    double *FR = w;            /* 5*n : right movers of the current stage */
+    double *FL = w + 5 * n;    /* 5*n : left movers */
+    double *Uh = w + 10 * n;   /* 5*n : half-step state */
+    double *fl = w + 15 * n;   /* 5*n : interface flux, fl[q*n+i] at i+1/2 */
+    double *cs = w + 20 * n;   /* n   : freezing speed */
+    double u[5], b[3], F[5];
+    int i, q;
+
+    /* stage 1: first-order upwind fluxes from U, half step tau/2 */
+    for (i = 0; i < n; i++) {
+        for (q = 0; q < 5; q++) u[q] = U[q][i];
+        for (q = 0; q < 3; q++) b[q] = B[q][i];
+        flux_and_speed(u, b, gamma, F, &cs[i]);
+        for (q = 0; q < 5; q++) {
+            FR[q * n + i] = 0.5 * (cs[i] * u[q] + F[q]);
+            FL[q * n + i] = 0.5 * (cs[i] * u[q] - F[q]);
+        }
+    }
+    for (q = 0; q < 5; q++)
+        for (i = 0; i < n; i++)
+            fl[q * n + i] = FR[q * n + i] - FL[q * n + wrap(i + 1, n)];
+    for (q = 0; q < 5; q++)
+        for (i = 0; i < n; i++)
+            Uh[q * n + i] = U[q][i] - (tau / (2.0 * h)) *
+                                          (fl[q * n + i] - fl[q * n + wrap(i - 1, n)]);
+
+    /* stage 2: van Leer limited second-order fluxes from the half-step state */
+    for (i = 0; i < n; i++) {
+        for (q = 0; q < 5; q++) u[q] = Uh[q * n + i];
+        for (q = 0; q < 3; q++) b[q] = B[q][i];
+        flux_and_speed(u, b, gamma, F, &cs[i]);
+        for (q = 0; q < 5; q++) {
+            FR[q * n + i] = 0.5 * (cs[i] * u[q] + F[q]);
+            FL[q * n + i] = 0.5 * (cs[i] * u[q] - F[q]);
+        }
+    }
+    for (q = 0; q < 5; q++) {
+        const double *R = FR + q * n, *L = FL + q * n;
+        for (i = 0; i < n; i++) {
+            int im = wrap(i - 1, n), ip = wrap(i + 1, n), ipp = wrap(i + 2, n);
+            double right = R[i] + 0.5 * vanleer(R[i] - R[im], R[ip] - R[i]);
+            double left = L[ip] - 0.5 * vanleer(L[ip] - L[i], L[ipp] - L[ip]);
+            fl[q * n + i] = right - left;
+        }
+    }
+    for (q = 0; q < 5; q++)
+        for (i = 0; i < n; i++)
+            U[q][i] = U[q][i] - (tau / h) * (fl[q * n + i] - fl[q * n + wrap(i - 1, n)]);
+}
+
+/*
+ * Edge flux of the advected transverse field along a periodic pencil
+ * (Section II.B, magnetic part).  q[i] is b_t on the pencil, ub[i] the
+ * advection velocity at edge i+1/2.  Output f[i] at edge i+1/2.
+ * w is workspace of at least 2*n doubles.
+ */
+static void advect_flux(int n, double h, double tau, const double *q,
+                        const double *ub, double *f, double *w) {
+    double *g = w, *qh = w + n;
+    int i;
+    /* stage 1: upwind flux, half step */
+    for (i = 0; i < n; i++)
+        g[i] = ub[i] * (ub[i] >= 0.0 ? q[i] : q[wrap(i + 1, n)]);
+    for (i = 0; i < n; i++)
+        qh[i] = q[i] - (tau / (2.0 * h)) * (g[i] - g[wrap(i - 1, n)]);
+    /* stage 2: upwind value plus half the limited slope of the upwind cell */
+    for (i = 0; i < n; i++) {
+        int im = wrap(i - 1, n), ip = wrap(i + 1, n), ipp = wrap(i + 2, n);
+        if (ub[i] >= 0.0)
+            f[i] = ub[i] * (qh[i] + 0.5 * vanleer(qh[i] - qh[im], qh[ip] - qh[i]));
+        else
+            f[i] = ub[i] * (qh[ip] - 0.5 * vanleer(qh[ip] - qh[i], qh[ipp] - qh[ip]));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+
+/* transverse axes of a sweep along d: cyclic (d+1, d+2) */
+static int t1_of(int d) { return (d + 1) % 3; }
+static int t2_of(int d) { return (d + 2) % 3; }
+
+/*
+ * Fluid sweep along axis d with step tau: every pencil along d independently
+ * (the magnetic field is frozen; it only enters through b_c).
+ */
+void orc_fluid_sweep(const int n[3], double gamma, double *f[8], int d, double tau) {
+    int t1 = t1_of(d), t2 = t2_of(d);
+    int nd = n[d];
+    double h = 1.0 / nd;
+    int np = n[t1] * n[t2];
+    int p;
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < np; p++) {
+        double *buf = (double *)malloc(sizeof(double) * (size_t)nd * (5 + 3 + 25));
+        double *U[5], *B[3];
+        int q, s, c[3], cn[3];
+        long id;
+        for (q = 0; q < 5; q++) U[q] = buf + q * nd;
+        for (q = 0; q < 3; q++) B[q] = buf + (5 + q) * nd;
+        c[t1] = p % n[t1];
+        c[t2] = p / n[t1];
+        for (s = 0; s < nd; s++) {
+            c[d] = s;
+            id = at(n, c);
+            U[0][s] = f[RHO][id];
+            U[1][s] = f[MX + d][id];
+            U[2][s] = f[MX + t1][id];
+            U[3][s] = f[MX + t2][id];
+            U[4][s] = f[EN][id];
+            /* cell-centred field: mean of the low and high faces (axis a) */
+            {
+                int ax[3] = {d, t1, t2}, a;
+                for (a = 0; a < 3; a++) {
+                    memcpy(cn, c, sizeof cn);
+                    cn[ax[a]] += 1;
+                    B[a][s] = 0.5 * (f[BX + ax[a]][id] + f[BX + ax[a]][at(n, cn)]);
+                }
+            }
+        }
+        fluid_pencil(nd, h, tau, gamma, U, B, buf + 8 * nd);
+        for (s = 0; s < nd; s++) {
+            c[d] = s;
+            id = at(n, c);
+            f[RHO][id] = U[0][s];
+            f[MX + d][id] = U[1][s];
+            f[MX + t1][id] = U[2][s];
+            f[MX + t2][id] = U[3][s];
+            f[EN][id] = U[4][s];
+        }
+        free(buf);
+    }
+}
+
+/*
+ * Magnetic advection-constraint sweep along axis d with step tau.
+ * For each transverse axis t: the edge flux e_t of b_t along d is computed on
+ * every pencil from the unmodified state; then
+ *   b_t(cell)            -= tau/h_d * (e_t(i+1/2) - e_t(i-1/2))   (advection)
+ *   b_d(face i+1/2, j)   += tau/h_t * (e_t(pencil j+1) - e_t(pencil j))
+ *                                                               (constraint)
+ * where e_t on pencil j lives on the edge (d: i+1/2, t: j-1/2).  The total
+ * energy e is not touched (it is the conserved variable of Eq. 3).
+ */
+void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
+    int nd = n[d];
+    double hd = 1.0 / nd;
+    long N = (long)n[0] * n[1] * n[2];
+    int ts[2] = {t1_of(d), t2_of(d)};
+    double *E[2];
+    int k;
+
+    for (k = 0; k < 2; k++) {
+        int t = ts[k], o = 3 - d - t; /* o: the third axis */
+        int np = n[t] * n[o];
+        int p;
+        E[k] = (double *)malloc(sizeof(double) * (size_t)N);
+#pragma omp parallel for schedule(static)
+        for (p = 0; p < np; p++) {
+            double *buf = (double *)malloc(sizeof(double) * (size_t)nd * 6);
+            double *q = buf, *u = buf + nd, *ub = buf + 2 * nd, *fe = buf + 3 * nd;
+            int s, c[3], cm[3];
+            c[t] = p % n[t];
+            c[o] = p / n[t];
+            for (s = 0; s < nd; s++) {
+                long id, idm;
+                c[d] = s;
+                memcpy(cm, c, sizeof cm);
+                cm[t] -= 1;
+                id = at(n, c);
+                idm = at(n, cm);
+                q[s] = f[BX + t][id];
+                /* v_d averaged to the b_t face between cells j-1 and j */
+                u[s] = 0.5 * (f[MX + d][id] / f[RHO][id] + f[MX + d][idm] / f[RHO][idm]);
+            }
+            for (s = 0; s < nd; s++) ub[s] = 0.5 * (u[s] + u[wrap(s + 1, nd)]);
+            advect_flux(nd, hd, tau, q, ub, fe, buf + 4 * nd);
+            for (s = 0; s < nd; s++) {
+                c[d] = s;
+                E[k][at(n, c)] = fe[s];
+            }
+            free(buf);
+        }
+    }
+    /* apply: advection of each b_t, then the constraint on b_d */
+    for (k = 0; k < 2; k++) {
+        int t = ts[k];
+        double ht = 1.0 / n[t];
+        long id;
+#pragma omp parallel for schedule(static)
+        for (id = 0; id < N; id++) {
+            int c[3], cm[3];
+            c[0] = (int)(id % n[0]);
+            c[1] = (int)((id / n[0]) % n[1]);
+            c[2] = (int)(id / ((long)n[0] * n[1]));
+            memcpy(cm, c, sizeof cm);
+            cm[d] -= 1;
+            f[BX + t][id] -= (tau / hd) * (E[k][id] - E[k][at(n, cm)]);
+        }
+#pragma omp parallel for schedule(static)
+        for (id = 0; id < N; id++) {
+            /* b_d on the low face of cell c along d = face (c_d - 1) + 1/2 */
+            int c[3], e0[3], e1[3];
+            c[0] = (int)(id % n[0]);
+            c[1] = (int)((id / n[0]) % n[1]);
+            c[2] = (int)(id / ((long)n[0] * n[1]));
+            memcpy(e0, c, sizeof e0);
+            e0[d] -= 1;              /* edge (d: c_d - 1/2, t: c_t - 1/2) */
+            memcpy(e1, e0, sizeof e1);
+            e1[t] += 1;              /* edge (d: c_d - 1/2, t: c_t + 1/2) */
+            f[BX + d][id] += (tau / ht) * (E[k][at(n, e1)] - E[k][at(n, e0)]);
+        }
+    }
+    free(E[0]);
+    free(E[1]);
+}
+
+/* Largest signal rate max_cells max_d (|v_d| + c_f*) / h_d, c_f* the fast-speed
+ * bound sqrt((gamma p + |b_c|^2)/rho); the CFL timestep is 2*cfl/rate. */
+double orc_cfl_rate(const int n[3], double gamma, double *const f[8]) {
+    long N = (long)n[0] * n[1] * n[2];
+    double rmax = 0.0;
+    long id;
+#pragma omp parallel for reduction(max : rmax) schedule(static)
+    for (id = 0; id < N; id++) {
+        int c[3], cn[3], a;
+        double b[3], v[3], rho = f[RHO][id], b2 = 0.0, kin = 0.0, p, cf, r = 0.0;
+        c[0] = (int)(id % n[0]);
+        c[1] = (int)((id / n[0]) % n[1]);
+        c[2] = (int)(id / ((long)n[0] * n[1]));
+        for (a = 0; a < 3; a++) {
+            memcpy(cn, c, sizeof cn);
+            cn[a] += 1;
+            b[a] = 0.5 * (f[BX + a][id] + f[BX + a][at(n, cn)]);
+            v[a] = f[MX + a][id] / rho;
+            b2 += b[a] * b[a];
+            kin += 0.5 * f[MX + a][id] * v[a];
+        }
+        p = (gamma - 1.0) * (f[EN][id] - kin - 0.5 * b2);
+        cf = sqrt((gamma * p + b2) / rho);
+        for (a = 0; a < 3; a++) {
+            double ra = (fabs(v[a]) + cf) * n[a];
+            if (ra > r) r = ra;
+        }
+        if (r > rmax) rmax = r;
+    }
+    return rmax;
+}
+
+/* One full timestep dt: x, y, z then z, y, x, each sweep with tau = dt/2. */
+void orc_step(const int n[3], double gamma, double *f[8], double dt) {
+    double tau = 0.5 * dt;
+    int d;
+    for (d = 0; d < 3; d++) {
+        orc_fluid_sweep(n, gamma, f, d, tau);
+        orc_mag_sweep(n, f, d, tau);
+    }
+    for (d = 2; d >= 0; d--) {
+        orc_mag_sweep(n, f, d, tau);
+        orc_fluid_sweep(n, gamma, f, d, tau);
+    }
+}
+
+/* nsteps full steps, each with its own CFL timestep; returns elapsed time.
+ * dts (optional, length nsteps) receives the timesteps taken. */
+double orc_run(const int n[3], double gamma, double *f[8], int nsteps, double cfl,
+               double *dts) {
+    double t = 0.0;
+    int s;
+    for (s = 0; s < nsteps; s++) {
+        double dt = 2.0 * cfl / orc_cfl_rate(n, gamma, f);
+        if (dts) dts[s] = dt;
+        orc_step(n, gamma, f, dt);
+        t += dt;
+    }
+    return t;
+}
+
+/* thread count the OpenMP runtime will use (1 without OpenMP) */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_threads(void) { return omp_get_max_threads(); }
+void orc_set_threads(int t) { omp_set_num_threads(t); }
+#else
+int orc_threads(void) { return 1; }
+void orc_set_threads(int t) { (void)t; }
+#endif
