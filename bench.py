@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Throughput of the dimensionally split MHD grid update on GB300.
+
+Metric: cell-updates/s per full step (one step = CFL timestep + fluid/magnetic
+sweeps x, y, z then z, y, x), on 512^3 periodic decaying MHD turbulence
+(rho = 1, p = 1, k^-2 spectrum for 2 <= k <= 8, rms Mach 1, beta 1, seed 0),
+FP32 state.  The state (4.3 GB) is far larger than L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  `value` is device time (CUDA events on the
+library's stream) with the state resident in HBM; `e2e` is the same metric
+through the C ABI with host buffers, the host->device copy of the state and
+the device->host copy of the result inside every timed step; `roofline` is
+the dominant kernel's algorithmic bytes over its measured launch time;
+`cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
+
+--impl reference times the FP64 CPU oracle instead (no installable reference
+implementation exists for this paper).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per full step"
+UNIT = "cell-updates/s"
+# Algorithmic bytes per cell of one launch (each field read once, written once):
+#   fluid sweep: reads rho, m (3), e, b (3) = 32 B, writes rho, m, e = 20 B
+#   magnetic sweep: reads rho, m_d, b (3) = 20 B, writes b (3) = 12 B
+ALGO_BYTES = {"fluid": 52, "mag": 32}
+STEP_BYTES = 384  # 6 sweeps x (read + write of 8 FP32 fields): the full-step model
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--size", type=int, default=512)
+    p.add_argument("--cfl", type=float, default=0.7)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample", type=int, default=128, help="edge of the oracle's sample box")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+
+def cpu_baseline(n: int, seed: int, cfl: float, budget_s: float = 15.0, min_steps: int = 1):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    s = ic.turbulence((n, n, n), seed=seed, dtype=torch.float64).numpy().copy()
+    g = 5.0 / 3.0
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        oracle.step(s, oracle.cfl_dt(s, g, cfl), g)
+        steps += 1
+        if steps >= 50:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n}^3 box of the same turbulence recipe (seed {seed}), {steps} full steps "
+                      f"(CFL dt each), FP64, {el:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("sweep_fluid.cu", "sweep_mag.cu", "mhd_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1004_1680_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    r = rec.get(kernel)
+    if not r or r.get("source_hash") != kernel_source_hash():
+        return None
+    return r["bytes_per_cell"] * n ** 3
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import torch
+
+    import oracle
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    n = args.cpu_sample
+    g = 5.0 / 3.0
+    s = ic.turbulence((n, n, n), seed=args.seed, dtype=torch.float64).numpy().copy()
+    for _ in range(args.warmup):
+        oracle.step(s, oracle.cfl_dt(s, g, args.cfl), g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(s, oracle.cfl_dt(s, g, args.cfl), g)
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"turbulence {n}^3 sample of the {args.size}^3 recipe "
+                                  f"(FP64 CPU oracle)", "n": n, "seed": args.seed, "cfl": args.cfl},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": f"{n}^3 turbulence, {args.steps} timed full steps"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    from paper_1004_1680_gb300 import mhd
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.size
+    N = n ** 3
+    box = mhd.Box(n, n, n, gamma=5.0 / 3.0)
+    stream = torch.cuda.current_stream()
+    st = ic.turbulence((n, n, n), seed=args.seed + rank, device="cuda", dtype=torch.float32)
+    host = st.cpu().pin_memory()     # for the end-to-end leg
+    box.set_state(st)
+    torch.cuda.synchronize()
+    del st
+    torch.cuda.empty_cache()
+
+    box.run(args.warmup, args.cfl)
+    box.cfl_dt(args.cfl)               # raises if the state went invalid
+    launches_per_step = 13
+    box.profile(args.steps * launches_per_step + 16)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    box.run(args.steps, args.cfl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    box.cfl_dt(args.cfl)               # state still valid after the timed run
+    prof = box.profile_read()
+    box.profile(0)
+    if world > 1:
+        t = torch.tensor([secs], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    value = N * args.steps * world / secs
+
+    # per-kernel roofline of the dominant kernel family
+    fam = {"fluid": [prof[k] for k in ("fluid_x", "fluid_y", "fluid_z")],
+           "mag": [prof[k] for k in ("mag_x", "mag_y", "mag_z")]}
+    tot = {f: sum(ms for _, ms in v) for f, v in fam.items()}
+    dom = max(tot, key=tot.get)
+    cnt = sum(c for c, _ in fam[dom])
+    avg_s = tot[dom] / cnt / 1e3
+    achieved = ALGO_BYTES[dom] * N / avg_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic(dom, n)
+    per_kernel = {k: {"launches": c, "avg_ms": (ms / c if c else None),
+                      "GB/s": ((ALGO_BYTES["fluid" if k.startswith("fluid") else "mag"] * N / (ms / c / 1e3) / 1e9)
+                               if c and k != "control" else None)}
+                  for k, (c, ms) in prof.items()}
+    launches = sum(c for c, _ in prof.values())
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        out_host = torch.empty_like(host).pin_memory()
+        box.set_state(host)
+        box.run(1, args.cfl)
+        box.get_state(out_host)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            box.set_state(host)          # H2D of the 8 fields
+            box.run(1, args.cfl)         # CFL + 12 sweeps
+            box.get_state(out_host)      # D2H of the 8 fields (synchronises)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        es = f0.elapsed_time(f1) / 1e3
+        if world > 1:
+            t = torch.tensor([es], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            es = float(t.item())
+        e2e = {"value": N * args.e2e_steps * world / es, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * 4 * N, "d2h_bytes_per_step": 8 * 4 * N,
+               "ms_per_step": 1e3 * es / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample, args.seed, args.cfl)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"decaying MHD turbulence {n}^3, periodic, FP32 state",
+                          "n": n, "seed": args.seed, "cfl": args.cfl,
+                          "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
+                          "l2": f"state {32 * N / 1e9:.1f} GB per copy > L2 (no flush needed)",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom} sweep",
+                            "algorithmic_bytes_per_cell": ALGO_BYTES[dom],
+                            "peak_kind": peak_kind},
+               "step_roofline": {"model_bytes_per_cell": STEP_BYTES,
+                                 "achieved_GBps": STEP_BYTES * N * args.steps / secs / 1e9,
+                                 "frac": STEP_BYTES * N * args.steps / secs / 1e9 / peak},
+               "per_kernel": per_kernel,
+               "gpu_launches": launches,
+               "clocks": clk,
+               "e2e": e2e,
+               "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    box.close()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,152 @@
+/*
+ * mhd.h -- C ABI of the GB300 (sm_103a) dimensionally split ideal-MHD grid
+ * update of Pang, Pen & Perrone, "Magnetohydrodynamics on Heterogeneous
+ * architectures: a performance comparison".
+ *
+ * The problem (Section III, first paragraphs): evolve a periodic 3-D box of
+ * nx*ny*nz zones of ideal MHD (Eq. 1-5) by one timestep, in single
+ * precision, with no host<->device traffic inside the evolution.  One
+ * timestep (Section II.B) is a CFL timestep choice followed by sweeps along
+ * x, y, z and then z, y, x; every sweep is a relaxing-TVD fluid update
+ * (Eq. 6, MUSCL + van Leer, 2-stage Runge-Kutta) and a constrained-transport
+ * advection-constraint update of the face-centred magnetic field.
+ *
+ * Conventions shared by every call:
+ *   - Domain: the periodic unit cube, cell size h_d = 1/n_d.
+ *   - State: 8 single-precision fields, in this order:
+ *       0 rho, 1 m_x, 2 m_y, 3 m_z, 4 e, 5 b_x, 6 b_y, 7 b_z.
+ *     Each field is a contiguous array of nx*ny*nz floats, flat index
+ *     i + nx*(j + ny*k) (x fastest).  b is in units with 4*pi absorbed
+ *     (Section II.A); e = rho v^2/2 + p/(gamma-1) + b^2/2 (Eq. 3).
+ *     b_d[i,j,k] is the mean normal field over the LOW face of cell (i,j,k)
+ *     along d; the cell-centred field is the mean of the cell's two faces.
+ *   - Ownership: every device buffer behind an mhd_t is allocated by
+ *     mhd_create and freed by mhd_destroy.  Pointers passed in are borrowed
+ *     for the duration of the call only.  No call allocates memory the
+ *     caller must free.
+ *   - Streams: all device work is ordered on the stream set with
+ *     mhd_set_stream (default: the legacy default stream).  Calls that
+ *     return host data (mhd_get_state, mhd_cfl_dt, mhd_time,
+ *     mhd_diagnostics) synchronise that stream.
+ *   - Errors: every int-returning call returns MHD_OK (0) or one of the
+ *     codes below; mhd_last_error() then describes the failure (thread-local
+ *     string, valid until the next failing call on the same thread).
+ *   - Sizes: nx, ny, nz >= 1, nx a multiple of 4 (128-bit loads along x),
+ *     and a single field must hold fewer than 2^31 cells.
+ */
+#ifndef MHD_GB300_H
+#define MHD_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHD_OK 0
+#define MHD_E_ARG 1     /* invalid argument: NULL, bad size, gamma <= 1, ...   */
+#define MHD_E_CUDA 2    /* a CUDA runtime call failed                          */
+#define MHD_E_OOM 3     /* device allocation failed                            */
+#define MHD_E_STATE 4   /* NaN, rho <= 0 or p <= 0 found in the state          */
+#define MHD_E_TIMEOUT 5 /* a bounded device-side wait gave up                  */
+
+typedef struct mhd_s mhd_t;
+
+/* Create a box of nx*ny*nz zones with adiabatic index gamma (> 1).
+ * Allocates two copies of the 8-field state on the current CUDA device
+ * (sweeps write out of place).  Returns NULL on failure (see mhd_last_error).
+ * The state is zero until mhd_set_state. */
+mhd_t *mhd_create(int nx, int ny, int nz, double gamma);
+
+/* Free all device memory of the box.  NULL is ignored. */
+void mhd_destroy(mhd_t *m);
+
+/* Order all later work of this box on `cuda_stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream).  NULL selects the default stream. */
+int mhd_set_stream(mhd_t *m, void *cuda_stream);
+
+/* Copy a state in.  f[q] points at field q (nx*ny*nz floats, layout above),
+ * in device memory if on_device != 0, else in host memory (pinned memory
+ * gives asynchronous copies).  Also recomputes the CFL rate of the new state
+ * and sets the simulation time to 0. */
+int mhd_set_state(mhd_t *m, const float *const f[8], int on_device);
+
+/* Copy the current state out into caller-allocated buffers f[q] (device if
+ * on_device != 0, else host).  Synchronises the stream. */
+int mhd_get_state(const mhd_t *m, float *const f[8], int on_device);
+
+/* Largest stable full timestep of the current state (Section II.B: the
+ * fastest wave moves at most `cfl` cells per sweep):
+ *   dt_full = 2 * cfl / max_cells max_d (|v_d| + c_f*) / h_d,
+ *   c_f* = sqrt((gamma p + |b_c|^2) / rho).
+ * Each of the 6 sweeps of a step uses dt_full/2.  Returns MHD_E_STATE if any
+ * cell has NaN, rho <= 0 or p <= 0.  Synchronises the stream. */
+int mhd_cfl_dt(mhd_t *m, double cfl, double *dt_full);
+
+/* One full timestep of length dt_full (Section II.B): fluid_x, mag_x,
+ * fluid_y, mag_y, fluid_z, mag_z, then mag_z, fluid_z, mag_y, fluid_y,
+ * mag_x, fluid_x, every sweep with step dt_full/2.  Asynchronous. */
+int mhd_step(mhd_t *m, double dt_full);
+
+/* nsteps full timesteps, each with its own CFL timestep computed on the
+ * device from the state at the start of that step (no host round trip).
+ * Asynchronous.  A step whose starting state is invalid (NaN, rho <= 0 or
+ * p <= 0) gets dt = 0; mhd_cfl_dt afterwards reports MHD_E_STATE. */
+int mhd_run(mhd_t *m, int nsteps, double cfl);
+
+/* Simulation time accumulated by mhd_step / mhd_run since mhd_set_state.
+ * Synchronises the stream. */
+int mhd_time(const mhd_t *m, double *t);
+
+/* A single sweep along axis (0 = x, 1 = y, 2 = z) with step tau:
+ * kind 0 = relaxing-TVD fluid update (b frozen), kind 1 = magnetic
+ * advection-constraint update (Section II.B).  Asynchronous.  Used to test
+ * the sweeps one by one. */
+int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
+
+/* Pencil segment lengths used by the sweeps along x, y and z.  A sweep splits
+ * every pencil of n_d cells into n_d/seg_d pieces, each marched by its own
+ * thread (more parallelism for small boxes, 8 cells of warm-up re-read per
+ * piece).  Each seg_d must be a multiple of 4 that divides n_d; 0 restores
+ * the automatic choice.  The arithmetic of every cell is the same for any
+ * segmentation, so results are bitwise independent of it. */
+int mhd_set_segments(mhd_t *m, int seg_x, int seg_y, int seg_z);
+
+/* FP64 diagnostics of the current state, computed on the device with
+ * compensated (Neumaier) sums in a fixed order, so repeated calls on the same
+ * state give bitwise identical results:
+ *   out[0..7] = sums over all cells of rho, m_x, m_y, m_z, e, b_x, b_y, b_z;
+ *   out[8]    = max over cells of |div b| * h_min, div b the cell's discrete
+ *               flux balance sum_d (b_d(high) - b_d(low)) / h_d,
+ *               h_min = 1 / max(nx, ny, nz);
+ *   out[9]    = min over cells of the gas pressure p.
+ * `out` is host memory.  Synchronises the stream. */
+int mhd_diagnostics(mhd_t *m, double out[10]);
+
+/* Kernel classes reported by mhd_profile_read. */
+#define MHD_K_FLUID_X 0
+#define MHD_K_FLUID_Y 1
+#define MHD_K_FLUID_Z 2
+#define MHD_K_MAG_X 3
+#define MHD_K_MAG_Y 4
+#define MHD_K_MAG_Z 5
+#define MHD_K_CONTROL 6 /* step control, CFL reduction, diagnostics */
+#define MHD_K_CLASSES 7
+
+/* Per-kernel device timing (tracing).  With capacity > 0, every later kernel
+ * launch of this box is bracketed by a pair of CUDA events on its stream,
+ * for up to `capacity` launches (later launches are not timed); capacity 0
+ * stops timing and drops the records.  Events are created here, not at
+ * launch time. */
+int mhd_profile(mhd_t *m, int capacity);
+
+/* Launch counts and summed device milliseconds per kernel class since
+ * mhd_profile (arrays of MHD_K_CLASSES entries, host memory).  Synchronises
+ * the stream.  Records are kept, so repeated reads give the same totals. */
+int mhd_profile_read(mhd_t *m, int counts[], double ms[]);
+
+/* Description of the last failure on this thread ("" if none). */
+const char *mhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_GB300_H */

@@ -1,0 +1,392 @@
+// Host side of the C ABI declared in include/mhd.h: the box context, its
+// device memory, the timestep schedule of Section II.B and error handling.
+//
+// Memory layout in HBM: one arena of 16 planar FP32 arrays (two copies of the
+// 8 fields; every sweep reads one copy and writes the other, field by field),
+// plus a few device scalars (sweep step, two CFL-rate accumulators, the
+// simulation time) and the FP64 diagnostics scratch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mhd.h"
+#include "mhd_launch.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, const char* what = "") {
+  std::snprintf(g_err, sizeof g_err, fmt, what);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MHD_E_OOM : MHD_E_CUDA;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+struct Scalars {  // small device block
+  float tau;
+  unsigned rate[2];
+  unsigned pad;
+  double time;
+  double diag[10];
+};
+
+}  // namespace
+
+struct mhd_s {
+  int n[3];
+  double gamma;
+  long long N;
+  mhd::Box box;
+  float* arena = nullptr;
+  float* buf[2][8];
+  int cur[8];
+  Scalars* sc = nullptr;
+  double* diag_partial = nullptr;
+  int rcur = 0;
+  cudaStream_t stream = nullptr;
+  int seg[3];
+  // tracing: event pairs around launches (see mhd_profile)
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+// Segment length along each axis: whole pencils when they already give the
+// GPU enough threads, otherwise split pencils (each split re-reads 8 cells of
+// warm-up) down to 32 cells.
+int choose_seg(const mhd_s* m, int d) {
+  const int nd = m->n[d];
+  const long long pencils = m->N / nd;
+  const long long want = 152LL * 1024;  // threads for about one full wave of the GPU
+  int seg = nd;
+  while (pencils * (nd / seg) < want && seg % 8 == 0 && seg / 2 >= 32 && nd % (seg / 2) == 0)
+    seg /= 2;
+  return seg;
+}
+
+// Bracket the launches issued by `body` with an event pair when tracing.
+template <class F>
+int traced(mhd_s* m, int kind, F body) {
+  const bool on = m->ev_used < m->ev_kind.size();
+  if (on) CK(cudaEventRecord(m->ev[2 * m->ev_used], m->stream));
+  int rc = body();
+  if (rc) return rc;
+  if (on) {
+    CK(cudaEventRecord(m->ev[2 * m->ev_used + 1], m->stream));
+    m->ev_kind[m->ev_used++] = kind;
+  }
+  return MHD_OK;
+}
+
+void drop_events(mhd_s* m) {
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  m->ev.clear();
+  m->ev_kind.clear();
+  m->ev_used = 0;
+}
+
+void field_ptrs(const mhd_s* m, const float* out[8]) {
+  for (int q = 0; q < 8; q++) out[q] = m->buf[m->cur[q]][q];
+}
+
+int fluid(mhd_s* m, int d, bool rate) {
+  mhd::FluidArgs a;
+  for (int q = 0; q < 8; q++) {
+    a.in[q] = m->buf[m->cur[q]][q];
+    a.out[q] = m->buf[1 - m->cur[q]][q];
+  }
+  a.box = m->box;
+  a.gamma = (float)m->gamma;
+  a.tau = &m->sc->tau;
+  a.rate = rate ? &m->sc->rate[1 - m->rcur] : nullptr;
+  a.seg = m->seg[d];
+  int rc = traced(m, MHD_K_FLUID_X + d, [&] {
+    CK(mhd::launch_fluid(d, rate, a, m->stream));
+    return MHD_OK;
+  });
+  if (rc) return rc;
+  for (int q = 0; q < 5; q++) m->cur[q] ^= 1;
+  return MHD_OK;
+}
+
+int magnetic(mhd_s* m, int d) {
+  mhd::MagArgs a;
+  for (int q = 0; q < 8; q++) a.in[q] = m->buf[m->cur[q]][q];
+  for (int q = 0; q < 3; q++) a.out[q] = m->buf[1 - m->cur[5 + q]][5 + q];
+  a.box = m->box;
+  a.tau = &m->sc->tau;
+  a.seg = m->seg[d];
+  int rc = traced(m, MHD_K_MAG_X + d, [&] {
+    CK(mhd::launch_mag(d, a, m->stream));
+    return MHD_OK;
+  });
+  if (rc) return rc;
+  for (int q = 5; q < 8; q++) m->cur[q] ^= 1;
+  return MHD_OK;
+}
+
+// The sweep schedule of one full step (Section II.B): x, y, z forward with
+// fluid before magnetic, then z, y, x with magnetic before fluid; the last
+// fluid sweep also accumulates the CFL rate of the new state.
+int full_step(mhd_s* m) {
+  int rc;
+  for (int d = 0; d < 3; d++) {
+    if ((rc = fluid(m, d, false))) return rc;
+    if ((rc = magnetic(m, d))) return rc;
+  }
+  for (int d = 2; d >= 0; d--) {
+    if ((rc = magnetic(m, d))) return rc;
+    if ((rc = fluid(m, d, d == 0))) return rc;
+  }
+  m->rcur ^= 1;
+  return MHD_OK;
+}
+
+bool check_box(const mhd_t* m) {
+  if (!m) {
+    fail(MHD_E_ARG, "null mhd_t");
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
+  if (nx < 4 || ny < 1 || nz < 1 || nx % 4 != 0) {
+    fail(MHD_E_ARG, "bad box size (need nx >= 4, nx %% 4 == 0, ny, nz >= 1)");
+    return nullptr;
+  }
+  if (!(gamma > 1.0)) {
+    fail(MHD_E_ARG, "gamma must be > 1");
+    return nullptr;
+  }
+  const long long N = (long long)nx * ny * nz;
+  if (N >= (1LL << 31)) {
+    fail(MHD_E_ARG, "box too large: a field must hold fewer than 2^31 cells");
+    return nullptr;
+  }
+  mhd_s* m = new (std::nothrow) mhd_s;
+  if (!m) {
+    fail(MHD_E_OOM, "host allocation failed");
+    return nullptr;
+  }
+  m->n[0] = nx;
+  m->n[1] = ny;
+  m->n[2] = nz;
+  m->gamma = gamma;
+  m->N = N;
+  m->box.n[0] = nx;
+  m->box.n[1] = ny;
+  m->box.n[2] = nz;
+  m->box.stride[0] = 1;
+  m->box.stride[1] = nx;
+  m->box.stride[2] = (long long)nx * ny;
+  cudaError_t e = cudaMalloc(&m->arena, sizeof(float) * (size_t)N * 16);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "cudaMalloc(state)");
+    delete m;
+    return nullptr;
+  }
+  for (int c = 0; c < 2; c++)
+    for (int q = 0; q < 8; q++) m->buf[c][q] = m->arena + (size_t)N * (8 * c + q);
+  for (int q = 0; q < 8; q++) m->cur[q] = 0;
+  const int nblk = mhd::diag_blocks(m->box);
+  if ((e = cudaMalloc(&m->sc, sizeof(Scalars))) != cudaSuccess ||
+      (e = cudaMalloc(&m->diag_partial, sizeof(double) * mhd::kDiagSlots * nblk)) != cudaSuccess ||
+      (e = cudaMemset(m->sc, 0, sizeof(Scalars))) != cudaSuccess ||
+      (e = cudaMemset(m->arena, 0, sizeof(float) * (size_t)N * 16)) != cudaSuccess) {
+    cuda_fail(e, "mhd_create");
+    cudaFree(m->arena);
+    cudaFree(m->sc);
+    cudaFree(m->diag_partial);
+    delete m;
+    return nullptr;
+  }
+  for (int d = 0; d < 3; d++) m->seg[d] = choose_seg(m, d);
+  return m;
+}
+
+void mhd_destroy(mhd_t* m) {
+  if (!m) return;
+  drop_events(m);
+  cudaFree(m->arena);
+  cudaFree(m->sc);
+  cudaFree(m->diag_partial);
+  delete m;
+}
+
+int mhd_set_stream(mhd_t* m, void* cuda_stream) {
+  if (!check_box(m)) return MHD_E_ARG;
+  m->stream = (cudaStream_t)cuda_stream;
+  return MHD_OK;
+}
+
+int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
+  if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  for (int q = 0; q < 8; q++)
+    if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  const size_t bytes = sizeof(float) * (size_t)m->N;
+  for (int q = 0; q < 8; q++) {
+    m->cur[q] = 0;
+    CK(cudaMemcpyAsync(m->buf[0][q], f[q], bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+  }
+  CK(cudaMemsetAsync(m->sc, 0, sizeof(Scalars), m->stream));
+  m->rcur = 0;
+  const float* cf[8];
+  field_ptrs(m, cf);
+  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[0], m->stream));
+  return MHD_OK;
+}
+
+int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
+  if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  for (int q = 0; q < 8; q++)
+    if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  const size_t bytes = sizeof(float) * (size_t)m->N;
+  for (int q = 0; q < 8; q++)
+    CK(cudaMemcpyAsync(f[q], m->buf[m->cur[q]][q], bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return MHD_OK;
+}
+
+int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
+  if (!check_box(m) || !dt_full) return fail(MHD_E_ARG, "null argument");
+  if (!(cfl > 0.0)) return fail(MHD_E_ARG, "cfl must be > 0");
+  unsigned bits = 0;
+  CK(cudaMemcpyAsync(&bits, &m->sc->rate[m->rcur], sizeof bits, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  float r;
+  std::memcpy(&r, &bits, sizeof r);
+  if (!(r > 0.f) || !std::isfinite(r)) {
+    *dt_full = 0.0;
+    return fail(MHD_E_STATE, "invalid state: NaN, rho <= 0 or p <= 0 in some cell");
+  }
+  *dt_full = 2.0 * cfl / (double)r;
+  return MHD_OK;
+}
+
+int mhd_step(mhd_t* m, double dt_full) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (!(dt_full >= 0.0) || !std::isfinite(dt_full)) return fail(MHD_E_ARG, "dt must be finite and >= 0");
+  int rc = traced(m, MHD_K_CONTROL, [&] {
+    CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
+                                &m->sc->time, -1.0, 0.5 * dt_full, m->stream));
+    return MHD_OK;
+  });
+  return rc ? rc : full_step(m);
+}
+
+int mhd_run(mhd_t* m, int nsteps, double cfl) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (nsteps < 0 || !(cfl > 0.0)) return fail(MHD_E_ARG, "need nsteps >= 0 and cfl > 0");
+  for (int s = 0; s < nsteps; s++) {
+    int rc = traced(m, MHD_K_CONTROL, [&] {
+      CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
+                                  &m->sc->time, cfl, 0.0, m->stream));
+      return MHD_OK;
+    });
+    if (!rc) rc = full_step(m);
+    if (rc) return rc;
+  }
+  return MHD_OK;
+}
+
+int mhd_time(const mhd_t* m, double* t) {
+  if (!check_box(m) || !t) return fail(MHD_E_ARG, "null argument");
+  CK(cudaMemcpyAsync(t, &m->sc->time, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return MHD_OK;
+}
+
+int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (axis < 0 || axis > 2 || kind < 0 || kind > 1 || !(tau >= 0.0))
+    return fail(MHD_E_ARG, "bad axis/kind/tau");
+  // a single sweep does not advance the simulation time; afterwards the CFL
+  // rate is recomputed for the new state
+  CK(mhd::launch_set_tau(&m->sc->tau, tau, m->stream));
+  int rc = kind == 0 ? fluid(m, axis, false) : magnetic(m, axis);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(&m->sc->rate[m->rcur], 0, sizeof(unsigned), m->stream));
+  const float* cf[8];
+  field_ptrs(m, cf);
+  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[m->rcur], m->stream));
+  return MHD_OK;
+}
+
+int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {
+  if (!check_box(m)) return MHD_E_ARG;
+  const int seg[3] = {seg_x, seg_y, seg_z};
+  for (int d = 0; d < 3; d++)
+    if (seg[d] != 0 && (seg[d] < 4 || seg[d] % 4 != 0 || m->n[d] % seg[d] != 0))
+      return fail(MHD_E_ARG, "segment length must be a multiple of 4 dividing n_d");
+  for (int d = 0; d < 3; d++) m->seg[d] = seg[d] ? seg[d] : choose_seg(m, d);
+  return MHD_OK;
+}
+
+int mhd_diagnostics(mhd_t* m, double out[10]) {
+  if (!check_box(m) || !out) return fail(MHD_E_ARG, "null argument");
+  const float* cf[8];
+  field_ptrs(m, cf);
+  CK(mhd::launch_diagnostics(cf, m->box, m->gamma, m->diag_partial, m->sc->diag, m->stream));
+  CK(cudaMemcpyAsync(out, m->sc->diag, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return MHD_OK;
+}
+
+int mhd_profile(mhd_t* m, int capacity) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (capacity < 0) return fail(MHD_E_ARG, "capacity must be >= 0");
+  CK(cudaStreamSynchronize(m->stream));
+  drop_events(m);
+  m->ev.resize(2 * (size_t)capacity);
+  for (auto& e : m->ev) {
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) {
+      e = nullptr;
+      drop_events(m);
+      return cuda_fail(err, "cudaEventCreate");
+    }
+  }
+  m->ev_kind.assign((size_t)capacity, -1);
+  return MHD_OK;
+}
+
+int mhd_profile_read(mhd_t* m, int counts[], double ms[]) {
+  if (!check_box(m) || !counts || !ms) return fail(MHD_E_ARG, "null argument");
+  for (int k = 0; k < MHD_K_CLASSES; k++) {
+    counts[k] = 0;
+    ms[k] = 0.0;
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  for (size_t i = 0; i < m->ev_used; i++) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, m->ev[2 * i], m->ev[2 * i + 1]));
+    counts[m->ev_kind[i]] += 1;
+    ms[m->ev_kind[i]] += t;
+  }
+  return MHD_OK;
+}
+
+const char* mhd_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// Magnetic advection-constraint sweep along one axis D (Section II.B), FP32.
+//
+// For each transverse axis t the face field b_t is advected along D by the
+// upwind + van Leer, 2-stage scheme (MagPipe), and the edge flux f_t it
+// produces is applied to b_D:
+//   b_t(cell)          -= tau/h_D (f_t(i+1/2) - f_t(i-1/2))
+//   b_D(face i+1/2, P) += tau/h_t (f_t(pencil P+e_t) - f_t(pencil P)),
+// which keeps the discrete div b of every cell unchanged (Eq. 5).  The edge
+// flux lives on the edge (D: i+1/2, t: low face of pencil P); the EMF pieces
+// are applied directly and never written to memory.
+//
+// A block owns a tile of 32 (lane axis A) x kMagWarps (row axis O) pencils and
+// marches all of them together along D.  Two extra warps march the halo
+// pencils whose flux the tile needs: row O+kMagWarps (its f along O) and
+// column A+32 (its f along A).  Fluxes are exchanged through shared memory
+// once per chunk of 4 positions.  Writes are out of place.
+#include "mhd_device.cuh"
+#include "mhd_launch.h"
+
+namespace mhd {
+
+template <int D>
+struct MagAxes {
+  static constexpr int A = (D == 0) ? 1 : 0;
+  static constexpr int O = (D == 2) ? 1 : 2;
+  static constexpr int T1 = (D + 1) % 3;
+};
+
+template <int D>
+__global__ void __launch_bounds__(32 * (kMagWarps + 2))
+mag_sweep_kernel(MagArgs a) {
+  using X = MagAxes<D>;
+  __shared__ float fA_s[4][kMagWarps][33];       // flux of b_A, column 32 = halo column
+  __shared__ float fO_s[4][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
+
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int nA = a.box.n[X::A], nO = a.box.n[X::O], nD = a.box.n[D];
+  const int a0 = blockIdx.x * 32, b0 = blockIdx.y * kMagWarps;
+  const int cntA = min(32, nA - a0), cntO = min(kMagWarps, nO - b0);
+
+  // this thread's pencil and role
+  int pa, pb;
+  bool interior = false;
+  int row, col;  // slot in the exchange arrays
+  if (w < kMagWarps) {
+    pa = a0 + min(lane, cntA - 1);
+    pb = b0 + min(w, cntO - 1);
+    interior = (lane < cntA) && (w < cntO);
+    row = w;
+    col = lane;
+  } else if (w == kMagWarps) {             // halo row: pencils (a0+lane, b0+cntO)
+    pa = a0 + min(lane, cntA - 1);
+    pb = wrapi(b0 + cntO, nO);
+    row = cntO;
+    col = lane;
+  } else {                                 // halo column: pencils (a0+cntA, b0+lane)
+    pa = wrapi(a0 + cntA, nA);
+    pb = b0 + min(lane, cntO - 1);
+    row = min(lane, kMagWarps - 1);
+    col = cntA;
+  }
+  const long long sA = a.box.stride[X::A], sO = a.box.stride[X::O], sD = a.box.stride[D];
+  const long long base = pa * sA + pb * sO;
+  const long long baseAm = wrapi(pa - 1, nA) * sA + pb * sO;  // pencil -1 along A
+  const long long baseOm = pa * sA + wrapi(pb - 1, nO) * sO;  // pencil -1 along O
+
+  const float* __restrict__ rho = a.in[RHO];
+  const float* __restrict__ md = a.in[MX + D];
+  const float* __restrict__ bA = a.in[BX + X::A];
+  const float* __restrict__ bO = a.in[BX + X::O];
+  const float* __restrict__ bD = a.in[BX + D];
+  float* __restrict__ o_bA = a.out[X::A];
+  float* __restrict__ o_bO = a.out[X::O];
+  float* __restrict__ o_bD = a.out[D];
+
+  const float tau = *a.tau;
+  const float c_full = tau * (float)nD;        // tau / h_D
+  const float c_half = 0.5f * c_full;
+  const float kA = tau * (float)nA;             // tau / h_A
+  const float kO = tau * (float)nO;             // tau / h_O
+  const int s0 = blockIdx.z * a.seg;
+  const int s1 = s0 + a.seg;
+  // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
+  // warm-up cell so that x chunks start 16-byte aligned)
+  const int nchunk = (a.seg + 7 + 3) / 4;
+  // slots read by the tile: fO rows 0..cntO (row cntO = halo row), fA columns
+  // 0..cntA (column cntA = halo column); idle lanes of a partial tile must not
+  // overwrite a halo slot
+  const bool write_row = (w < kMagWarps) ? (w < cntO) : (w == kMagWarps);
+  const bool write_col = (w < kMagWarps) ? (w < cntO && lane < cntA)
+                                         : (w == kMagWarps + 1 && lane < cntO);
+
+  MagPipe pA, pO;
+  pA.init();
+  pO.init();
+  float bD1 = 0.f, bD2 = 0.f;  // raw b_D at t-1, t-2
+
+  for (int c = 0; c < nchunk; c++) {
+    const int p0 = s0 - 4 + 4 * c;
+    const int pw = wrapi(p0, nD);
+    float r[4], m[4], rA[4], mA[4], rO[4], mO[4], qA[4], qO[4], qD[4];
+    if (D == 0) {
+      float4 v;
+#define LD4(dst, ptr, off)                                   \
+  v = __ldg(reinterpret_cast<const float4*>((ptr) + (off))); \
+  dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+      LD4(r, rho, base + pw) LD4(m, md, base + pw)
+      LD4(rA, rho, baseAm + pw) LD4(mA, md, baseAm + pw)
+      LD4(rO, rho, baseOm + pw) LD4(mO, md, baseOm + pw)
+      LD4(qA, bA, base + pw) LD4(qO, bO, base + pw) LD4(qD, bD, base + pw)
+#undef LD4
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const long long off = (long long)wrapi(p0 + j, nD) * sD;
+        r[j] = __ldg(rho + base + off);
+        m[j] = __ldg(md + base + off);
+        rA[j] = __ldg(rho + baseAm + off);
+        mA[j] = __ldg(md + baseAm + off);
+        rO[j] = __ldg(rho + baseOm + off);
+        mO[j] = __ldg(md + baseOm + off);
+        qA[j] = __ldg(bA + base + off);
+        qO[j] = __ldg(bO + base + off);
+        qD[j] = __ldg(bD + base + off);
+      }
+    }
+    float bDold[4];  // raw b_D at the face each position's constraint updates
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const float v = __fdividef(m[j], r[j]);
+      const float uA = 0.5f * (v + __fdividef(mA[j], rA[j]));  // v_D on the b_A face
+      const float uO = 0.5f * (v + __fdividef(mO[j], rO[j]));  // v_D on the b_O face
+      float nA_new, nO_new;
+      const float fa = pA.step(qA[j], uA, c_half, c_full, nA_new);
+      const float fo = pO.step(qO[j], uO, c_half, c_full, nO_new);
+      if (write_row) fO_s[j][row][col] = fo;
+      if (write_col) fA_s[j][row][col] = fa;
+      bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
+      bD2 = bD1;
+      bD1 = qD[j];
+      const int t = p0 + j;
+      const int po = t - 3;
+      if (interior && po >= s0 && po < s1) {
+        const long long cell = base + (long long)wrapi(po, nD) * sD;
+        o_bA[cell] = nA_new;
+        o_bO[cell] = nO_new;
+      }
+    }
+    __syncthreads();
+    if (interior) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int t = p0 + j;
+        const int pf = t - 2;  // b_D face updated by the edge flux f(t-5/2)
+        if (pf >= s0 && pf < s1) {
+          const float fa0 = fA_s[j][row][col], fa1 = fA_s[j][row][col + 1];
+          const float fo0 = fO_s[j][row][col], fo1 = fO_s[j][row + 1][col];
+          float b = bDold[j];
+          if (X::T1 == X::A) {
+            b += kA * (fa1 - fa0);
+            b += kO * (fo1 - fo0);
+          } else {
+            b += kO * (fo1 - fo0);
+            b += kA * (fa1 - fa0);
+          }
+          o_bD[base + (long long)wrapi(pf, nD) * sD] = b;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace mhd
+
+namespace mhd {
+
+cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s) {
+  const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
+  dim3 block(32, kMagWarps + 2);
+  dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
+  switch (axis) {
+    case 0: mag_sweep_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 1: mag_sweep_kernel<1><<<grid, block, 0, s>>>(a); break;
+    default: mag_sweep_kernel<2><<<grid, block, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,179 @@
+"""Python binding of the C ABI in include/mhd.h (argument marshalling only).
+
+Every step of the update runs in the CUDA library libmhd_gb300.so; this module
+only converts torch tensors / numpy arrays into pointers and return codes
+into exceptions.  There is no fallback: if the library or a GPU is missing,
+constructing a Box raises.
+
+State tensors have shape (8, nz, ny, nx), dtype float32, fields in the order
+rho, m_x, m_y, m_z, e, b_x, b_y, b_z (b_d on the low face of each cell).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MHD_OK, MHD_E_ARG, MHD_E_CUDA, MHD_E_OOM, MHD_E_STATE, MHD_E_TIMEOUT = range(6)
+_ERR_NAMES = {1: "MHD_E_ARG", 2: "MHD_E_CUDA", 3: "MHD_E_OOM", 4: "MHD_E_STATE", 5: "MHD_E_TIMEOUT"}
+
+_lib = None
+_lock = threading.Lock()
+
+# Exported symbols and their ctypes signatures (kept in sync with include/mhd.h).
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "mhd_create": (_P, [_I, _I, _I, _D]),
+    "mhd_destroy": (None, [_P]),
+    "mhd_set_stream": (_I, [_P, _P]),
+    "mhd_set_state": (_I, [_P, _PP, _I]),
+    "mhd_get_state": (_I, [_P, _PP, _I]),
+    "mhd_cfl_dt": (_I, [_P, _D, _DP]),
+    "mhd_step": (_I, [_P, _D]),
+    "mhd_run": (_I, [_P, _I, _D]),
+    "mhd_time": (_I, [_P, _DP]),
+    "mhd_sweep": (_I, [_P, _I, _I, _D]),
+    "mhd_set_segments": (_I, [_P, _I, _I, _I]),
+    "mhd_diagnostics": (_I, [_P, _DP]),
+    "mhd_profile": (_I, [_P, _I]),
+    "mhd_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_int), _DP]),
+    "mhd_last_error": (ctypes.c_char_p, []),
+}
+
+
+KERNEL_CLASSES = ["fluid_x", "fluid_y", "fluid_z", "mag_x", "mag_y", "mag_z", "control"]
+K_CLASSES = len(KERNEL_CLASSES)
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libmhd_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and _build.stale():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path}")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MHD_OK:
+        raise MHDError(rc, _lib.mhd_last_error().decode())
+
+
+def _field_ptrs(t: torch.Tensor):
+    return (ctypes.c_void_p * 8)(*[t[q].data_ptr() for q in range(8)])
+
+
+class Box:
+    """One periodic MHD box on the current CUDA device (wraps mhd_t)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, gamma: float = 5.0 / 3.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.lib = load()
+        self.shape = (8, nz, ny, nx)
+        self.n = (nx, ny, nz)
+        self.gamma = gamma
+        h = self.lib.mhd_create(nx, ny, nz, gamma)
+        if not h:
+            raise MHDError(MHD_E_ARG, self.lib.mhd_last_error().decode())
+        self.h = ctypes.c_void_p(h)
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.stream = stream
+        _check(self.lib.mhd_set_stream(self.h, ctypes.c_void_p(ptr)))
+
+    def set_state(self, state: torch.Tensor):
+        """Copy a float32 (8, nz, ny, nx) state in (CUDA or host tensor)."""
+        if state.shape != self.shape or state.dtype != torch.float32 or not state.is_contiguous():
+            raise ValueError(f"state must be contiguous float32 {self.shape}")
+        _check(self.lib.mhd_set_state(self.h, _field_ptrs(state), 1 if state.is_cuda else 0))
+        self._keep = state  # the copy is asynchronous: keep the source alive
+
+    def get_state(self, out: torch.Tensor | None = None, device="cuda") -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=device)
+        if out.shape != self.shape or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        _check(self.lib.mhd_get_state(self.h, _field_ptrs(out), 1 if out.is_cuda else 0))
+        return out
+
+    def cfl_dt(self, cfl: float = 0.7) -> float:
+        dt = ctypes.c_double()
+        _check(self.lib.mhd_cfl_dt(self.h, cfl, ctypes.byref(dt)))
+        return dt.value
+
+    def step(self, dt: float):
+        _check(self.lib.mhd_step(self.h, float(dt)))
+
+    def run(self, nsteps: int, cfl: float = 0.7):
+        _check(self.lib.mhd_run(self.h, int(nsteps), float(cfl)))
+
+    def time(self) -> float:
+        t = ctypes.c_double()
+        _check(self.lib.mhd_time(self.h, ctypes.byref(t)))
+        return t.value
+
+    def sweep(self, axis: int, kind: int, tau: float):
+        """kind 0: fluid sweep, kind 1: magnetic sweep, along axis with step tau."""
+        _check(self.lib.mhd_sweep(self.h, int(axis), int(kind), float(tau)))
+
+    def set_segments(self, sx: int = 0, sy: int = 0, sz: int = 0):
+        _check(self.lib.mhd_set_segments(self.h, int(sx), int(sy), int(sz)))
+
+    def profile(self, capacity: int):
+        """Time every later kernel launch with CUDA events (up to `capacity`)."""
+        _check(self.lib.mhd_profile(self.h, int(capacity)))
+
+    def profile_read(self) -> dict:
+        """{kernel class: (launches, total device ms)} since profile()."""
+        c = (ctypes.c_int * K_CLASSES)()
+        t = (ctypes.c_double * K_CLASSES)()
+        _check(self.lib.mhd_profile_read(self.h, c, t))
+        return {KERNEL_CLASSES[k]: (c[k], t[k]) for k in range(K_CLASSES)}
+
+    def diagnostics(self) -> np.ndarray:
+        out = (ctypes.c_double * 10)()
+        _check(self.lib.mhd_diagnostics(self.h, out))
+        return np.array(out[:], dtype=np.float64)

@@ -1,0 +1,60 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
+every function declared in include/mhd.h, and rejects bad arguments before
+touching the GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1004_1680_gb300 import build as B
+from paper_1004_1680_gb300 import mhd as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(mhd_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.load()
+
+
+def test_library_builds_for_sm103a(lib):
+    assert os.path.exists(B.LIB)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "mhd_step" in names and "mhd_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding covers them all
+    assert set(names) <= set(M.SIGNATURES)
+
+
+@pytest.mark.parametrize("dims,gamma", [((6, 4, 4), 5 / 3), ((0, 4, 4), 5 / 3), ((8, 0, 4), 5 / 3),
+                                        ((8, 4, 4), 1.0), ((8, 4, 4), float("nan")),
+                                        ((1 << 12, 1 << 10, 1 << 10), 5 / 3)])
+def test_create_rejects_bad_arguments(lib, dims, gamma):
+    assert not lib.mhd_create(dims[0], dims[1], dims[2], gamma)
+    assert b"" != lib.mhd_last_error()
+
+
+def test_null_handle_is_an_argument_error(lib):
+    assert lib.mhd_step(None, 0.1) == M.MHD_E_ARG
+    assert lib.mhd_run(None, 1, 0.7) == M.MHD_E_ARG
+    assert lib.mhd_set_segments(None, 0, 0, 0) == M.MHD_E_ARG
+    dt = ctypes.c_double()
+    assert lib.mhd_cfl_dt(None, 0.7, ctypes.byref(dt)) == M.MHD_E_ARG
+    lib.mhd_destroy(None)

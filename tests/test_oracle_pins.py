@@ -373,6 +373,33 @@ def test_van_leer_advection_step_is_tvd(oracle_lib):
 
 
 # --------------------------------------------------------------------------
+# locality: one full step reaches 14 cells, and depends on tau/h only
+
+def test_one_step_reach_and_sub_block_equivalence(oracle_lib):
+    """The 7-point fluid stencil and the +-1-pencil magnetic coupling give one
+    full step (12 sweeps) a finite reach; a periodic sub-box with a 16-cell
+    halo, stepped with dt scaled by n_full/n_sub (same tau/h), reproduces the
+    interior of the full step exactly."""
+    from tests.parity_util import sub_block
+    n = 64
+    st = ic.turbulence((n, n, n), seed=3, dtype=torch.float64, kmin=1.0, kmax=5.0).numpy().copy()
+    dt = oracle.cfl_dt(st, G, 0.7)
+    a = st.copy()
+    oracle.step(a, dt, G)
+    b = st.copy()
+    b[:, 32, 32, 32] *= 1.001
+    oracle.step(b, dt, G)
+    k, j, i = np.nonzero(np.abs(a - b).max(axis=0) > 0)
+    assert max(abs(i - 32).max(), abs(j - 32).max(), abs(k - 32).max()) <= 14
+    H, L = 16, 8
+    nb = L + 2 * H
+    lo = (20, 3, 50)
+    blk = sub_block(st, [c - H for c in lo], [nb] * 3)
+    oracle.step(blk, dt * n / nb, G)
+    assert np.array_equal(blk[:, H:H + L, H:H + L, H:H + L], sub_block(a, lo, [L] * 3))
+
+
+# --------------------------------------------------------------------------
 # diagnostics and restriction (plain definitions)
 
 def test_diagnostics_definitions(oracle_lib):
