@@ -22,11 +22,36 @@ __host__ __device__ inline int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-// van Leer limiter (Section II.B): 2ab/(a+b) when a and b have the same sign,
-// else 0.  a+b cannot vanish when ab > 0.
-__device__ __forceinline__ float vanleer(float a, float b) {
-  float ab = a * b;
-  return ab > 0.f ? __fdividef(2.f * ab, a + b) : 0.f;
+// Periodic image of a position within a few cells of [0, n): two compares
+// instead of an integer division when n is large enough.
+__device__ __forceinline__ int wrapn(int i, int n) {
+  if (n >= 16) {
+    i = i < 0 ? i + n : i;
+    return i >= n ? i - n : i;
+  }
+  return wrapi(i, n);
+}
+
+// Hardware approximate reciprocal and square root (PTX rcp.approx / sqrt.approx,
+// relative error of a few ulp; the FP32 path's tolerance against the FP64
+// oracle is four orders of magnitude looser).
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fast_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Half the van Leer limiter of Section II.B: phi(a,b)/2 = ab/(a+b) when a and
+// b have the same sign, else 0 (a+b cannot vanish when ab > 0).  The
+// second-order correction adds phi/2 to the upwind value.
+__device__ __forceinline__ float vanleer_half(float a, float b) {
+  const float ab = a * b;
+  return ab > 0.f ? ab * fast_rcp(a + b) : 0.f;
 }
 
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame
@@ -36,25 +61,25 @@ __device__ __forceinline__ float vanleer(float a, float b) {
 // Returns the right and left movers FR = (cu + F)/2, FL = (cu - F)/2.
 __device__ __forceinline__ void split_flux(const float u[5], const float b[3], float gamma,
                                            float FR[5], float FL[5]) {
-  float rinv = __fdividef(1.f, u[0]);
-  float vd = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
-  float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-  float kin = 0.5f * (u[1] * vd + u[2] * v1 + u[3] * v2);
-  float p = (gamma - 1.f) * (u[4] - kin - 0.5f * b2);
-  float pstar = p + 0.5f * b2;
-  float bv = b[0] * vd + b[1] * v1 + b[2] * v2;
+  const float rinv = fast_rcp(u[0]);
+  const float vd = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
+  const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const float kin = 0.5f * (u[1] * vd + u[2] * v1 + u[3] * v2);
+  const float p = (gamma - 1.f) * (u[4] - kin - 0.5f * b2);
+  const float pstar = p + 0.5f * b2;
+  const float bv = b[0] * vd + b[1] * v1 + b[2] * v2;
   float F[5];
   F[0] = u[1];
   F[1] = u[1] * vd + pstar - b[0] * b[0];
   F[2] = u[2] * vd - b[0] * b[1];
   F[3] = u[3] * vd - b[0] * b[2];
   F[4] = (u[4] + pstar) * vd - b[0] * bv;
-  float c = fabsf(vd) + sqrtf((gamma * p + b2) * rinv);
+  const float hc = 0.5f * (fabsf(vd) + fast_sqrt((gamma * p + b2) * rinv));  // c/2
 #pragma unroll
   for (int q = 0; q < 5; q++) {
-    float cu = c * u[q];
-    FR[q] = 0.5f * (cu + F[q]);
-    FL[q] = 0.5f * (cu - F[q]);
+    const float hF = 0.5f * F[q];
+    FR[q] = hc * u[q] + hF;
+    FL[q] = hc * u[q] - hF;
   }
 }
 
@@ -63,12 +88,12 @@ __device__ __forceinline__ void split_flux(const float u[5], const float b[3], f
 // +inf so that a max-reduction flags them.
 __device__ __forceinline__ float cell_rate(float rho, const float m[3], float e, const float b[3],
                                            float gamma, const int n[3]) {
-  float rinv = __fdividef(1.f, rho);
+  float rinv = fast_rcp(rho);
   float v0 = m[0] * rinv, v1 = m[1] * rinv, v2 = m[2] * rinv;
   float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
   float kin = 0.5f * (m[0] * v0 + m[1] * v1 + m[2] * v2);
   float p = (gamma - 1.f) * (e - kin - 0.5f * b2);
-  float cf = sqrtf((gamma * p + b2) * rinv);
+  float cf = fast_sqrt((gamma * p + b2) * rinv);
   float r = fmaxf(fmaxf((fabsf(v0) + cf) * n[0], (fabsf(v1) + cf) * n[1]), (fabsf(v2) + cf) * n[2]);
   bool ok = (rho > 0.f) && (p > 0.f) && (r <= 3.0e38f);
   return ok ? r : __int_as_float(0x7f800000);
@@ -91,15 +116,17 @@ struct FluidPipe {
   float b1[3];                // frozen b at t-1
   float FR1[5];               // stage-1 right mover at t-1
   float f1m[5];               // stage-1 interface flux at t-3/2
-  float Rh2[5], Rh3[5], Rh4[5];  // stage-2 right movers at t-2, t-3, t-4
-  float Lh2[5], Lh3[5];          // stage-2 left movers at t-2, t-3
+  float Rh2[5], Rh3[5];       // stage-2 right movers at t-2, t-3
+  float dR3[5];               // Rh(t-3) - Rh(t-4)
+  float Lh2[5];               // stage-2 left mover at t-2
+  float dL2[5];               // Lh(t-2) - Lh(t-3)
   float F2m[5];               // stage-2 interface flux at t-7/2
 
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = 0.f;
-      Rh2[q] = Rh3[q] = Rh4[q] = Lh2[q] = Lh3[q] = F2m[q] = 0.f;
+      Rh2[q] = Rh3[q] = dR3[q] = Lh2[q] = dL2[q] = F2m[q] = 0.f;
     }
     b1[0] = b1[1] = b1[2] = 0.f;
   }
@@ -120,9 +147,13 @@ struct FluidPipe {
     split_flux(Uh, b1, gamma, Rh, Lh);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      float right = Rh3[q] + 0.5f * vanleer(Rh3[q] - Rh4[q], Rh2[q] - Rh3[q]);
-      float left = Lh2[q] - 0.5f * vanleer(Lh2[q] - Lh3[q], Lh[q] - Lh2[q]);
-      float F2 = right - left;
+      // right mover at t-5/2 from cell t-3, left mover from cell t-2, each
+      // with half its van Leer limited slope
+      const float dR = Rh2[q] - Rh3[q];
+      const float dL = Lh[q] - Lh2[q];
+      const float right = Rh3[q] + vanleer_half(dR3[q], dR);
+      const float left = Lh2[q] - vanleer_half(dL2[q], dL);
+      const float F2 = right - left;
       out[q] = U3[q] - c_full * (F2 - F2m[q]);
       F2m[q] = F2;
       // shift the windows
@@ -131,10 +162,10 @@ struct FluidPipe {
       U1[q] = U[q];
       FR1[q] = FR[q];
       f1m[q] = f1[q];
-      Rh4[q] = Rh3[q];
+      dR3[q] = dR;
       Rh3[q] = Rh2[q];
       Rh2[q] = Rh[q];
-      Lh3[q] = Lh2[q];
+      dL2[q] = dL;
       Lh2[q] = Lh[q];
     }
     b1[0] = b[0];
@@ -157,24 +188,28 @@ struct MagPipe {
   float q1, q2, q3;   // q at t-1, t-2, t-3
   float u1;           // face velocity at t-1
   float g1m;          // first-order flux at t-3/2
-  float h2, h3, h4;   // qh at t-2, t-3, t-4
+  float h2, h3;       // qh at t-2, t-3
+  float d32, d43;     // qh(t-2) - qh(t-3), qh(t-3) - qh(t-4)
   float ub1, ub2;     // ubar at t-3/2, t-5/2
   float fm;           // edge flux at t-7/2
 
   __device__ __forceinline__ void init() {
-    q1 = q2 = q3 = u1 = g1m = h2 = h3 = h4 = ub1 = ub2 = fm = 0.f;
+    q1 = q2 = q3 = u1 = g1m = h2 = h3 = d32 = d43 = ub1 = ub2 = fm = 0.f;
   }
 
   // Returns the edge flux f(t-5/2); writes qnew(t-3) into qnew.
   __device__ __forceinline__ float step(float q, float u, float c_half, float c_full, float &qnew) {
-    float ub = 0.5f * (u1 + u);
-    float g = ub * (ub >= 0.f ? q1 : q);
-    float h = q1 - c_half * (g - g1m);
-    float f;
-    if (ub2 >= 0.f)
-      f = ub2 * (h3 + 0.5f * vanleer(h3 - h4, h2 - h3));
-    else
-      f = ub2 * (h2 - 0.5f * vanleer(h2 - h3, h - h2));
+    const float ub = 0.5f * (u1 + u);
+    const float g = ub * (ub >= 0.f ? q1 : q);
+    const float h = q1 - c_half * (g - g1m);
+    const float d21 = h - h2;
+    // upwind cell t-3 (ubar >= 0) or t-2, plus half its limited slope
+    const bool pos = ub2 >= 0.f;
+    const float base = pos ? h3 : h2;
+    const float sa = pos ? d43 : d32;
+    const float sb = pos ? d32 : d21;
+    const float lim = vanleer_half(sa, sb);
+    const float f = ub2 * (pos ? base + lim : base - lim);
     qnew = q3 - c_full * (f - fm);
     fm = f;
     q3 = q2;
@@ -182,7 +217,8 @@ struct MagPipe {
     q1 = q;
     u1 = u;
     g1m = g;
-    h4 = h3;
+    d43 = d32;
+    d32 = d21;
     h3 = h2;
     h2 = h;
     ub2 = ub1;

@@ -9,8 +9,8 @@
 //
 // No transposes: for the y and z sweeps the 32 lanes of a warp are 32
 // neighbouring pencils along x, so every load and store of a plane is a
-// coalesced 128-byte row; for the x sweep each thread reads its own pencil in
-// aligned 16-byte pieces (4 cells along x per load).
+// coalesced 128-byte row; for the x sweep a warp stages 8 cells of its 32
+// pencils in shared memory, loading whole 32-byte sectors.
 //
 // The sweep writes out of place (in -> out): neighbouring threads read the
 // transverse faces of this thread's pencil.
@@ -35,23 +35,50 @@ struct Axes {
 
 constexpr int kFluidWarps = 4;
 
+// x sweeps: each warp stages 8 cells x 32 pencils of every source field in
+// shared memory (rows padded to 9 floats: conflict-free column reads), loaded
+// as 32-byte row pieces so each DRAM sector is fetched by exactly one load.
+constexpr int kXChunk = 8;
+constexpr int kXPad = 9;
+constexpr int kXTiles = 10;  // rho, m_d, m_t1, m_t2, e, b_d, b_t1, b_t1(+1), b_t2, b_t2(+1)
+constexpr int kXTile = 32 * kXPad;
+
+// Stage positions p0 .. p0+7 (periodic along x, p0 a multiple of 4) of the
+// pencils whose flat base index lane r holds in `rowbase` into tile[r][0..7].
+__device__ __forceinline__ void stage_rows(float* tile, const float* __restrict__ src,
+                                           int rowbase, int p0, int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrapn(p0 + 4 * h, nx)));
+    float* t = tile + r * kXPad + 4 * h;
+    t[0] = v.x;
+    t[1] = v.y;
+    t[2] = v.z;
+    t[3] = v.w;
+  }
+}
+
 template <int D, bool RATE>
-__global__ void __launch_bounds__(32 * kFluidWarps)
+__global__ void __launch_bounds__(32 * kFluidWarps, 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
+  constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
+  __shared__ float xs[(D == 0) ? kFluidWarps * kXTiles * kXTile : 1];
   const int lane = threadIdx.x;
   const int nA = a.box.n[X::A], nO = a.box.n[X::O], nD = a.box.n[D];
   const int pa = blockIdx.x * 32 + lane;
   const int pb = blockIdx.y * kFluidWarps + threadIdx.y;
   const bool active = (pa < nA) && (pb < nO);
   const int ia = min(pa, nA - 1), ib = min(pb, nO - 1);
-  const long long sA = a.box.stride[X::A], sO = a.box.stride[X::O], sD = a.box.stride[D];
-  const long long base = ia * sA + ib * sO;
-  const long long baseA1 = wrapi(ia + 1, nA) * sA + ib * sO;  // pencil +1 along A
-  const long long baseO1 = ia * sA + wrapi(ib + 1, nO) * sO;  // pencil +1 along O
+  const int sA = (int)a.box.stride[X::A], sO = (int)a.box.stride[X::O], sD = (int)a.box.stride[D];
+  const int base = ia * sA + ib * sO;
+  const int baseA1 = wrapi(ia + 1, nA) * sA + ib * sO;  // pencil +1 along A
+  const int baseO1 = ia * sA + wrapi(ib + 1, nO) * sO;  // pencil +1 along O
   // +1 along the local-frame transverse axes
-  const long long baseT1 = (X::T1 == X::A) ? baseA1 : baseO1;
-  const long long baseT2 = (X::T2 == X::A) ? baseA1 : baseO1;
+  const int baseT1 = (X::T1 == X::A) ? baseA1 : baseO1;
+  const int baseT2 = (X::T2 == X::A) ? baseA1 : baseO1;
 
   const float* __restrict__ rho = a.in[RHO];
   const float* __restrict__ md = a.in[MX + D];
@@ -66,6 +93,7 @@ fluid_sweep_kernel(FluidArgs a) {
   float* __restrict__ o_m1 = a.out[MX + X::T1];
   float* __restrict__ o_m2 = a.out[MX + X::T2];
   float* __restrict__ o_en = a.out[EN];
+  float* xw = xs + (D == 0 ? threadIdx.y * kXTiles * kXTile : 0);  // this warp's tiles
 
   const float gamma = a.gamma;
   const float tau = *a.tau;
@@ -75,40 +103,39 @@ fluid_sweep_kernel(FluidArgs a) {
   const int s1 = s0 + a.seg;
   // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
   // warm-up cell so that x chunks start 16-byte aligned)
-  const int nchunk = (a.seg + 7 + 3) / 4;
+  const int nchunk = (a.seg + 7 + CH - 1) / CH;
 
   FluidPipe pipe;
   pipe.init();
-  float bc2[3] = {0.f, 0.f, 0.f}, bc3[3] = {0.f, 0.f, 0.f};  // b_c at t-2, t-3 (RATE only)
+  float bc2[3] = {0.f, 0.f, 0.f}, bc3[3] = {0.f, 0.f, 0.f};  // b_c at t-1, t-2 (RATE only)
   float rmax = 0.f;
 
   for (int c = 0; c < nchunk; c++) {
-    const int p0 = s0 - 4 + 4 * c;        // first position of this chunk
-    const int pw = wrapi(p0, nD);          // its periodic image (multiple of 4)
-    float U[4][5], B[4][3], bdn[5], t1n[4], t2n[4];
-    if (D == 0) {
-      // 16-byte loads along x: 4 consecutive cells of this pencil
-      const long long cx = base + pw;
-      float4 v;
-#define LD4(dst, ptr, off)                                   \
-  v = __ldg(reinterpret_cast<const float4*>((ptr) + (off))); \
-  dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
-      float t0[4], t1[4], t2[4], t3[4], t4[4], tb1[4], tb2[4];
-      LD4(t0, rho, cx) LD4(t1, md, cx) LD4(t2, m1, cx) LD4(t3, m2, cx) LD4(t4, en, cx)
-      LD4(bdn, bd, cx) LD4(tb1, b1, cx) LD4(tb2, b2, cx)
-      LD4(t1n, b1, baseT1 + pw) LD4(t2n, b2, baseT2 + pw)
-#undef LD4
-      bdn[4] = __ldg(bd + base + wrapi(p0 + 4, nD));
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        U[j][0] = t0[j]; U[j][1] = t1[j]; U[j][2] = t2[j]; U[j][3] = t3[j]; U[j][4] = t4[j];
-        B[j][1] = tb1[j]; B[j][2] = tb2[j];
-      }
+    const int p0 = s0 - 4 + CH * c;  // first position of this chunk
+    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
+    float U[(D == 0) ? 1 : CH][5], B[(D == 0) ? 1 : CH][3];
+    const float* row = xw + lane * kXPad;
+    float bd_next = 0.f;
+    if constexpr (D == 0) {
+      __syncwarp();
+      stage_rows(xw + 0 * kXTile, rho, base, p0, nD, lane);
+      stage_rows(xw + 1 * kXTile, md, base, p0, nD, lane);
+      stage_rows(xw + 2 * kXTile, m1, base, p0, nD, lane);
+      stage_rows(xw + 3 * kXTile, m2, base, p0, nD, lane);
+      stage_rows(xw + 4 * kXTile, en, base, p0, nD, lane);
+      stage_rows(xw + 5 * kXTile, bd, base, p0, nD, lane);
+      stage_rows(xw + 6 * kXTile, b1, base, p0, nD, lane);
+      stage_rows(xw + 7 * kXTile, b1, baseT1, p0, nD, lane);
+      stage_rows(xw + 8 * kXTile, b2, base, p0, nD, lane);
+      stage_rows(xw + 9 * kXTile, b2, baseT2, p0, nD, lane);
+      bd_next = __ldg(bd + base + wrapn(p0 + CH, nD));  // high face of the last cell
+      __syncwarp();
     } else {
       // one coalesced row per plane
+      float bdn[CH + 1], t1n[CH], t2n[CH];
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const long long off = (long long)wrapi(p0 + j, nD) * sD;
+      for (int j = 0; j < CH; j++) {
+        const int off = wrapn(p0 + j, nD) * sD;
         U[j][0] = __ldg(rho + base + off);
         U[j][1] = __ldg(md + base + off);
         U[j][2] = __ldg(m1 + base + off);
@@ -120,24 +147,39 @@ fluid_sweep_kernel(FluidArgs a) {
         t1n[j] = __ldg(b1 + baseT1 + off);
         t2n[j] = __ldg(b2 + baseT2 + off);
       }
-      bdn[4] = __ldg(bd + base + (long long)wrapi(p0 + 4, nD) * sD);
+      bdn[CH] = __ldg(bd + base + wrapn(p0 + CH, nD) * sD);
+#pragma unroll
+      for (int j = 0; j < CH; j++) {
+        // cell-centred field: mean of the low and high face of the cell
+        B[j][0] = 0.5f * (bdn[j] + bdn[j + 1]);
+        B[j][1] = 0.5f * (B[j][1] + t1n[j]);
+        B[j][2] = 0.5f * (B[j][2] + t2n[j]);
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      // cell-centred field: mean of the low and high face of the cell
-      B[j][0] = 0.5f * (bdn[j] + bdn[j + 1]);
-      B[j][1] = 0.5f * (B[j][1] + t1n[j]);
-      B[j][2] = 0.5f * (B[j][2] + t2n[j]);
-    }
+    for (int j = 0; j < CH; j++) {
+      float o[5], Uj[5], Bj[3];
+      if constexpr (D == 0) {
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      float o[5];
+        for (int q = 0; q < 5; q++) Uj[q] = row[q * kXTile + j];
+        const float hi = (j + 1 < CH) ? row[5 * kXTile + j + 1] : bd_next;
+        // cell-centred field: mean of the low and high face of the cell
+        Bj[0] = 0.5f * (row[5 * kXTile + j] + hi);
+        Bj[1] = 0.5f * (row[6 * kXTile + j] + row[7 * kXTile + j]);
+        Bj[2] = 0.5f * (row[8 * kXTile + j] + row[9 * kXTile + j]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; q++) Uj[q] = U[j][q];
+        Bj[0] = B[j][0];
+        Bj[1] = B[j][1];
+        Bj[2] = B[j][2];
+      }
       const float bprev0 = pipe.b1[0], bprev1 = pipe.b1[1], bprev2 = pipe.b1[2];  // b_c(t-1)
-      pipe.step(U[j], B[j], gamma, c_half, c_full, o);
+      pipe.step(Uj, Bj, gamma, c_half, c_full, o);
       const int t = p0 + j;
       const int po = t - 3;  // position of the finished cell
       if (active && po >= s0 && po < s1) {
-        const long long cell = base + (long long)wrapi(po, nD) * sD;
+        const int cell = base + wrapn(po, nD) * sD;
         o_rho[cell] = o[0];
         o_md[cell] = o[1];
         o_m1[cell] = o[2];

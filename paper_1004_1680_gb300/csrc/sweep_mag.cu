@@ -9,6 +9,8 @@
 // flux lives on the edge (D: i+1/2, t: low face of pencil P); the EMF pieces
 // are applied directly and never written to memory.
 //
+// Velocities v_D = m_D/rho are formed once per loaded value.
+//
 // A block owns a tile of 32 (lane axis A) x kMagWarps (row axis O) pencils and
 // marches all of them together along D.  Two extra warps march the halo
 // pencils whose flux the tile needs: row O+kMagWarps (its f along O) and
@@ -26,12 +28,57 @@ struct MagAxes {
   static constexpr int T1 = (D + 1) % 3;
 };
 
+// x sweeps stage 8 cells of each warp's 32 pencils in shared memory (rows of
+// 9 floats, 32-byte sector loads): v_x = m_x/rho at the pencil and at its -A
+// and -O neighbours, and the three face fields.
+constexpr int kMXChunk = 8;
+constexpr int kMXPad = 9;
+constexpr int kMXTiles = 6;
+constexpr int kMXTile = 32 * kMXPad;
+constexpr size_t kMagXSmem = sizeof(float) * (kMagWarps + 2) * kMXTiles * kMXTile;
+
+__device__ __forceinline__ void stage_rows_m(float* tile, const float* __restrict__ src,
+                                             int rowbase, int p0, int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrapn(p0 + 4 * h, nx)));
+    float* t = tile + r * kMXPad + 4 * h;
+    t[0] = v.x;
+    t[1] = v.y;
+    t[2] = v.z;
+    t[3] = v.w;
+  }
+}
+
+// velocity rows: v = m / rho
+__device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__ rho,
+                                          const float* __restrict__ m, int rowbase, int p0,
+                                          int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const int off = wrapn(p0 + 4 * h, nx);
+    const float4 rr = __ldg(reinterpret_cast<const float4*>(rho + rb + off));
+    const float4 mm = __ldg(reinterpret_cast<const float4*>(m + rb + off));
+    float* t = tile + r * kMXPad + 4 * h;
+    t[0] = __fdividef(mm.x, rr.x);
+    t[1] = __fdividef(mm.y, rr.y);
+    t[2] = __fdividef(mm.z, rr.z);
+    t[3] = __fdividef(mm.w, rr.w);
+  }
+}
+
 template <int D>
-__global__ void __launch_bounds__(32 * (kMagWarps + 2))
+__global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_kernel(MagArgs a) {
   using X = MagAxes<D>;
-  __shared__ float fA_s[4][kMagWarps][33];       // flux of b_A, column 32 = halo column
-  __shared__ float fO_s[4][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
+  constexpr int CH = (D == 0) ? kMXChunk : 4;
+  __shared__ float fA_s[CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
+  __shared__ float fO_s[CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
+  extern __shared__ float xs_dyn[];               // x sweeps only: staged rows
 
   const int lane = threadIdx.x, w = threadIdx.y;
   const int nA = a.box.n[X::A], nO = a.box.n[X::O], nD = a.box.n[D];
@@ -59,10 +106,10 @@ mag_sweep_kernel(MagArgs a) {
     row = min(lane, kMagWarps - 1);
     col = cntA;
   }
-  const long long sA = a.box.stride[X::A], sO = a.box.stride[X::O], sD = a.box.stride[D];
-  const long long base = pa * sA + pb * sO;
-  const long long baseAm = wrapi(pa - 1, nA) * sA + pb * sO;  // pencil -1 along A
-  const long long baseOm = pa * sA + wrapi(pb - 1, nO) * sO;  // pencil -1 along O
+  const int sA = (int)a.box.stride[X::A], sO = (int)a.box.stride[X::O], sD = (int)a.box.stride[D];
+  const int base = pa * sA + pb * sO;
+  const int baseAm = wrapi(pa - 1, nA) * sA + pb * sO;  // pencil -1 along A
+  const int baseOm = pa * sA + wrapi(pb - 1, nO) * sO;  // pencil -1 along O
 
   const float* __restrict__ rho = a.in[RHO];
   const float* __restrict__ md = a.in[MX + D];
@@ -72,6 +119,7 @@ mag_sweep_kernel(MagArgs a) {
   float* __restrict__ o_bA = a.out[X::A];
   float* __restrict__ o_bO = a.out[X::O];
   float* __restrict__ o_bD = a.out[D];
+  float* xw = xs_dyn + (D == 0 ? w * kMXTiles * kMXTile : 0);
 
   const float tau = *a.tau;
   const float c_full = tau * (float)nD;        // tau / h_D
@@ -82,7 +130,7 @@ mag_sweep_kernel(MagArgs a) {
   const int s1 = s0 + a.seg;
   // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
   // warm-up cell so that x chunks start 16-byte aligned)
-  const int nchunk = (a.seg + 7 + 3) / 4;
+  const int nchunk = (a.seg + 7 + CH - 1) / CH;
   // slots read by the tile: fO rows 0..cntO (row cntO = halo row), fA columns
   // 0..cntA (column cntA = halo column); idle lanes of a partial tile must not
   // overwrite a halo slot
@@ -96,52 +144,61 @@ mag_sweep_kernel(MagArgs a) {
   float bD1 = 0.f, bD2 = 0.f;  // raw b_D at t-1, t-2
 
   for (int c = 0; c < nchunk; c++) {
-    const int p0 = s0 - 4 + 4 * c;
-    const int pw = wrapi(p0, nD);
-    float r[4], m[4], rA[4], mA[4], rO[4], mO[4], qA[4], qO[4], qD[4];
-    if (D == 0) {
-      float4 v;
-#define LD4(dst, ptr, off)                                   \
-  v = __ldg(reinterpret_cast<const float4*>((ptr) + (off))); \
-  dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
-      LD4(r, rho, base + pw) LD4(m, md, base + pw)
-      LD4(rA, rho, baseAm + pw) LD4(mA, md, baseAm + pw)
-      LD4(rO, rho, baseOm + pw) LD4(mO, md, baseOm + pw)
-      LD4(qA, bA, base + pw) LD4(qO, bO, base + pw) LD4(qD, bD, base + pw)
-#undef LD4
+    const int p0 = s0 - 4 + CH * c;
+    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
+    constexpr int R = (D == 0) ? 1 : CH;
+    float v[R], vA[R], vO[R], qA[R], qO[R], qD[R];
+    const float* rw = xw + lane * kMXPad;
+    if constexpr (D == 0) {
+      __syncwarp();
+      stage_vel(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
+      stage_vel(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
+      stage_vel(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
+      stage_rows_m(xw + 3 * kMXTile, bA, base, p0, nD, lane);
+      stage_rows_m(xw + 4 * kMXTile, bO, base, p0, nD, lane);
+      stage_rows_m(xw + 5 * kMXTile, bD, base, p0, nD, lane);
+      __syncwarp();
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const long long off = (long long)wrapi(p0 + j, nD) * sD;
-        r[j] = __ldg(rho + base + off);
-        m[j] = __ldg(md + base + off);
-        rA[j] = __ldg(rho + baseAm + off);
-        mA[j] = __ldg(md + baseAm + off);
-        rO[j] = __ldg(rho + baseOm + off);
-        mO[j] = __ldg(md + baseOm + off);
+      for (int j = 0; j < CH; j++) {
+        const int off = wrapn(p0 + j, nD) * sD;
+        v[j] = __fdividef(__ldg(md + base + off), __ldg(rho + base + off));
+        vA[j] = __fdividef(__ldg(md + baseAm + off), __ldg(rho + baseAm + off));
+        vO[j] = __fdividef(__ldg(md + baseOm + off), __ldg(rho + baseOm + off));
         qA[j] = __ldg(bA + base + off);
         qO[j] = __ldg(bO + base + off);
         qD[j] = __ldg(bD + base + off);
       }
     }
-    float bDold[4];  // raw b_D at the face each position's constraint updates
+    float bDold[CH];  // raw b_D at the face each position's constraint updates
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const float v = __fdividef(m[j], r[j]);
-      const float uA = 0.5f * (v + __fdividef(mA[j], rA[j]));  // v_D on the b_A face
-      const float uO = 0.5f * (v + __fdividef(mO[j], rO[j]));  // v_D on the b_O face
-      float nA_new, nO_new;
-      const float fa = pA.step(qA[j], uA, c_half, c_full, nA_new);
-      const float fo = pO.step(qO[j], uO, c_half, c_full, nO_new);
+    for (int j = 0; j < CH; j++) {
+      float vj, vAj, vOj, qAj, qOj, qDj;
+      if constexpr (D == 0) {
+        vj = rw[0 * kMXTile + j];
+        vAj = rw[1 * kMXTile + j];
+        vOj = rw[2 * kMXTile + j];
+        qAj = rw[3 * kMXTile + j];
+        qOj = rw[4 * kMXTile + j];
+        qDj = rw[5 * kMXTile + j];
+      } else {
+        vj = v[j]; vAj = vA[j]; vOj = vO[j]; qAj = qA[j]; qOj = qO[j]; qDj = qD[j];
+      }
+      const float uA = 0.5f * (vj + vAj);  // v_D on the b_A face
+      const float uO = 0.5f * (vj + vOj);  // v_D on the b_O face
+      // the halo row needs only the flux along O, the halo column only along A
+      float nA_new = 0.f, nO_new = 0.f, fa = 0.f, fo = 0.f;
+      if (w != kMagWarps) fa = pA.step(qAj, uA, c_half, c_full, nA_new);
+      if (w != kMagWarps + 1) fo = pO.step(qOj, uO, c_half, c_full, nO_new);
       if (write_row) fO_s[j][row][col] = fo;
       if (write_col) fA_s[j][row][col] = fa;
       bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
       bD2 = bD1;
-      bD1 = qD[j];
+      bD1 = qDj;
       const int t = p0 + j;
       const int po = t - 3;
       if (interior && po >= s0 && po < s1) {
-        const long long cell = base + (long long)wrapi(po, nD) * sD;
+        const int cell = base + wrapn(po, nD) * sD;
         o_bA[cell] = nA_new;
         o_bO[cell] = nO_new;
       }
@@ -149,7 +206,7 @@ mag_sweep_kernel(MagArgs a) {
     __syncthreads();
     if (interior) {
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
+      for (int j = 0; j < CH; j++) {
         const int t = p0 + j;
         const int pf = t - 2;  // b_D face updated by the edge flux f(t-5/2)
         if (pf >= s0 && pf < s1) {
@@ -163,7 +220,7 @@ mag_sweep_kernel(MagArgs a) {
             b += kO * (fo1 - fo0);
             b += kA * (fa1 - fa0);
           }
-          o_bD[base + (long long)wrapi(pf, nD) * sD] = b;
+          o_bD[base + wrapn(pf, nD) * sD] = b;
         }
       }
     }
@@ -179,8 +236,13 @@ cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s) {
   const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
   dim3 block(32, kMagWarps + 2);
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
+  if (axis == 0) {  // the x sweep stages rows in more than 48 KB of shared memory
+    cudaError_t e = cudaFuncSetAttribute(mag_sweep_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMagXSmem);
+    if (e != cudaSuccess) return e;
+  }
   switch (axis) {
-    case 0: mag_sweep_kernel<0><<<grid, block, 0, s>>>(a); break;
+    case 0: mag_sweep_kernel<0><<<grid, block, kMagXSmem, s>>>(a); break;
     case 1: mag_sweep_kernel<1><<<grid, block, 0, s>>>(a); break;
     default: mag_sweep_kernel<2><<<grid, block, 0, s>>>(a); break;
   }

@@ -26,10 +26,12 @@ def field_scales(s0: np.ndarray, gamma: float = G) -> np.ndarray:
 
 
 def rel_err(gpu: np.ndarray, orc: np.ndarray, S: np.ndarray) -> np.ndarray:
-    """err_f = max |gpu - oracle| / max(max |oracle_f|, S_f), per field."""
+    """err_f = max |gpu - oracle| / max(max |oracle_f|, S_f), per field (an
+    identically zero field, e.g. b in a hydrodynamic tube, is compared
+    absolutely)."""
     out = np.zeros(8)
     for q in range(8):
-        den = max(float(np.max(np.abs(orc[q]))), float(S[q]))
+        den = max(float(np.max(np.abs(orc[q]))), float(S[q])) or 1.0
         out[q] = float(np.max(np.abs(gpu[q].astype(np.float64) - orc[q]))) / den
     return out
 
@@ -38,7 +40,7 @@ def l1_rel(gpu: np.ndarray, orc: np.ndarray, S: np.ndarray) -> np.ndarray:
     """Mean absolute difference over the scale, per field."""
     out = np.zeros(8)
     for q in range(8):
-        den = max(float(np.mean(np.abs(orc[q]))), float(S[q]))
+        den = max(float(np.mean(np.abs(orc[q]))), float(S[q])) or 1.0
         out[q] = float(np.mean(np.abs(gpu[q].astype(np.float64) - orc[q]))) / den
     return out
 
