@@ -110,6 +110,15 @@ int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
  * segmentation, so results are bitwise independent of it. */
 int mhd_set_segments(mhd_t *m, int seg_x, int seg_y, int seg_z);
 
+/* How x sweeps read the state: 1 = directly (a warp stages 8-cell row pieces
+ * of its 32 pencils in shared memory), 2 = through a copy with x and y
+ * exchanged (all 8 fields transposed once before a group of x sweeps and once
+ * after; consecutive steps share one group, so a run of steps costs two
+ * transposes per step), 0 = automatic (2 once the state exceeds 64 MiB).
+ * Both paths compute the same update; results differ by FP32 rounding of
+ * sums taken in another order. */
+int mhd_set_xpath(mhd_t *m, int mode);
+
 /* FP64 diagnostics of the current state, computed on the device with
  * compensated (Neumaier) sums in a fixed order, so repeated calls on the same
  * state give bitwise identical results:
@@ -129,7 +138,8 @@ int mhd_diagnostics(mhd_t *m, double out[10]);
 #define MHD_K_MAG_Y 4
 #define MHD_K_MAG_Z 5
 #define MHD_K_CONTROL 6 /* step control, CFL reduction, diagnostics */
-#define MHD_K_CLASSES 7
+#define MHD_K_TRANSPOSE 7 /* x <-> y exchange of the state (x sweep path 2) */
+#define MHD_K_CLASSES 8
 
 /* Per-kernel device timing (tracing).  With capacity > 0, every later kernel
  * launch of this box is bracketed by a pair of CUDA events on its stream,

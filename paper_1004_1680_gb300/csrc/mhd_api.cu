@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "mhd.h"
@@ -49,9 +50,13 @@ struct mhd_s {
   double gamma;
   long long N;
   mhd::Box box;
+  mhd::Box tbox;       // the same box with x and y exchanged
   float* arena = nullptr;
-  float* buf[2][8];
-  int cur[8];
+  float* cur[8];        // current copy of each field (in the current layout)
+  float* spare[8];      // the other copy, written by the next kernel
+  int layout = 0;       // 0: x fastest; 1: x and y exchanged (for x sweeps)
+  int xpath = 0;        // x sweeps: 1 direct, 2 through the exchanged layout
+  int xpath_req = 0;    // requested by mhd_set_xpath (0 = automatic)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
@@ -64,6 +69,11 @@ struct mhd_s {
 };
 
 namespace {
+
+// x sweeps go through the exchanged layout once the state no longer fits in
+// L2 (direct x sweeps read 32 different lines per warp and position, which
+// only L2 can absorb).
+int auto_xpath(const mhd_s* m) { return m->N * 32LL > (64LL << 20) ? 2 : 1; }
 
 // Segment length along each axis: whole pencils when they already give the
 // GPU enough threads, otherwise split pencils (each split re-reads 8 cells of
@@ -100,42 +110,100 @@ void drop_events(mhd_s* m) {
 }
 
 void field_ptrs(const mhd_s* m, const float* out[8]) {
-  for (int q = 0; q < 8; q++) out[q] = m->buf[m->cur[q]][q];
+  for (int q = 0; q < 8; q++) out[q] = m->cur[q];
+}
+
+// Exchange x and y of all fields (out of place).  In the exchanged layout the
+// field slots are relabelled so that slot 1 / 5 hold the momentum / face field
+// along the new fast axis (physical y) and slots 2 / 6 those along physical x.
+int exchange_xy(mhd_s* m) {
+  mhd::TransposeArgs a;
+  const mhd::Box& b = m->layout == 0 ? m->box : m->tbox;
+  for (int q = 0; q < 8; q++) {
+    a.in[q] = m->cur[q];
+    a.out[q] = m->spare[q];
+  }
+  a.n[0] = b.n[0];
+  a.n[1] = b.n[1];
+  a.n[2] = b.n[2];
+  int rc = traced(m, MHD_K_TRANSPOSE, [&] {
+    CK(mhd::launch_transpose01(a, m->stream));
+    return MHD_OK;
+  });
+  if (rc) return rc;
+  static const int relabel[8] = {0, 2, 1, 3, 4, 6, 5, 7};
+  float* nc[8];
+  float* ns[8];
+  for (int q = 0; q < 8; q++) {
+    nc[relabel[q]] = m->spare[q];
+    ns[relabel[q]] = m->cur[q];
+  }
+  for (int q = 0; q < 8; q++) {
+    m->cur[q] = nc[q];
+    m->spare[q] = ns[q];
+  }
+  m->layout ^= 1;
+  return MHD_OK;
+}
+
+int ensure_layout(mhd_s* m, int layout) { return m->layout == layout ? MHD_OK : exchange_xy(m); }
+
+// Frame of a sweep along physical axis d: the layout it runs in, the box as
+// the kernels see it and the kernel axis.  y sweeps need x fastest; x sweeps
+// run in the exchanged layout when xpath == 2 (as kernel axis 1); z sweeps
+// run in whichever layout is current.
+int sweep_frame(mhd_s* m, int d, const mhd::Box** box, int* kaxis) {
+  int want = m->layout;
+  if (d == 0) want = (m->xpath == 2) ? 1 : 0;
+  if (d == 1) want = 0;
+  int rc = ensure_layout(m, want);
+  if (rc) return rc;
+  *box = m->layout ? &m->tbox : &m->box;
+  *kaxis = (m->layout && d < 2) ? 1 - d : d;
+  return MHD_OK;
 }
 
 int fluid(mhd_s* m, int d, bool rate) {
+  const mhd::Box* box;
+  int ka;
+  int rc = sweep_frame(m, d, &box, &ka);
+  if (rc) return rc;
   mhd::FluidArgs a;
   for (int q = 0; q < 8; q++) {
-    a.in[q] = m->buf[m->cur[q]][q];
-    a.out[q] = m->buf[1 - m->cur[q]][q];
+    a.in[q] = m->cur[q];
+    a.out[q] = m->spare[q];
   }
-  a.box = m->box;
+  a.box = *box;
   a.gamma = (float)m->gamma;
   a.tau = &m->sc->tau;
   a.rate = rate ? &m->sc->rate[1 - m->rcur] : nullptr;
   a.seg = m->seg[d];
-  int rc = traced(m, MHD_K_FLUID_X + d, [&] {
-    CK(mhd::launch_fluid(d, rate, a, m->stream));
+  rc = traced(m, MHD_K_FLUID_X + d, [&] {
+    CK(mhd::launch_fluid(ka, rate, a, m->stream));
     return MHD_OK;
   });
   if (rc) return rc;
-  for (int q = 0; q < 5; q++) m->cur[q] ^= 1;
+  for (int q = 0; q < 5; q++) std::swap(m->cur[q], m->spare[q]);
   return MHD_OK;
 }
 
 int magnetic(mhd_s* m, int d) {
+  const mhd::Box* box;
+  int ka;
+  int rc = sweep_frame(m, d, &box, &ka);
+  if (rc) return rc;
   mhd::MagArgs a;
-  for (int q = 0; q < 8; q++) a.in[q] = m->buf[m->cur[q]][q];
-  for (int q = 0; q < 3; q++) a.out[q] = m->buf[1 - m->cur[5 + q]][5 + q];
-  a.box = m->box;
+  for (int q = 0; q < 8; q++) a.in[q] = m->cur[q];
+  for (int q = 0; q < 3; q++) a.out[q] = m->spare[5 + q];
+  a.box = *box;
   a.tau = &m->sc->tau;
   a.seg = m->seg[d];
-  int rc = traced(m, MHD_K_MAG_X + d, [&] {
-    CK(mhd::launch_mag(d, a, m->stream));
+  rc = traced(m, MHD_K_MAG_X + d, [&] {
+    CK(mhd::launch_mag(ka, a, m->stream));
     return MHD_OK;
   });
   if (rc) return rc;
-  for (int q = 5; q < 8; q++) m->cur[q] ^= 1;
+  for (int q = 5; q < 8; q++) std::swap(m->cur[q], m->spare[q]);
   return MHD_OK;
 }
 
@@ -204,9 +272,17 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
     delete m;
     return nullptr;
   }
-  for (int c = 0; c < 2; c++)
-    for (int q = 0; q < 8; q++) m->buf[c][q] = m->arena + (size_t)N * (8 * c + q);
-  for (int q = 0; q < 8; q++) m->cur[q] = 0;
+  for (int q = 0; q < 8; q++) {
+    m->cur[q] = m->arena + (size_t)N * q;
+    m->spare[q] = m->arena + (size_t)N * (8 + q);
+  }
+  m->tbox.n[0] = ny;
+  m->tbox.n[1] = nx;
+  m->tbox.n[2] = nz;
+  m->tbox.stride[0] = 1;
+  m->tbox.stride[1] = ny;
+  m->tbox.stride[2] = (long long)nx * ny;
+  m->xpath = auto_xpath(m);
   const int nblk = mhd::diag_blocks(m->box);
   if ((e = cudaMalloc(&m->sc, sizeof(Scalars))) != cudaSuccess ||
       (e = cudaMalloc(&m->diag_partial, sizeof(double) * mhd::kDiagSlots * nblk)) != cudaSuccess ||
@@ -243,11 +319,16 @@ int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   const size_t bytes = sizeof(float) * (size_t)m->N;
-  for (int q = 0; q < 8; q++) {
-    m->cur[q] = 0;
-    CK(cudaMemcpyAsync(m->buf[0][q], f[q], bytes,
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+  if (m->layout) {  // back to the plain layout (the old state is overwritten)
+    std::swap(m->cur[1], m->cur[2]);
+    std::swap(m->spare[1], m->spare[2]);
+    std::swap(m->cur[5], m->cur[6]);
+    std::swap(m->spare[5], m->spare[6]);
+    m->layout = 0;
   }
+  for (int q = 0; q < 8; q++)
+    CK(cudaMemcpyAsync(m->cur[q], f[q], bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
   CK(cudaMemsetAsync(m->sc, 0, sizeof(Scalars), m->stream));
   m->rcur = 0;
   const float* cf[8];
@@ -261,8 +342,9 @@ int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   const size_t bytes = sizeof(float) * (size_t)m->N;
+  if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
   for (int q = 0; q < 8; q++)
-    CK(cudaMemcpyAsync(f[q], m->buf[m->cur[q]][q], bytes,
+    CK(cudaMemcpyAsync(f[q], m->cur[q], bytes,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
   return MHD_OK;
@@ -292,7 +374,8 @@ int mhd_step(mhd_t* m, double dt_full) {
                                 &m->sc->time, -1.0, 0.5 * dt_full, m->stream));
     return MHD_OK;
   });
-  return rc ? rc : full_step(m);
+  if (!rc) rc = full_step(m);
+  return rc ? rc : ensure_layout(m, 0);
 }
 
 int mhd_run(mhd_t* m, int nsteps, double cfl) {
@@ -307,7 +390,7 @@ int mhd_run(mhd_t* m, int nsteps, double cfl) {
     if (!rc) rc = full_step(m);
     if (rc) return rc;
   }
-  return MHD_OK;
+  return ensure_layout(m, 0);  // consecutive steps share their x-sweep layout
 }
 
 int mhd_time(const mhd_t* m, double* t) {
@@ -325,6 +408,7 @@ int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
   // rate is recomputed for the new state
   CK(mhd::launch_set_tau(&m->sc->tau, tau, m->stream));
   int rc = kind == 0 ? fluid(m, axis, false) : magnetic(m, axis);
+  if (!rc) rc = ensure_layout(m, 0);
   if (rc) return rc;
   CK(cudaMemsetAsync(&m->sc->rate[m->rcur], 0, sizeof(unsigned), m->stream));
   const float* cf[8];
@@ -340,6 +424,15 @@ int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {
     if (seg[d] != 0 && (seg[d] < 4 || seg[d] % 4 != 0 || m->n[d] % seg[d] != 0))
       return fail(MHD_E_ARG, "segment length must be a multiple of 4 dividing n_d");
   for (int d = 0; d < 3; d++) m->seg[d] = seg[d] ? seg[d] : choose_seg(m, d);
+  return MHD_OK;
+}
+
+int mhd_set_xpath(mhd_t* m, int mode) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (mode < 0 || mode > 2) return fail(MHD_E_ARG, "x path mode must be 0, 1 or 2");
+  if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
+  m->xpath_req = mode;
+  m->xpath = mode ? mode : auto_xpath(m);
   return MHD_OK;
 }
 

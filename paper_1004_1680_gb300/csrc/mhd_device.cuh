@@ -22,14 +22,17 @@ __host__ __device__ inline int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Periodic image of a position within a few cells of [0, n): two compares
-// instead of an integer division when n is large enough.
-__device__ __forceinline__ int wrapn(int i, int n) {
-  if (n >= 16) {
+// Periodic image of a position within one period of [0, n) (SMALL = false,
+// valid for n >= 16) or anywhere (SMALL = true).  Branch-free, so the loads
+// of a whole chunk can be issued before the first one is used.
+template <bool SMALL>
+__device__ __forceinline__ int wrap_near(int i, int n) {
+  if constexpr (SMALL) {
+    return wrapi(i, n);
+  } else {
     i = i < 0 ? i + n : i;
     return i >= n ? i - n : i;
   }
-  return wrapi(i, n);
 }
 
 // Hardware approximate reciprocal and square root (PTX rcp.approx / sqrt.approx,

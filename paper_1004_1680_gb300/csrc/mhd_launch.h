@@ -27,7 +27,14 @@ struct MagArgs {
   int seg;
 };
 
+struct TransposeArgs {
+  const float* in[8];
+  float* out[8];
+  int n[3];  // input extents, fastest first; the output has n[1] fastest
+};
+
 // launchers (return cudaGetLastError of the launch)
+cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);
 cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
 cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s);
 cudaError_t launch_cfl_rate(const float* const f[8], const Box& box, float gamma, unsigned* rate,

@@ -45,13 +45,14 @@ constexpr int kXTile = 32 * kXPad;
 
 // Stage positions p0 .. p0+7 (periodic along x, p0 a multiple of 4) of the
 // pencils whose flat base index lane r holds in `rowbase` into tile[r][0..7].
+template <bool SMALL>
 __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict__ src,
                                            int rowbase, int p0, int nx, int lane) {
 #pragma unroll
   for (int k = 0; k < 2; k++) {
     const int r = 16 * k + (lane >> 1), h = lane & 1;
     const int rb = __shfl_sync(0xffffffffu, rowbase, r);
-    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrapn(p0 + 4 * h, nx)));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrap_near<SMALL>(p0 + 4 * h, nx)));
     float* t = tile + r * kXPad + 4 * h;
     t[0] = v.x;
     t[1] = v.y;
@@ -60,7 +61,7 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
   }
 }
 
-template <int D, bool RATE>
+template <int D, bool RATE, bool SMALL>
 __global__ void __launch_bounds__(32 * kFluidWarps, 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
@@ -118,24 +119,24 @@ fluid_sweep_kernel(FluidArgs a) {
     float bd_next = 0.f;
     if constexpr (D == 0) {
       __syncwarp();
-      stage_rows(xw + 0 * kXTile, rho, base, p0, nD, lane);
-      stage_rows(xw + 1 * kXTile, md, base, p0, nD, lane);
-      stage_rows(xw + 2 * kXTile, m1, base, p0, nD, lane);
-      stage_rows(xw + 3 * kXTile, m2, base, p0, nD, lane);
-      stage_rows(xw + 4 * kXTile, en, base, p0, nD, lane);
-      stage_rows(xw + 5 * kXTile, bd, base, p0, nD, lane);
-      stage_rows(xw + 6 * kXTile, b1, base, p0, nD, lane);
-      stage_rows(xw + 7 * kXTile, b1, baseT1, p0, nD, lane);
-      stage_rows(xw + 8 * kXTile, b2, base, p0, nD, lane);
-      stage_rows(xw + 9 * kXTile, b2, baseT2, p0, nD, lane);
-      bd_next = __ldg(bd + base + wrapn(p0 + CH, nD));  // high face of the last cell
+      stage_rows<SMALL>(xw + 0 * kXTile, rho, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 1 * kXTile, md, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 2 * kXTile, m1, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 3 * kXTile, m2, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 4 * kXTile, en, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 5 * kXTile, bd, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 6 * kXTile, b1, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 7 * kXTile, b1, baseT1, p0, nD, lane);
+      stage_rows<SMALL>(xw + 8 * kXTile, b2, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 9 * kXTile, b2, baseT2, p0, nD, lane);
+      bd_next = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD));  // high face of the last cell
       __syncwarp();
     } else {
       // one coalesced row per plane
       float bdn[CH + 1], t1n[CH], t2n[CH];
 #pragma unroll
       for (int j = 0; j < CH; j++) {
-        const int off = wrapn(p0 + j, nD) * sD;
+        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
         U[j][0] = __ldg(rho + base + off);
         U[j][1] = __ldg(md + base + off);
         U[j][2] = __ldg(m1 + base + off);
@@ -147,7 +148,7 @@ fluid_sweep_kernel(FluidArgs a) {
         t1n[j] = __ldg(b1 + baseT1 + off);
         t2n[j] = __ldg(b2 + baseT2 + off);
       }
-      bdn[CH] = __ldg(bd + base + wrapn(p0 + CH, nD) * sD);
+      bdn[CH] = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD) * sD);
 #pragma unroll
       for (int j = 0; j < CH; j++) {
         // cell-centred field: mean of the low and high face of the cell
@@ -179,7 +180,7 @@ fluid_sweep_kernel(FluidArgs a) {
       const int t = p0 + j;
       const int po = t - 3;  // position of the finished cell
       if (active && po >= s0 && po < s1) {
-        const int cell = base + wrapn(po, nD) * sD;
+        const int cell = base + po * sD;  // po is inside [s0, s1)
         o_rho[cell] = o[0];
         o_md[cell] = o[1];
         o_m1[cell] = o[2];
@@ -213,14 +214,15 @@ cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s
   dim3 block(32, kFluidWarps);
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kFluidWarps - 1) / kFluidWarps,
             a.box.n[axis] / a.seg);
-  switch (axis * 2 + (rate ? 1 : 0)) {
-    case 0: fluid_sweep_kernel<0, false><<<grid, block, 0, s>>>(a); break;
-    case 1: fluid_sweep_kernel<0, true><<<grid, block, 0, s>>>(a); break;
-    case 2: fluid_sweep_kernel<1, false><<<grid, block, 0, s>>>(a); break;
-    case 3: fluid_sweep_kernel<1, true><<<grid, block, 0, s>>>(a); break;
-    case 4: fluid_sweep_kernel<2, false><<<grid, block, 0, s>>>(a); break;
-    default: fluid_sweep_kernel<2, true><<<grid, block, 0, s>>>(a); break;
+  const bool small = a.box.n[axis] < 16;
+#define FLUID_CASE(DD, RR)                                                        \
+  if (axis == DD && rate == RR) {                                                 \
+    if (small) fluid_sweep_kernel<DD, RR, true><<<grid, block, 0, s>>>(a);        \
+    else fluid_sweep_kernel<DD, RR, false><<<grid, block, 0, s>>>(a);             \
   }
+  FLUID_CASE(0, false) FLUID_CASE(0, true) FLUID_CASE(1, false) FLUID_CASE(1, true)
+  FLUID_CASE(2, false) FLUID_CASE(2, true)
+#undef FLUID_CASE
   return cudaGetLastError();
 }
 

@@ -37,13 +37,14 @@ constexpr int kMXTiles = 6;
 constexpr int kMXTile = 32 * kMXPad;
 constexpr size_t kMagXSmem = sizeof(float) * (kMagWarps + 2) * kMXTiles * kMXTile;
 
+template <bool SMALL>
 __device__ __forceinline__ void stage_rows_m(float* tile, const float* __restrict__ src,
                                              int rowbase, int p0, int nx, int lane) {
 #pragma unroll
   for (int k = 0; k < 2; k++) {
     const int r = 16 * k + (lane >> 1), h = lane & 1;
     const int rb = __shfl_sync(0xffffffffu, rowbase, r);
-    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrapn(p0 + 4 * h, nx)));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrap_near<SMALL>(p0 + 4 * h, nx)));
     float* t = tile + r * kMXPad + 4 * h;
     t[0] = v.x;
     t[1] = v.y;
@@ -53,6 +54,7 @@ __device__ __forceinline__ void stage_rows_m(float* tile, const float* __restric
 }
 
 // velocity rows: v = m / rho
+template <bool SMALL>
 __device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__ rho,
                                           const float* __restrict__ m, int rowbase, int p0,
                                           int nx, int lane) {
@@ -60,7 +62,7 @@ __device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__
   for (int k = 0; k < 2; k++) {
     const int r = 16 * k + (lane >> 1), h = lane & 1;
     const int rb = __shfl_sync(0xffffffffu, rowbase, r);
-    const int off = wrapn(p0 + 4 * h, nx);
+    const int off = wrap_near<SMALL>(p0 + 4 * h, nx);
     const float4 rr = __ldg(reinterpret_cast<const float4*>(rho + rb + off));
     const float4 mm = __ldg(reinterpret_cast<const float4*>(m + rb + off));
     float* t = tile + r * kMXPad + 4 * h;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__
   }
 }
 
-template <int D>
+template <int D, bool SMALL>
 __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_kernel(MagArgs a) {
   using X = MagAxes<D>;
@@ -151,17 +153,17 @@ mag_sweep_kernel(MagArgs a) {
     const float* rw = xw + lane * kMXPad;
     if constexpr (D == 0) {
       __syncwarp();
-      stage_vel(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
-      stage_vel(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
-      stage_vel(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
-      stage_rows_m(xw + 3 * kMXTile, bA, base, p0, nD, lane);
-      stage_rows_m(xw + 4 * kMXTile, bO, base, p0, nD, lane);
-      stage_rows_m(xw + 5 * kMXTile, bD, base, p0, nD, lane);
+      stage_vel<SMALL>(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
+      stage_vel<SMALL>(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
+      stage_vel<SMALL>(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 3 * kMXTile, bA, base, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 4 * kMXTile, bO, base, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 5 * kMXTile, bD, base, p0, nD, lane);
       __syncwarp();
     } else {
 #pragma unroll
       for (int j = 0; j < CH; j++) {
-        const int off = wrapn(p0 + j, nD) * sD;
+        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
         v[j] = __fdividef(__ldg(md + base + off), __ldg(rho + base + off));
         vA[j] = __fdividef(__ldg(md + baseAm + off), __ldg(rho + baseAm + off));
         vO[j] = __fdividef(__ldg(md + baseOm + off), __ldg(rho + baseOm + off));
@@ -198,7 +200,7 @@ mag_sweep_kernel(MagArgs a) {
       const int t = p0 + j;
       const int po = t - 3;
       if (interior && po >= s0 && po < s1) {
-        const int cell = base + wrapn(po, nD) * sD;
+        const int cell = base + po * sD;  // po is inside [s0, s1)
         o_bA[cell] = nA_new;
         o_bO[cell] = nO_new;
       }
@@ -220,7 +222,7 @@ mag_sweep_kernel(MagArgs a) {
             b += kO * (fo1 - fo0);
             b += kA * (fa1 - fa0);
           }
-          o_bD[base + wrapn(pf, nD) * sD] = b;
+          o_bD[base + pf * sD] = b;  // pf is inside [s0, s1)
         }
       }
     }
@@ -236,16 +238,21 @@ cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s) {
   const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
   dim3 block(32, kMagWarps + 2);
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
+  const bool small = a.box.n[axis] < 16;
   if (axis == 0) {  // the x sweep stages rows in more than 48 KB of shared memory
-    cudaError_t e = cudaFuncSetAttribute(mag_sweep_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kMagXSmem);
+    cudaError_t e = small ? cudaFuncSetAttribute(mag_sweep_kernel<0, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem)
+                          : cudaFuncSetAttribute(mag_sweep_kernel<0, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem);
     if (e != cudaSuccess) return e;
   }
-  switch (axis) {
-    case 0: mag_sweep_kernel<0><<<grid, block, kMagXSmem, s>>>(a); break;
-    case 1: mag_sweep_kernel<1><<<grid, block, 0, s>>>(a); break;
-    default: mag_sweep_kernel<2><<<grid, block, 0, s>>>(a); break;
+#define MAG_CASE(DD, SMEM)                                                  \
+  if (axis == DD) {                                                         \
+    if (small) mag_sweep_kernel<DD, true><<<grid, block, SMEM, s>>>(a);     \
+    else mag_sweep_kernel<DD, false><<<grid, block, SMEM, s>>>(a);          \
   }
+  MAG_CASE(0, kMagXSmem) MAG_CASE(1, 0) MAG_CASE(2, 0)
+#undef MAG_CASE
   return cudaGetLastError();
 }
 

@@ -43,6 +43,7 @@ SIGNATURES = {
     "mhd_time": (_I, [_P, _DP]),
     "mhd_sweep": (_I, [_P, _I, _I, _D]),
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
+    "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_diagnostics": (_I, [_P, _DP]),
     "mhd_profile": (_I, [_P, _I]),
     "mhd_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_int), _DP]),
@@ -50,7 +51,7 @@ SIGNATURES = {
 }
 
 
-KERNEL_CLASSES = ["fluid_x", "fluid_y", "fluid_z", "mag_x", "mag_y", "mag_z", "control"]
+KERNEL_CLASSES = ["fluid_x", "fluid_y", "fluid_z", "mag_x", "mag_y", "mag_z", "control", "transpose"]
 K_CLASSES = len(KERNEL_CLASSES)
 
 
@@ -161,6 +162,10 @@ class Box:
 
     def set_segments(self, sx: int = 0, sy: int = 0, sz: int = 0):
         _check(self.lib.mhd_set_segments(self.h, int(sx), int(sy), int(sz)))
+
+    def set_xpath(self, mode: int):
+        """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic."""
+        _check(self.lib.mhd_set_xpath(self.h, int(mode)))
 
     def profile(self, capacity: int):
         """Time every later kernel launch with CUDA events (up to `capacity`)."""

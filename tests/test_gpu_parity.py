@@ -61,6 +61,42 @@ def test_single_sweep_parity(mhd, axis, kind):
     assert np.all(err < 1e-5), err
 
 
+@pytest.mark.parametrize("xpath", [1, 2])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_x_sweep_both_paths(mhd, xpath, kind):
+    """x sweeps read directly (path 1) or through the x<->y exchanged copy
+    (path 2); both against the oracle, on boxes with ragged tiles and a short
+    (< 16 cell) x axis."""
+    for dims in ((48, 40, 36), (12, 20, 8)):
+        st = ic.turbulence(dims, seed=23, dtype=torch.float64, kmin=1.0, kmax=3.0)
+        s = oracle_input(st)
+        tau = 0.35 / oracle.cfl_rate(s, G)
+        box = make_box(mhd, st)
+        box.set_xpath(xpath)
+        box.sweep(0, kind, tau)
+        g = from_gpu(box.get_state())
+        if kind == 0:
+            oracle.fluid_sweep(s, 0, tau, G)
+        else:
+            oracle.mag_sweep(s, 0, tau)
+        err = rel_err(g, s, field_scales(s))
+        assert np.all(err < 1e-5), (dims, err)
+
+
+@pytest.mark.parametrize("xpath", [1, 2])
+def test_full_steps_both_x_paths(mhd, xpath):
+    st = ic.turbulence((40, 24, 20), seed=24, dtype=torch.float64, kmin=1.0, kmax=3.0)
+    s = oracle_input(st)
+    S = field_scales(s)
+    box = make_box(mhd, st)
+    box.set_xpath(xpath)
+    t_orc, _ = oracle.run(s, 4, 0.7, G)
+    box.run(4, 0.7)
+    assert box.time() == pytest.approx(t_orc, rel=1e-5)
+    err = rel_err(from_gpu(box.get_state()), s, S)
+    assert np.all(err < 1e-4), err
+
+
 @pytest.mark.parametrize("segs", [(16, 8, 12), (8, 20, 4), (48, 40, 36)])
 def test_segmentation_is_bitwise_neutral(mhd, segs):
     st = ic.turbulence((48, 40, 36), seed=22, dtype=torch.float64, kmin=1.0, kmax=4.0)
