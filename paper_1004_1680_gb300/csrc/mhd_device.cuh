@@ -57,6 +57,15 @@ __device__ __forceinline__ float vanleer_half(float a, float b) {
   return ab > 0.f ? ab * fast_rcp(a + b) : 0.f;
 }
 
+// van Leer limiter of Section II.B: 2ab/(a+b) when a and b have the same
+// sign, else 0 (a+b cannot vanish when ab > 0).  (This plain form schedules
+// better in the fluid pipe than the half-limiter form used by the magnetic
+// pipe; measured on GB300.)
+__device__ __forceinline__ float vanleer(float a, float b) {
+  float ab = a * b;
+  return ab > 0.f ? __fdividef(2.f * ab, a + b) : 0.f;
+}
+
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame
 // (u = (rho, m_d, m_t1, m_t2, e), b = cell-centred (b_d, b_t1, b_t2)), and the
 // relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
@@ -64,25 +73,25 @@ __device__ __forceinline__ float vanleer_half(float a, float b) {
 // Returns the right and left movers FR = (cu + F)/2, FL = (cu - F)/2.
 __device__ __forceinline__ void split_flux(const float u[5], const float b[3], float gamma,
                                            float FR[5], float FL[5]) {
-  const float rinv = fast_rcp(u[0]);
-  const float vd = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
-  const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-  const float kin = 0.5f * (u[1] * vd + u[2] * v1 + u[3] * v2);
-  const float p = (gamma - 1.f) * (u[4] - kin - 0.5f * b2);
-  const float pstar = p + 0.5f * b2;
-  const float bv = b[0] * vd + b[1] * v1 + b[2] * v2;
+  float rinv = __fdividef(1.f, u[0]);
+  float vd = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
+  float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  float kin = 0.5f * (u[1] * vd + u[2] * v1 + u[3] * v2);
+  float p = (gamma - 1.f) * (u[4] - kin - 0.5f * b2);
+  float pstar = p + 0.5f * b2;
+  float bv = b[0] * vd + b[1] * v1 + b[2] * v2;
   float F[5];
   F[0] = u[1];
   F[1] = u[1] * vd + pstar - b[0] * b[0];
   F[2] = u[2] * vd - b[0] * b[1];
   F[3] = u[3] * vd - b[0] * b[2];
   F[4] = (u[4] + pstar) * vd - b[0] * bv;
-  const float hc = 0.5f * (fabsf(vd) + fast_sqrt((gamma * p + b2) * rinv));  // c/2
+  float c = fabsf(vd) + sqrtf((gamma * p + b2) * rinv);
 #pragma unroll
   for (int q = 0; q < 5; q++) {
-    const float hF = 0.5f * F[q];
-    FR[q] = hc * u[q] + hF;
-    FL[q] = hc * u[q] - hF;
+    float cu = c * u[q];
+    FR[q] = 0.5f * (cu + F[q]);
+    FL[q] = 0.5f * (cu - F[q]);
   }
 }
 
@@ -119,17 +128,15 @@ struct FluidPipe {
   float b1[3];                // frozen b at t-1
   float FR1[5];               // stage-1 right mover at t-1
   float f1m[5];               // stage-1 interface flux at t-3/2
-  float Rh2[5], Rh3[5];       // stage-2 right movers at t-2, t-3
-  float dR3[5];               // Rh(t-3) - Rh(t-4)
-  float Lh2[5];               // stage-2 left mover at t-2
-  float dL2[5];               // Lh(t-2) - Lh(t-3)
+  float Rh2[5], Rh3[5], Rh4[5];  // stage-2 right movers at t-2, t-3, t-4
+  float Lh2[5], Lh3[5];          // stage-2 left movers at t-2, t-3
   float F2m[5];               // stage-2 interface flux at t-7/2
 
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = 0.f;
-      Rh2[q] = Rh3[q] = dR3[q] = Lh2[q] = dL2[q] = F2m[q] = 0.f;
+      Rh2[q] = Rh3[q] = Rh4[q] = Lh2[q] = Lh3[q] = F2m[q] = 0.f;
     }
     b1[0] = b1[1] = b1[2] = 0.f;
   }
@@ -150,13 +157,9 @@ struct FluidPipe {
     split_flux(Uh, b1, gamma, Rh, Lh);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      // right mover at t-5/2 from cell t-3, left mover from cell t-2, each
-      // with half its van Leer limited slope
-      const float dR = Rh2[q] - Rh3[q];
-      const float dL = Lh[q] - Lh2[q];
-      const float right = Rh3[q] + vanleer_half(dR3[q], dR);
-      const float left = Lh2[q] - vanleer_half(dL2[q], dL);
-      const float F2 = right - left;
+      float right = Rh3[q] + 0.5f * vanleer(Rh3[q] - Rh4[q], Rh2[q] - Rh3[q]);
+      float left = Lh2[q] - 0.5f * vanleer(Lh2[q] - Lh3[q], Lh[q] - Lh2[q]);
+      float F2 = right - left;
       out[q] = U3[q] - c_full * (F2 - F2m[q]);
       F2m[q] = F2;
       // shift the windows
@@ -165,10 +168,10 @@ struct FluidPipe {
       U1[q] = U[q];
       FR1[q] = FR[q];
       f1m[q] = f1[q];
-      dR3[q] = dR;
+      Rh4[q] = Rh3[q];
       Rh3[q] = Rh2[q];
       Rh2[q] = Rh[q];
-      dL2[q] = dL;
+      Lh3[q] = Lh2[q];
       Lh2[q] = Lh[q];
     }
     b1[0] = b[0];

@@ -149,7 +149,7 @@ mag_sweep_kernel(MagArgs a) {
     const int p0 = s0 - 4 + CH * c;
     // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
     constexpr int R = (D == 0) ? 1 : CH;
-    float v[R], vA[R], vO[R], qA[R], qO[R], qD[R];
+    float v[R], vA[R], vO[R], qA[R], qO[R], qD[R], rr[R], mm[R], rrA[R], mmA[R], rrO[R], mmO[R];
     const float* rw = xw + lane * kMXPad;
     if constexpr (D == 0) {
       __syncwarp();
@@ -162,11 +162,14 @@ mag_sweep_kernel(MagArgs a) {
       __syncwarp();
     } else {
 #pragma unroll
-      for (int j = 0; j < CH; j++) {
+      for (int j = 0; j < CH; j++) {  // all loads of the chunk first; divisions when used
         const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
-        v[j] = __fdividef(__ldg(md + base + off), __ldg(rho + base + off));
-        vA[j] = __fdividef(__ldg(md + baseAm + off), __ldg(rho + baseAm + off));
-        vO[j] = __fdividef(__ldg(md + baseOm + off), __ldg(rho + baseOm + off));
+        rr[j] = __ldg(rho + base + off);
+        mm[j] = __ldg(md + base + off);
+        rrA[j] = __ldg(rho + baseAm + off);
+        mmA[j] = __ldg(md + baseAm + off);
+        rrO[j] = __ldg(rho + baseOm + off);
+        mmO[j] = __ldg(md + baseOm + off);
         qA[j] = __ldg(bA + base + off);
         qO[j] = __ldg(bO + base + off);
         qD[j] = __ldg(bD + base + off);
@@ -184,7 +187,7 @@ mag_sweep_kernel(MagArgs a) {
         qOj = rw[4 * kMXTile + j];
         qDj = rw[5 * kMXTile + j];
       } else {
-        vj = v[j]; vAj = vA[j]; vOj = vO[j]; qAj = qA[j]; qOj = qO[j]; qDj = qD[j];
+        vj = __fdividef(mm[j], rr[j]); vAj = __fdividef(mmA[j], rrA[j]); vOj = __fdividef(mmO[j], rrO[j]); qAj = qA[j]; qOj = qO[j]; qDj = qD[j];
       }
       const float uA = 0.5f * (vj + vAj);  // v_D on the b_A face
       const float uO = 0.5f * (vj + vOj);  // v_D on the b_O face
