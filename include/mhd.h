@@ -153,6 +153,28 @@ int mhd_profile(mhd_t *m, int capacity);
  * the stream.  Records are kept, so repeated reads give the same totals. */
 int mhd_profile_read(mhd_t *m, int counts[], double ms[]);
 
+/* FP64 diagnostics of caller-owned fields, for callers that cannot allocate
+ * device memory (no counterpart in the paper).  Same numbers as
+ * mhd_diagnostics, computed by the same kernels, but without an mhd_t and
+ * without any allocation: code that runs where a framework's caching
+ * allocator owns all device memory, in a latency-critical loop where a
+ * cudaMalloc (which can synchronise the device) is not allowed, or in a
+ * plug-in with no allocation rights, can still take the conservation sums.
+ *   nx, ny, nz, gamma: box and adiabatic index (gamma > 1), at most
+ *     2^31 - 1 cells; larger boxes are rejected with MHD_E_ARG.
+ *   f[q]: device pointers to the 8 fields, layout as above (read only).
+ *   out: host array of 10 doubles (layout of mhd_diagnostics).
+ *   cuda_stream: the stream to run on (NULL = default); synchronised before
+ *     return.
+ * Scratch: a fixed 194 KiB array in the library's device memory, held by
+ * every GPU that loads the library until the process exits.  Its device
+ * address is looked up on the first call on each device, so call it once
+ * before capturing a stream that will contain it.  All calls share the
+ * array: calls that overlap on the GPU (different streams, threads or
+ * processes sharing a context) race and must be serialised by the caller. */
+int mhd_diagnostics_static(int nx, int ny, int nz, double gamma, const float *const f[8],
+                           double out[10], void *cuda_stream);
+
 /* Description of the last failure on this thread ("" if none). */
 const char *mhd_last_error(void);
 

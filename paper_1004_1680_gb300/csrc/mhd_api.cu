@@ -45,6 +45,13 @@ struct Scalars {  // small device block
 
 }  // namespace
 
+namespace mhd {
+int set_error(int code, const char* where, const char* what) {
+  std::snprintf(g_err, sizeof g_err, "%s: %s", where, what);
+  return code;
+}
+}  // namespace mhd
+
 struct mhd_s {
   int n[3];
   double gamma;

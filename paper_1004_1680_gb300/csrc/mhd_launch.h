@@ -33,6 +33,10 @@ struct TransposeArgs {
   int n[3];  // input extents, fastest first; the output has n[1] fastest
 };
 
+// Record "<where>: <what>" as this thread's last error (mhd_last_error) and
+// return code.
+int set_error(int code, const char* where, const char* what);
+
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);
 cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s);

@@ -149,7 +149,7 @@ mag_sweep_kernel(MagArgs a) {
     const int p0 = s0 - 4 + CH * c;
     // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
     constexpr int R = (D == 0) ? 1 : CH;
-    float v[R], vA[R], vO[R], qA[R], qO[R], qD[R], rr[R], mm[R], rrA[R], mmA[R], rrO[R], mmO[R];
+    float qA[R], qO[R], qD[R], rr[R], mm[R], rrA[R], mmA[R], rrO[R], mmO[R];
     const float* rw = xw + lane * kMXPad;
     if constexpr (D == 0) {
       __syncwarp();

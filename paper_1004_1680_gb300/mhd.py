@@ -47,6 +47,7 @@ SIGNATURES = {
     "mhd_diagnostics": (_I, [_P, _DP]),
     "mhd_profile": (_I, [_P, _I]),
     "mhd_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_int), _DP]),
+    "mhd_diagnostics_static": (_I, [_I, _I, _I, _D, _PP, _DP, _P]),
     "mhd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -91,6 +92,20 @@ def _check(rc: int):
 
 def _field_ptrs(t: torch.Tensor):
     return (ctypes.c_void_p * 8)(*[t[q].data_ptr() for q in range(8)])
+
+
+def diagnostics_static(state: torch.Tensor, gamma: float = 5.0 / 3.0, stream=None) -> np.ndarray:
+    """FP64 diagnostics of a float32 CUDA state tensor (8, nz, ny, nx) through
+    mhd_diagnostics_static: no mhd_t and no device allocation."""
+    lib = load()
+    if not state.is_cuda or state.dtype != torch.float32 or not state.is_contiguous():
+        raise ValueError("state must be a contiguous float32 CUDA tensor")
+    nz, ny, nx = state.shape[1:]
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = (ctypes.c_double * 10)()
+    _check(lib.mhd_diagnostics_static(nx, ny, nz, gamma, _field_ptrs(state), out,
+                                      ctypes.c_void_p(s.cuda_stream)))
+    return np.array(out[:], dtype=np.float64)
 
 
 class Box:
