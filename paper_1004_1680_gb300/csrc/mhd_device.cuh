@@ -49,21 +49,30 @@ __device__ __forceinline__ float fast_sqrt(float x) {
   return r;
 }
 
+// x > 0 ? q : 0 as a predicated select (never a branch): q is computed by
+// the caller unconditionally, so a limiter costs no control flow.
+__device__ __forceinline__ float keep_if_positive(float x, float q) {
+  float r;
+  asm("{\n\t.reg .pred p;\n\tsetp.gt.f32 p, %1, 0f00000000;\n\tselp.f32 %0, %2, 0f00000000, p;\n\t}"
+      : "=f"(r)
+      : "f"(x), "f"(q));
+  return r;
+}
+
 // Half the van Leer limiter of Section II.B: phi(a,b)/2 = ab/(a+b) when a and
 // b have the same sign, else 0 (a+b cannot vanish when ab > 0).  The
 // second-order correction adds phi/2 to the upwind value.
 __device__ __forceinline__ float vanleer_half(float a, float b) {
   const float ab = a * b;
-  return ab > 0.f ? ab * fast_rcp(a + b) : 0.f;
+  return keep_if_positive(ab, ab * fast_rcp(a + b));
 }
 
 // van Leer limiter of Section II.B: 2ab/(a+b) when a and b have the same
-// sign, else 0 (a+b cannot vanish when ab > 0).  (This plain form schedules
-// better in the fluid pipe than the half-limiter form used by the magnetic
-// pipe; measured on GB300.)
+// sign, else 0 (a+b cannot vanish when ab > 0; otherwise the quotient is
+// discarded by the select).
 __device__ __forceinline__ float vanleer(float a, float b) {
-  float ab = a * b;
-  return ab > 0.f ? __fdividef(2.f * ab, a + b) : 0.f;
+  const float ab = a * b;
+  return keep_if_positive(ab, __fdividef(2.f * ab, a + b));
 }
 
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame

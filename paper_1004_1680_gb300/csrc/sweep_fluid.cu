@@ -62,7 +62,7 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
 }
 
 template <int D, bool RATE, bool SMALL>
-__global__ void __launch_bounds__(32 * kFluidWarps, 4)
+__global__ void __launch_bounds__(32 * kFluidWarps, RATE ? 3 : 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
   constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
