@@ -175,6 +175,53 @@ int mhd_profile_read(mhd_t *m, int counts[], double ms[]);
 int mhd_diagnostics_static(int nx, int ny, int nz, double gamma, const float *const f[8],
                            double out[10], void *cuda_stream);
 
+/* ---- Ensembles of independent boxes -------------------------------------
+ * Many periodic boxes of uneven sizes advanced together: every sweep of the
+ * Section II.B schedule is one launch over all boxes, each box keeps its own
+ * CFL timestep and time, and a run of steps is one CUDA graph launch.  (The
+ * paper evolves one box; ensembles are an extension.)  Box b has the layout
+ * and conventions of a single box with dims3[3b..3b+2] = (nx, ny, nz). */
+typedef struct mhd_ens_s mhd_ens_t;
+
+/* Create nbox boxes (nx >= 4, nx % 4 == 0, ny, nz >= 1; at most 2^31 - 1
+ * cells in all boxes together).  Allocates two copies of every box's state
+ * on the current device.  NULL on failure. */
+mhd_ens_t *mhd_ens_create(int nbox, const int *dims3, double gamma);
+void mhd_ens_destroy(mhd_ens_t *e);
+int mhd_ens_set_stream(mhd_ens_t *e, void *cuda_stream);
+
+/* Copy box b's state in / out (layout of mhd_set_state / mhd_get_state).
+ * set_state resets that box's time and recomputes its CFL rate. */
+int mhd_ens_set_state(mhd_ens_t *e, int box, const float *const f[8], int on_device);
+int mhd_ens_get_state(const mhd_ens_t *e, int box, float *const f[8], int on_device);
+
+/* nsteps full steps of every box, each box with its own CFL timestep computed
+ * on the device.  The launches of the whole run are captured into a CUDA
+ * graph on first use (cached per step count, cfl and buffer assignment) and
+ * replayed.  Asynchronous. */
+int mhd_ens_run(mhd_ens_t *e, int nsteps, double cfl);
+
+/* Per-box simulation times (nbox doubles, host).  Synchronises. */
+int mhd_ens_times(const mhd_ens_t *e, double *t_out);
+
+/* Per-box full CFL timestep of the current states (nbox doubles, host);
+ * MHD_E_STATE if any box is invalid (its entry is 0).  Synchronises. */
+int mhd_ens_cfl_dt(mhd_ens_t *e, double cfl, double *dt_out);
+
+/* Per-box FP64 diagnostics (nbox x 10 doubles, host, layout of
+ * mhd_diagnostics).  Synchronises. */
+int mhd_ens_diagnostics(mhd_ens_t *e, double *out);
+
+/* Tiling of the ensemble launches: x path (1 direct, 2 exchanged layout; see
+ * mhd_set_xpath) and pencil segment divisor (1, 2 or 4: each pencil of a box
+ * is marched by that many threads when its length allows). */
+int mhd_ens_set_tuning(mhd_ens_t *e, int xpath, int segdiv);
+
+/* Pick the fastest tiling by timing two steps of each candidate on a copy of
+ * the current states (restored afterwards); the choice is cached per set of
+ * box sizes for the process.  Writes the choice if the pointers are not NULL. */
+int mhd_ens_autotune(mhd_ens_t *e, double cfl, int *xpath_out, int *segdiv_out);
+
 /* Description of the last failure on this thread ("" if none). */
 const char *mhd_last_error(void);
 

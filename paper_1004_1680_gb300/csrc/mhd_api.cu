@@ -273,7 +273,13 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   m->box.stride[0] = 1;
   m->box.stride[1] = nx;
   m->box.stride[2] = (long long)nx * ny;
-  cudaError_t e = cudaMalloc(&m->arena, sizeof(float) * (size_t)N * 16);
+  cudaError_t e = mhd::prepare_mag_kernels();
+  if (e != cudaSuccess) {
+    cuda_fail(e, "kernel attributes");
+    delete m;
+    return nullptr;
+  }
+  e = cudaMalloc(&m->arena, sizeof(float) * (size_t)N * 16);
   if (e != cudaSuccess) {
     cuda_fail(e, "cudaMalloc(state)");
     delete m;

@@ -9,6 +9,28 @@ namespace mhd {
 
 constexpr int kMagWarps = 8;  // interior rows of a magnetic-sweep tile
 
+// One box of an ensemble: physical extents, first cell in the concatenated
+// field arrays (a multiple of 32), and pencil segment length per axis.
+struct EnsBox {
+  int n[3];
+  int offset;
+  int seg[3];
+  int pad;
+};
+
+// Ensemble launches (items != nullptr): block b of the grid works on
+// items[b] = (box, block x, block y, block z) of that box; the box geometry
+// comes from boxes[box] (exchanged x and y when layout == 1), its sweep step
+// from tau_arr[box] and its CFL accumulator is rate_arr[box].
+struct EnsArgs {
+  const int4* items = nullptr;
+  const EnsBox* boxes = nullptr;
+  const float* tau_arr = nullptr;
+  unsigned* rate_arr = nullptr;
+  int layout = 0;
+  int phys_axis = 0;
+};
+
 struct FluidArgs {
   const float* in[8];  // current fields
   float* out[8];       // destinations of fields 0..4 (others unused)
@@ -17,6 +39,8 @@ struct FluidArgs {
   const float* tau;    // device scalar: step of this sweep
   unsigned* rate;      // fused CFL rate accumulator (float bits), or nullptr
   int seg;             // pencil segment length along the sweep axis
+  EnsArgs ens;         // ensemble launches only
+  int nblocks = 0;     // ensemble launches: number of work items
 };
 
 struct MagArgs {
@@ -25,13 +49,63 @@ struct MagArgs {
   Box box;
   const float* tau;
   int seg;
+  EnsArgs ens;
+  int nblocks = 0;
 };
 
 struct TransposeArgs {
   const float* in[8];
   float* out[8];
   int n[3];  // input extents, fastest first; the output has n[1] fastest
+  EnsArgs ens;   // ensemble: items = (box, tile i, tile j, k); layout = input layout
+  int nblocks = 0;
 };
+
+// Resolved geometry of the block a kernel is running: the box as the kernel
+// sees it, the block's coordinates, segment, step and CFL accumulator, and
+// the offset of the box in the field arrays.
+struct BlockGeom {
+  Box box;
+  int bx, by, bz;
+  int seg;
+  int off;
+  float tau;
+  unsigned* rate;
+};
+
+__device__ __forceinline__ BlockGeom block_geom(const EnsArgs& e, const Box& box, int seg,
+                                                const float* tau, unsigned* rate) {
+  BlockGeom g;
+  if (e.items) {
+    const int4 it = e.items[blockIdx.x];
+    const EnsBox eb = e.boxes[it.x];
+    const int n0 = e.layout ? eb.n[1] : eb.n[0];
+    const int n1 = e.layout ? eb.n[0] : eb.n[1];
+    g.box.n[0] = n0;
+    g.box.n[1] = n1;
+    g.box.n[2] = eb.n[2];
+    g.box.stride[0] = 1;
+    g.box.stride[1] = n0;
+    g.box.stride[2] = (long long)n0 * n1;
+    g.bx = it.y;
+    g.by = it.z;
+    g.bz = it.w;
+    g.seg = eb.seg[e.phys_axis];
+    g.off = eb.offset;
+    g.tau = tau ? e.tau_arr[it.x] : 0.f;
+    g.rate = e.rate_arr ? e.rate_arr + it.x : nullptr;
+  } else {
+    g.box = box;
+    g.bx = blockIdx.x;
+    g.by = blockIdx.y;
+    g.bz = blockIdx.z;
+    g.seg = seg;
+    g.off = 0;
+    g.tau = tau ? *tau : 0.f;
+    g.rate = rate;
+  }
+  return g;
+}
 
 // Record "<where>: <what>" as this thread's last error (mhd_last_error) and
 // return code.
@@ -39,8 +113,14 @@ int set_error(int code, const char* where, const char* what);
 
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);
+// ensemble step control: for every box b < nbox, tau[b] = cfl / rate_cur[b]
+// (0 for an invalid state), time[b] += 2 tau[b], rate_next[b] = 0
+cudaError_t launch_ens_control(const unsigned* rate_cur, unsigned* rate_next, float* tau,
+                               double* time, int nbox, double cfl, cudaStream_t s);
 cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
 cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s);
+// one-time per-device kernel attributes (call on the current device before launching)
+cudaError_t prepare_mag_kernels();
 cudaError_t launch_cfl_rate(const float* const f[8], const Box& box, float gamma, unsigned* rate,
                             cudaStream_t s);
 // device-side step control: tau = cfl / rate_cur (or the given tau if cfl<0),

@@ -74,6 +74,24 @@ cudaError_t launch_step_control(const unsigned* rate_cur, unsigned* rate_next, f
   return cudaGetLastError();
 }
 
+__global__ void ens_control_kernel(const unsigned* rate_cur, unsigned* rate_next, float* tau,
+                                   double* time, int nbox, double cfl) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const float r = __uint_as_float(rate_cur[b]);
+  const double t = (r > 0.f && r <= FLT_MAX) ? cfl / (double)r : 0.0;  // invalid state: stand still
+  const float tf = (float)t;
+  tau[b] = tf;
+  time[b] += 2.0 * (double)tf;
+  rate_next[b] = 0u;
+}
+
+cudaError_t launch_ens_control(const unsigned* rate_cur, unsigned* rate_next, float* tau,
+                               double* time, int nbox, double cfl, cudaStream_t s) {
+  ens_control_kernel<<<(nbox + 127) / 128, 128, 0, s>>>(rate_cur, rate_next, tau, time, nbox, cfl);
+  return cudaGetLastError();
+}
+
 __global__ void set_tau_kernel(float* tau, float value) { *tau = value; }
 
 cudaError_t launch_set_tau(float* tau, double value, cudaStream_t s) {

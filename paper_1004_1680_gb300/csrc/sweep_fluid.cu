@@ -68,12 +68,13 @@ fluid_sweep_kernel(FluidArgs a) {
   constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
   __shared__ float xs[(D == 0) ? kFluidWarps * kXTiles * kXTile : 1];
   const int lane = threadIdx.x;
-  const int nA = a.box.n[X::A], nO = a.box.n[X::O], nD = a.box.n[D];
-  const int pa = blockIdx.x * 32 + lane;
-  const int pb = blockIdx.y * kFluidWarps + threadIdx.y;
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, a.rate);
+  const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
+  const int pa = G.bx * 32 + lane;
+  const int pb = G.by * kFluidWarps + threadIdx.y;
   const bool active = (pa < nA) && (pb < nO);
   const int ia = min(pa, nA - 1), ib = min(pb, nO - 1);
-  const int sA = (int)a.box.stride[X::A], sO = (int)a.box.stride[X::O], sD = (int)a.box.stride[D];
+  const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
   const int base = ia * sA + ib * sO;
   const int baseA1 = wrapi(ia + 1, nA) * sA + ib * sO;  // pencil +1 along A
   const int baseO1 = ia * sA + wrapi(ib + 1, nO) * sO;  // pencil +1 along O
@@ -81,30 +82,30 @@ fluid_sweep_kernel(FluidArgs a) {
   const int baseT1 = (X::T1 == X::A) ? baseA1 : baseO1;
   const int baseT2 = (X::T2 == X::A) ? baseA1 : baseO1;
 
-  const float* __restrict__ rho = a.in[RHO];
-  const float* __restrict__ md = a.in[MX + D];
-  const float* __restrict__ m1 = a.in[MX + X::T1];
-  const float* __restrict__ m2 = a.in[MX + X::T2];
-  const float* __restrict__ en = a.in[EN];
-  const float* __restrict__ bd = a.in[BX + D];
-  const float* __restrict__ b1 = a.in[BX + X::T1];
-  const float* __restrict__ b2 = a.in[BX + X::T2];
-  float* __restrict__ o_rho = a.out[RHO];
-  float* __restrict__ o_md = a.out[MX + D];
-  float* __restrict__ o_m1 = a.out[MX + X::T1];
-  float* __restrict__ o_m2 = a.out[MX + X::T2];
-  float* __restrict__ o_en = a.out[EN];
+  const float* __restrict__ rho = a.in[RHO] + G.off;
+  const float* __restrict__ md = a.in[MX + D] + G.off;
+  const float* __restrict__ m1 = a.in[MX + X::T1] + G.off;
+  const float* __restrict__ m2 = a.in[MX + X::T2] + G.off;
+  const float* __restrict__ en = a.in[EN] + G.off;
+  const float* __restrict__ bd = a.in[BX + D] + G.off;
+  const float* __restrict__ b1 = a.in[BX + X::T1] + G.off;
+  const float* __restrict__ b2 = a.in[BX + X::T2] + G.off;
+  float* __restrict__ o_rho = a.out[RHO] + G.off;
+  float* __restrict__ o_md = a.out[MX + D] + G.off;
+  float* __restrict__ o_m1 = a.out[MX + X::T1] + G.off;
+  float* __restrict__ o_m2 = a.out[MX + X::T2] + G.off;
+  float* __restrict__ o_en = a.out[EN] + G.off;
   float* xw = xs + (D == 0 ? threadIdx.y * kXTiles * kXTile : 0);  // this warp's tiles
 
   const float gamma = a.gamma;
-  const float tau = *a.tau;
+  const float tau = G.tau;
   const float c_full = tau * (float)nD;  // tau / h_D
   const float c_half = 0.5f * c_full;    // tau / (2 h_D)
-  const int s0 = blockIdx.z * a.seg;
-  const int s1 = s0 + a.seg;
+  const int s0 = G.bz * G.seg;
+  const int s1 = s0 + G.seg;
   // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
   // warm-up cell so that x chunks start 16-byte aligned)
-  const int nchunk = (a.seg + 7 + CH - 1) / CH;
+  const int nchunk = (G.seg + 7 + CH - 1) / CH;
 
   FluidPipe pipe;
   pipe.init();
@@ -190,7 +191,7 @@ fluid_sweep_kernel(FluidArgs a) {
           float m[3], bg[3];
           m[D] = o[1]; m[X::T1] = o[2]; m[X::T2] = o[3];
           bg[D] = bc3[0]; bg[X::T1] = bc3[1]; bg[X::T2] = bc3[2];
-          rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, a.box.n));
+          rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, G.box.n));
         }
       }
       if (RATE) {  // window of b_c: bc2 = b_c(t-1), bc3 = b_c(t-2) for the next step
@@ -201,7 +202,7 @@ fluid_sweep_kernel(FluidArgs a) {
   }
   if (RATE) {
     for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    if (lane == 0) atomicMax(a.rate, __float_as_uint(rmax));
+    if (lane == 0) atomicMax(G.rate, __float_as_uint(rmax));
   }
 }
 
@@ -214,6 +215,9 @@ cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s
   dim3 block(32, kFluidWarps);
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kFluidWarps - 1) / kFluidWarps,
             a.box.n[axis] / a.seg);
+  // ensemble launches: one block per work item; `small` must hold for every
+  // box of the launch (the host passes the smallest extent in a.box)
+  if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
   const bool small = a.box.n[axis] < 16;
 #define FLUID_CASE(DD, RR)                                                        \
   if (axis == DD && rate == RR) {                                                 \

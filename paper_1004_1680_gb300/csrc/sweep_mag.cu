@@ -83,8 +83,9 @@ mag_sweep_kernel(MagArgs a) {
   extern __shared__ float xs_dyn[];               // x sweeps only: staged rows
 
   const int lane = threadIdx.x, w = threadIdx.y;
-  const int nA = a.box.n[X::A], nO = a.box.n[X::O], nD = a.box.n[D];
-  const int a0 = blockIdx.x * 32, b0 = blockIdx.y * kMagWarps;
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
+  const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
+  const int a0 = G.bx * 32, b0 = G.by * kMagWarps;
   const int cntA = min(32, nA - a0), cntO = min(kMagWarps, nO - b0);
 
   // this thread's pencil and role
@@ -108,31 +109,31 @@ mag_sweep_kernel(MagArgs a) {
     row = min(lane, kMagWarps - 1);
     col = cntA;
   }
-  const int sA = (int)a.box.stride[X::A], sO = (int)a.box.stride[X::O], sD = (int)a.box.stride[D];
+  const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
   const int base = pa * sA + pb * sO;
   const int baseAm = wrapi(pa - 1, nA) * sA + pb * sO;  // pencil -1 along A
   const int baseOm = pa * sA + wrapi(pb - 1, nO) * sO;  // pencil -1 along O
 
-  const float* __restrict__ rho = a.in[RHO];
-  const float* __restrict__ md = a.in[MX + D];
-  const float* __restrict__ bA = a.in[BX + X::A];
-  const float* __restrict__ bO = a.in[BX + X::O];
-  const float* __restrict__ bD = a.in[BX + D];
-  float* __restrict__ o_bA = a.out[X::A];
-  float* __restrict__ o_bO = a.out[X::O];
-  float* __restrict__ o_bD = a.out[D];
+  const float* __restrict__ rho = a.in[RHO] + G.off;
+  const float* __restrict__ md = a.in[MX + D] + G.off;
+  const float* __restrict__ bA = a.in[BX + X::A] + G.off;
+  const float* __restrict__ bO = a.in[BX + X::O] + G.off;
+  const float* __restrict__ bD = a.in[BX + D] + G.off;
+  float* __restrict__ o_bA = a.out[X::A] + G.off;
+  float* __restrict__ o_bO = a.out[X::O] + G.off;
+  float* __restrict__ o_bD = a.out[D] + G.off;
   float* xw = xs_dyn + (D == 0 ? w * kMXTiles * kMXTile : 0);
 
-  const float tau = *a.tau;
+  const float tau = G.tau;
   const float c_full = tau * (float)nD;        // tau / h_D
   const float c_half = 0.5f * c_full;
   const float kA = tau * (float)nA;             // tau / h_A
   const float kO = tau * (float)nO;             // tau / h_O
-  const int s0 = blockIdx.z * a.seg;
-  const int s1 = s0 + a.seg;
+  const int s0 = G.bz * G.seg;
+  const int s1 = s0 + G.seg;
   // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
   // warm-up cell so that x chunks start 16-byte aligned)
-  const int nchunk = (a.seg + 7 + CH - 1) / CH;
+  const int nchunk = (G.seg + 7 + CH - 1) / CH;
   // slots read by the tile: fO rows 0..cntO (row cntO = halo row), fA columns
   // 0..cntA (column cntA = halo column); idle lanes of a partial tile must not
   // overwrite a halo slot
@@ -237,18 +238,23 @@ mag_sweep_kernel(MagArgs a) {
 
 namespace mhd {
 
+// The x sweep stages rows in more than 48 KB of shared memory; the limit is
+// raised once per device before any launch (never during a graph capture).
+cudaError_t prepare_mag_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(mag_sweep_kernel<0, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mag_sweep_kernel<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMagXSmem);
+  return e;
+}
+
 cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s) {
   const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
   dim3 block(32, kMagWarps + 2);
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
+  if (a.ens.items) grid = dim3(a.nblocks, 1, 1);  // one block per work item
   const bool small = a.box.n[axis] < 16;
-  if (axis == 0) {  // the x sweep stages rows in more than 48 KB of shared memory
-    cudaError_t e = small ? cudaFuncSetAttribute(mag_sweep_kernel<0, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem)
-                          : cudaFuncSetAttribute(mag_sweep_kernel<0, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem);
-    if (e != cudaSuccess) return e;
-  }
 #define MAG_CASE(DD, SMEM)                                                  \
   if (axis == DD) {                                                         \
     if (small) mag_sweep_kernel<DD, true><<<grid, block, SMEM, s>>>(a);     \

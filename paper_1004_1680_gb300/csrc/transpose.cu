@@ -23,10 +23,15 @@ constexpr int kTRows = 8;  // threads along the tile's row index
 __global__ void __launch_bounds__(kTile * kTRows)
 transpose01_kernel(TransposeArgs a) {
   __shared__ float tile[8][kTile][kTile + 1];
-  const int n0 = a.n[0], n1 = a.n[1];
-  const int i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile, k = blockIdx.z;
+  Box in_box;
+  in_box.n[0] = a.n[0];
+  in_box.n[1] = a.n[1];
+  in_box.n[2] = a.n[2];
+  const BlockGeom G = block_geom(a.ens, in_box, 1, nullptr, nullptr);
+  const int n0 = G.box.n[0], n1 = G.box.n[1];
+  const int i0 = G.bx * kTile, j0 = G.by * kTile, k = G.bz;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long long plane = (long long)n0 * n1 * k;
+  const long long plane = (long long)n0 * n1 * k + G.off;
 #pragma unroll
   for (int q = 0; q < 8; q++) {
 #pragma unroll
@@ -49,6 +54,7 @@ transpose01_kernel(TransposeArgs a) {
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s) {
   dim3 block(kTile, kTRows);
   dim3 grid((a.n[0] + kTile - 1) / kTile, (a.n[1] + kTile - 1) / kTile, a.n[2]);
+  if (a.ens.items) grid = dim3(a.nblocks, 1, 1);  // one block per (box, tile, plane)
   transpose01_kernel<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }

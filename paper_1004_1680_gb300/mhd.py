@@ -48,6 +48,17 @@ SIGNATURES = {
     "mhd_profile": (_I, [_P, _I]),
     "mhd_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_int), _DP]),
     "mhd_diagnostics_static": (_I, [_I, _I, _I, _D, _PP, _DP, _P]),
+    "mhd_ens_create": (_P, [_I, ctypes.POINTER(ctypes.c_int), _D]),
+    "mhd_ens_destroy": (None, [_P]),
+    "mhd_ens_set_stream": (_I, [_P, _P]),
+    "mhd_ens_set_state": (_I, [_P, _I, _PP, _I]),
+    "mhd_ens_get_state": (_I, [_P, _I, _PP, _I]),
+    "mhd_ens_run": (_I, [_P, _I, _D]),
+    "mhd_ens_times": (_I, [_P, _DP]),
+    "mhd_ens_cfl_dt": (_I, [_P, _D, _DP]),
+    "mhd_ens_diagnostics": (_I, [_P, _DP]),
+    "mhd_ens_set_tuning": (_I, [_P, _I, _I]),
+    "mhd_ens_autotune": (_I, [_P, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mhd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -197,3 +208,75 @@ class Box:
         out = (ctypes.c_double * 10)()
         _check(self.lib.mhd_diagnostics(self.h, out))
         return np.array(out[:], dtype=np.float64)
+
+
+class Ensemble:
+    """Many independent periodic boxes advanced together (wraps mhd_ens_t)."""
+
+    def __init__(self, dims, gamma: float = 5.0 / 3.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.lib = load()
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.gamma = gamma
+        flat = (ctypes.c_int * (3 * len(self.dims)))(*[v for d in self.dims for v in d])
+        h = self.lib.mhd_ens_create(len(self.dims), flat, gamma)
+        if not h:
+            raise MHDError(MHD_E_ARG, self.lib.mhd_last_error().decode())
+        self.h = ctypes.c_void_p(h)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        _check(self.lib.mhd_ens_set_stream(self.h, ctypes.c_void_p(s.cuda_stream)))
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mhd_ens_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, b):
+        nx, ny, nz = self.dims[b]
+        return (8, nz, ny, nx)
+
+    def set_state(self, b: int, state: torch.Tensor):
+        if state.shape != self.shape(b) or state.dtype != torch.float32 or not state.is_contiguous():
+            raise ValueError(f"state must be contiguous float32 {self.shape(b)}")
+        _check(self.lib.mhd_ens_set_state(self.h, int(b), _field_ptrs(state), 1 if state.is_cuda else 0))
+        self._keep[b] = state
+
+    def get_state(self, b: int, device="cuda") -> torch.Tensor:
+        out = torch.empty(self.shape(b), dtype=torch.float32, device=device)
+        _check(self.lib.mhd_ens_get_state(self.h, int(b), _field_ptrs(out), 1 if out.is_cuda else 0))
+        return out
+
+    def run(self, nsteps: int, cfl: float = 0.7):
+        _check(self.lib.mhd_ens_run(self.h, int(nsteps), float(cfl)))
+
+    def times(self) -> np.ndarray:
+        out = (ctypes.c_double * len(self.dims))()
+        _check(self.lib.mhd_ens_times(self.h, out))
+        return np.array(out[:])
+
+    def cfl_dt(self, cfl: float = 0.7) -> np.ndarray:
+        out = (ctypes.c_double * len(self.dims))()
+        _check(self.lib.mhd_ens_cfl_dt(self.h, cfl, out))
+        return np.array(out[:])
+
+    def diagnostics(self) -> np.ndarray:
+        out = (ctypes.c_double * (10 * len(self.dims)))()
+        _check(self.lib.mhd_ens_diagnostics(self.h, out))
+        return np.array(out[:]).reshape(len(self.dims), 10)
+
+    def set_tuning(self, xpath: int, segdiv: int):
+        _check(self.lib.mhd_ens_set_tuning(self.h, int(xpath), int(segdiv)))
+
+    def autotune(self, cfl: float = 0.7):
+        x, s = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.mhd_ens_autotune(self.h, cfl, ctypes.byref(x), ctypes.byref(s)))
+        return x.value, s.value
