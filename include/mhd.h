@@ -102,6 +102,15 @@ int mhd_time(const mhd_t *m, double *t);
  * the sweeps one by one. */
 int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
 
+/* Optional floor on the gas pressure (not in the paper; 0 = off, the
+ * default).  The total-energy scheme leaves e untouched in the magnetic
+ * sweeps, so in strongly magnetised, supersonic flow the magnetic energy can
+ * outgrow the cell's thermal energy and p falls below zero.  With
+ * p_floor > 0, each fluid sweep raises e after its update where needed so
+ * that p >= p_floor (mass, momentum and b unchanged; energy is added only
+ * where the floor acts). */
+int mhd_set_pressure_floor(mhd_t *m, double p_floor);
+
 /* Pencil segment lengths used by the sweeps along x, y and z.  A sweep splits
  * every pencil of n_d cells into n_d/seg_d pieces, each marched by its own
  * thread (more parallelism for small boxes, 8 cells of warm-up re-read per
@@ -211,6 +220,9 @@ int mhd_ens_cfl_dt(mhd_ens_t *e, double cfl, double *dt_out);
 /* Per-box FP64 diagnostics (nbox x 10 doubles, host, layout of
  * mhd_diagnostics).  Synchronises. */
 int mhd_ens_diagnostics(mhd_ens_t *e, double *out);
+
+/* Pressure floor for every box (see mhd_set_pressure_floor). */
+int mhd_ens_set_pressure_floor(mhd_ens_t *e, double p_floor);
 
 /* Tiling of the ensemble launches: x path (1 direct, 2 exchanged layout; see
  * mhd_set_xpath) and pencil segment divisor (1, 2 or 4: each pencil of a box

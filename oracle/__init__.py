@@ -65,6 +65,7 @@ def _load():
             lib.orc_run.restype = ctypes.c_double
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_pressure_floor.argtypes = [ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -92,6 +93,11 @@ def threads() -> int:
 
 def set_threads(t: int) -> None:
     _load().orc_set_threads(int(t))
+
+
+def set_pressure_floor(p_floor: float) -> None:
+    """Optional floor on the gas pressure after each fluid sweep (0 = off)."""
+    _load().orc_set_pressure_floor(float(p_floor))
 
 
 def fluid_sweep(state: np.ndarray, d: int, tau: float, gamma: float) -> None:

@@ -48,6 +48,15 @@
 
 enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
 
+/* Optional pressure floor (0 = off, the paper's scheme).  When positive, the
+ * fluid sweep raises e after its update wherever the gas pressure would fall
+ * below p_floor: e = max(e, |m|^2/(2 rho) + |b_c|^2/2 + p_floor/(gamma-1)).
+ * Mass and momentum are untouched; energy is added only where the floor acts.
+ * Not in the paper: an extension for strongly magnetised, supersonic runs in
+ * which the total-energy scheme drives p negative. */
+static double g_pfloor = 0.0;
+void orc_set_pressure_floor(double p_floor) { g_pfloor = p_floor > 0.0 ? p_floor : 0.0; }
+
 /* periodic wrap of an index */
 static int wrap(int i, int n) {
     int r = i % n;
@@ -143,6 +152,14 @@ static void fluid_pencil(int n, double h, double tau, double gamma,
     for (q = 0; q < 5; q++)
         for (i = 0; i < n; i++)
             U[q][i] = U[q][i] - (tau / h) * (fl[q * n + i] - fl[q * n + wrap(i - 1, n)]);
+    if (g_pfloor > 0.0) {
+        for (i = 0; i < n; i++) {
+            double kin = 0.5 * (U[1][i] * U[1][i] + U[2][i] * U[2][i] + U[3][i] * U[3][i]) / U[0][i];
+            double mag = 0.5 * (B[0][i] * B[0][i] + B[1][i] * B[1][i] + B[2][i] * B[2][i]);
+            double emin = kin + mag + g_pfloor / (gamma - 1.0);
+            if (U[4][i] < emin) U[4][i] = emin;
+        }
+    }
 }
 
 /*

@@ -74,6 +74,7 @@ struct mhd_ens_s {
   int layout = 0;
   int xpath = 2;
   int segdiv = 1;
+  float p_floor = 0.f;
   float* tau = nullptr;
   unsigned* rate[2] = {nullptr, nullptr};
   double* time = nullptr;
@@ -215,6 +216,7 @@ int fluid(mhd_ens_s* e, int d, bool rate, cudaStream_t s) {
   a.box.n[0] = a.box.n[1] = a.box.n[2] = 32;
   a.box.n[ka] = e->fluid[d].minext;  // selects the short-axis kernel if any box needs it
   a.gamma = (float)e->gamma;
+  a.p_floor = e->p_floor;
   a.tau = e->tau;
   a.rate = nullptr;
   a.seg = 1;
@@ -491,6 +493,13 @@ int mhd_ens_diagnostics(mhd_ens_t* e, double* out) {
     CKE(cudaMemcpyAsync(out + 10 * b, e->diag_out, sizeof(double) * 10, cudaMemcpyDeviceToHost, e->stream));
   }
   CKE(cudaStreamSynchronize(e->stream));
+  return MHD_OK;
+}
+
+int mhd_ens_set_pressure_floor(mhd_ens_t* e, double p_floor) {
+  if (!e || !(p_floor >= 0.0)) return mhd::set_error(MHD_E_ARG, "mhd_ens_set_pressure_floor", "bad arguments");
+  e->p_floor = (float)p_floor;
+  drop_graphs(e);  // the floor is baked into captured launches
   return MHD_OK;
 }
 

@@ -64,6 +64,7 @@ struct mhd_s {
   int layout = 0;       // 0: x fastest; 1: x and y exchanged (for x sweeps)
   int xpath = 0;        // x sweeps: 1 direct, 2 through the exchanged layout
   int xpath_req = 0;    // requested by mhd_set_xpath (0 = automatic)
+  float p_floor = 0.f;  // optional pressure floor after fluid sweeps (0 = off)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
@@ -182,6 +183,7 @@ int fluid(mhd_s* m, int d, bool rate) {
   }
   a.box = *box;
   a.gamma = (float)m->gamma;
+  a.p_floor = m->p_floor;
   a.tau = &m->sc->tau;
   a.rate = rate ? &m->sc->rate[1 - m->rcur] : nullptr;
   a.seg = m->seg[d];
@@ -446,6 +448,13 @@ int mhd_set_xpath(mhd_t* m, int mode) {
   if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
   m->xpath_req = mode;
   m->xpath = mode ? mode : auto_xpath(m);
+  return MHD_OK;
+}
+
+int mhd_set_pressure_floor(mhd_t* m, double p_floor) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (!(p_floor >= 0.0)) return fail(MHD_E_ARG, "pressure floor must be >= 0");
+  m->p_floor = (float)p_floor;
   return MHD_OK;
 }
 

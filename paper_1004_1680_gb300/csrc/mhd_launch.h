@@ -36,6 +36,7 @@ struct FluidArgs {
   float* out[8];       // destinations of fields 0..4 (others unused)
   Box box;
   float gamma;
+  float p_floor = 0.f; // optional floor on the gas pressure of the output (0: off)
   const float* tau;    // device scalar: step of this sweep
   unsigned* rate;      // fused CFL rate accumulator (float bits), or nullptr
   int seg;             // pencil segment length along the sweep axis

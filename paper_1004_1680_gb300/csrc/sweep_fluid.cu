@@ -61,7 +61,7 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
   }
 }
 
-template <int D, bool RATE, bool SMALL>
+template <int D, bool RATE, bool SMALL, bool FLOOR>
 __global__ void __launch_bounds__(32 * kFluidWarps, RATE ? 3 : 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
@@ -182,6 +182,11 @@ fluid_sweep_kernel(FluidArgs a) {
       const int po = t - 3;  // position of the finished cell
       if (active && po >= s0 && po < s1) {
         const int cell = base + po * sD;  // po is inside [s0, s1)
+        if (FLOOR) {  // optional: raise e so that p >= p_floor (b_c of this cell is bc3)
+          const float kin = 0.5f * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) / o[0];
+          const float mag = 0.5f * (bc3[0] * bc3[0] + bc3[1] * bc3[1] + bc3[2] * bc3[2]);
+          o[4] = fmaxf(o[4], kin + mag + a.p_floor / (gamma - 1.f));
+        }
         o_rho[cell] = o[0];
         o_md[cell] = o[1];
         o_m1[cell] = o[2];
@@ -194,7 +199,7 @@ fluid_sweep_kernel(FluidArgs a) {
           rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, G.box.n));
         }
       }
-      if (RATE) {  // window of b_c: bc2 = b_c(t-1), bc3 = b_c(t-2) for the next step
+      if (RATE || FLOOR) {  // window of b_c: bc2 = b_c(t-1), bc3 = b_c(t-2) for the next step
         bc3[0] = bc2[0]; bc3[1] = bc2[1]; bc3[2] = bc2[2];
         bc2[0] = bprev0; bc2[1] = bprev1; bc2[2] = bprev2;
       }
@@ -219,10 +224,16 @@ cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s
   // box of the launch (the host passes the smallest extent in a.box)
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
   const bool small = a.box.n[axis] < 16;
-#define FLUID_CASE(DD, RR)                                                        \
-  if (axis == DD && rate == RR) {                                                 \
-    if (small) fluid_sweep_kernel<DD, RR, true><<<grid, block, 0, s>>>(a);        \
-    else fluid_sweep_kernel<DD, RR, false><<<grid, block, 0, s>>>(a);             \
+  const bool floor = a.p_floor > 0.f;
+#define FLUID_CASE(DD, RR)                                                              \
+  if (axis == DD && rate == RR) {                                                       \
+    if (floor) {                                                                        \
+      if (small) fluid_sweep_kernel<DD, RR, true, true><<<grid, block, 0, s>>>(a);      \
+      else fluid_sweep_kernel<DD, RR, false, true><<<grid, block, 0, s>>>(a);           \
+    } else {                                                                            \
+      if (small) fluid_sweep_kernel<DD, RR, true, false><<<grid, block, 0, s>>>(a);     \
+      else fluid_sweep_kernel<DD, RR, false, false><<<grid, block, 0, s>>>(a);          \
+    }                                                                                   \
   }
   FLUID_CASE(0, false) FLUID_CASE(0, true) FLUID_CASE(1, false) FLUID_CASE(1, true)
   FLUID_CASE(2, false) FLUID_CASE(2, true)

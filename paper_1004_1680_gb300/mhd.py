@@ -44,6 +44,8 @@ SIGNATURES = {
     "mhd_sweep": (_I, [_P, _I, _I, _D]),
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
+    "mhd_set_pressure_floor": (_I, [_P, _D]),
+    "mhd_ens_set_pressure_floor": (_I, [_P, _D]),
     "mhd_diagnostics": (_I, [_P, _DP]),
     "mhd_profile": (_I, [_P, _I]),
     "mhd_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_int), _DP]),
@@ -189,6 +191,10 @@ class Box:
     def set_segments(self, sx: int = 0, sy: int = 0, sz: int = 0):
         _check(self.lib.mhd_set_segments(self.h, int(sx), int(sy), int(sz)))
 
+    def set_pressure_floor(self, p_floor: float):
+        """Optional floor on the gas pressure after fluid sweeps (0 = off)."""
+        _check(self.lib.mhd_set_pressure_floor(self.h, float(p_floor)))
+
     def set_xpath(self, mode: int):
         """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic."""
         _check(self.lib.mhd_set_xpath(self.h, int(mode)))
@@ -268,10 +274,21 @@ class Ensemble:
         _check(self.lib.mhd_ens_cfl_dt(self.h, cfl, out))
         return np.array(out[:])
 
+    def cfl_dt_safe(self, cfl: float = 0.7) -> np.ndarray:
+        """Like cfl_dt, but invalid boxes give 0 instead of raising."""
+        out = (ctypes.c_double * len(self.dims))()
+        rc = self.lib.mhd_ens_cfl_dt(self.h, cfl, out)
+        if rc not in (MHD_OK, MHD_E_STATE):
+            _check(rc)
+        return np.array(out[:])
+
     def diagnostics(self) -> np.ndarray:
         out = (ctypes.c_double * (10 * len(self.dims)))()
         _check(self.lib.mhd_ens_diagnostics(self.h, out))
         return np.array(out[:]).reshape(len(self.dims), 10)
+
+    def set_pressure_floor(self, p_floor: float):
+        _check(self.lib.mhd_ens_set_pressure_floor(self.h, float(p_floor)))
 
     def set_tuning(self, xpath: int, segdiv: int):
         _check(self.lib.mhd_ens_set_tuning(self.h, int(xpath), int(segdiv)))

@@ -400,6 +400,42 @@ def test_one_step_reach_and_sub_block_equivalence(oracle_lib):
 
 
 # --------------------------------------------------------------------------
+# optional pressure floor (not in the paper; off by default)
+
+def test_without_floor_strong_fields_lose_positivity_and_floor_holds(oracle_lib):
+    """A strongly magnetised supersonic box (beta 0.35, Mach 1) reaches p <= 0
+    within a few steps with the paper's scheme (no floor); with a floor of
+    1e-3 the pressure after every step is >= the floor, mass and momentum are
+    still conserved, and energy only grows (the floor adds energy)."""
+    sp = ic.ensemble_specs(256, seed=2024)[8]
+    st = ic.turbulence(sp["dims"], seed=sp["seed"], mach=sp["mach"], beta=sp["beta"],
+                       dtype=torch.float64)
+    s = st.numpy().copy()
+    failed = False
+    for _ in range(10):
+        oracle.step(s, oracle.cfl_dt(s, G, 0.7), G)
+        if not (oracle.diagnostics(s, G)[9] > 0):
+            failed = True
+            break
+    assert failed
+    try:
+        oracle.set_pressure_floor(1e-3)
+        s = st.numpy().copy()
+        d0 = oracle.diagnostics(s, G)
+        absm = np.sum(np.abs(s[1:4]))
+        for _ in range(10):
+            oracle.step(s, oracle.cfl_dt(s, G, 0.7), G)
+            assert np.min(oracle.pressure(s, G)) >= 1e-3 * (1 - 1e-9)
+        d1 = oracle.diagnostics(s, G)
+        assert abs(d1[0] - d0[0]) / d0[0] < 1e-13
+        for q in (1, 2, 3):
+            assert abs(d1[q] - d0[q]) / absm < 1e-13
+        assert d1[4] >= d0[4] * (1 - 1e-13)
+    finally:
+        oracle.set_pressure_floor(0.0)
+
+
+# --------------------------------------------------------------------------
 # diagnostics and restriction (plain definitions)
 
 def test_diagnostics_definitions(oracle_lib):
