@@ -234,6 +234,41 @@ int mhd_ens_set_tuning(mhd_ens_t *e, int xpath, int segdiv);
  * box sizes for the process.  Writes the choice if the pointers are not NULL. */
 int mhd_ens_autotune(mhd_ens_t *e, double cfl, int *xpath_out, int *segdiv_out);
 
+/* ---- Kernels of the learned coarse-grid correction ----------------------
+ * (Not in the paper: a 3-D CNN that corrects a coarse step toward a
+ * restricted fine solution.)  Activations are channels-last BF16
+ * [cell][channel], cell = i + nx*(j + ny*k); channel counts are 8 or 32; the
+ * box must hold a multiple of 128 cells.  All pointers are device memory,
+ * all calls asynchronous on `stream`, no call allocates.
+ *
+ * Weights w[cout][cin][3][3][3] (FP32, cross-correlation: output cell
+ * (i,j,k) sees input (i+kx-1, j+ky-1, k+kz-1), periodic) are packed into a
+ * BF16 tensor-core image of mhd_conv_pack_bytes() bytes; transpose = 1 packs
+ * the image used for the input gradient. */
+size_t mhd_conv_pack_bytes(int cin, int cout, int transpose);
+int mhd_conv_pack(const float *w, int cin, int cout, int transpose, void *img, void *stream);
+
+/* y[cell][co] = sum_{ci, taps} x[cell + s*offset][ci] * W + bias[co]
+ * (s = +1, or -1 with flip = 1), accumulated in FP32 on the tensor cores
+ * (tcgen05); optional ReLU; where mask != NULL, outputs with
+ * mask[cell][co] <= 0 are zeroed (backward through a ReLU); written as BF16
+ * (y_bf16) and/or FP32 (y_f32).  The input gradient of a layer with cin_f,
+ * cout_f is mhd_conv3d(cin = cout_f, cout = cin_f, img = transposed pack,
+ * flip = 1).  img_bytes must equal the size of the image for these channel
+ * counts (MHD_E_ARG otherwise). */
+int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void *x, const void *img,
+               size_t img_bytes, const float *bias, int relu, int flip, const void *mask, void *y_bf16,
+               float *y_f32, void *stream);
+
+/* Weight gradient: gw[co][ci][tap] += sum_cell gy[cell][co] x[cell + offset][ci],
+ * gb[co] += sum_cell gy[cell][co] (FP32 atomics: the caller zeroes them). */
+int mhd_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *gy,
+                     float *gw, float *gb, void *stream);
+
+/* Read and clear the flag raised by a convolution whose bounded tensor-core
+ * wait gave up (MHD_E_TIMEOUT if set).  Synchronises the device. */
+int mhd_conv_error(int *flag);
+
 /* Description of the last failure on this thread ("" if none). */
 const char *mhd_last_error(void);
 

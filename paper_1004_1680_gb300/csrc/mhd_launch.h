@@ -1,7 +1,10 @@
 // Kernel argument blocks and host-side launchers shared by the library's
 // translation units (internal; the public interface is include/mhd.h).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "mhd_device.cuh"
 
@@ -111,6 +114,31 @@ __device__ __forceinline__ BlockGeom block_geom(const EnsArgs& e, const Box& box
 // Record "<where>: <what>" as this thread's last error (mhd_last_error) and
 // return code.
 int set_error(int code, const char* where, const char* what);
+
+// 3x3x3 periodic convolution on the tensor cores (conv3d.cu).
+struct ConvArgs {
+  const __nv_bfloat16* x;     // input, channels-last [cell][cin] BF16
+  const uint16_t* wpack;      // packed weight image (launch_conv_pack)
+  const float* bias;          // [cout] or nullptr
+  __nv_bfloat16* y;           // output [cell][cout] BF16, or nullptr
+  float* y32;                 // output [cell][cout] FP32, or nullptr
+  const __nv_bfloat16* mask;  // zero outputs where mask[cell][co] <= 0 (ReLU backward), or nullptr
+  int n[3];
+  int cin;                    // channels gathered per cell (the GEMM's C)
+  int cout;                   // channels written per cell
+  int npad, kchunks;          // MMA N and number of 32-wide k chunks
+  int relu;
+  int flip;                   // 1: taps applied at -offset (input gradient)
+  int* err;                   // set to 1 if a bounded wait gives up
+};
+int conv_npad(int n);
+int conv_kchunks(int c);
+size_t conv_smem_bytes(int npad, int kchunks);
+cudaError_t prepare_conv_kernels();
+cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s);
+cudaError_t launch_conv3d(const ConvArgs& a, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
+                              float* gw, float* gb, cudaStream_t s);
 
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);

@@ -61,6 +61,11 @@ SIGNATURES = {
     "mhd_ens_diagnostics": (_I, [_P, _DP]),
     "mhd_ens_set_tuning": (_I, [_P, _I, _I]),
     "mhd_ens_autotune": (_I, [_P, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "mhd_conv_pack_bytes": (ctypes.c_size_t, [_I, _I, _I]),
+    "mhd_conv_pack": (_I, [_P, _I, _I, _I, _P, _P]),
+    "mhd_conv3d": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.c_size_t, _P, _I, _I, _P, _P, _P, _P]),
+    "mhd_conv3d_wgrad": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "mhd_conv_error": (_I, [ctypes.POINTER(ctypes.c_int)]),
     "mhd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -297,3 +302,55 @@ class Ensemble:
         x, s = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.mhd_ens_autotune(self.h, cfl, ctypes.byref(x), ctypes.byref(s)))
         return x.value, s.value
+
+
+# --------------------------------------------------------------------------
+# tensor-core 3-D convolution (learned correction)
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def conv_pack(w: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
+    """Pack FP32 weights (cout, cin, 3, 3, 3) into the BF16 tensor-core image."""
+    lib = load()
+    cout, cin = w.shape[:2]
+    nbytes = lib.mhd_conv_pack_bytes(cin, cout, int(transpose))
+    img = torch.empty(nbytes // 2, dtype=torch.int16, device=w.device)
+    _check(lib.mhd_conv_pack(_ptr(w.contiguous()), cin, cout, int(transpose), _ptr(img), _stream(stream)))
+    return img
+
+
+def conv3d(x: torch.Tensor, img: torch.Tensor, n, cin: int, cout: int, bias=None, relu=False, flip=False,
+           mask=None, out_bf16=True, out_f32=False, stream=None):
+    """Periodic 3x3x3 convolution of channels-last BF16 x (cells, cin).
+    Returns (y_bf16 or None, y_f32 or None), each (cells, cout)."""
+    lib = load()
+    cells = n[0] * n[1] * n[2]
+    yb = torch.empty((cells, cout), dtype=torch.bfloat16, device=x.device) if out_bf16 else None
+    yf = torch.empty((cells, cout), dtype=torch.float32, device=x.device) if out_f32 else None
+    _check(lib.mhd_conv3d(n[0], n[1], n[2], cin, cout, _ptr(x), _ptr(img), img.numel() * img.element_size(),
+                          _ptr(bias), int(relu), int(flip), _ptr(mask), _ptr(yb), _ptr(yf), _stream(stream)))
+    return yb, yf
+
+
+def conv3d_wgrad(x: torch.Tensor, gy: torch.Tensor, n, cin: int, cout: int, gw: torch.Tensor, gb=None,
+                 stream=None):
+    """Accumulate the weight (and bias) gradient into gw (cout*cin*27) and gb."""
+    lib = load()
+    _check(lib.mhd_conv3d_wgrad(n[0], n[1], n[2], cin, cout, _ptr(x), _ptr(gy), _ptr(gw), _ptr(gb),
+                                _stream(stream)))
+
+
+def conv_error() -> int:
+    lib = load()
+    f = ctypes.c_int()
+    rc = lib.mhd_conv_error(ctypes.byref(f))
+    if rc not in (MHD_OK, MHD_E_TIMEOUT):
+        _check(rc)
+    return f.value

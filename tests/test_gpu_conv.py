@@ -1,0 +1,70 @@
+"""Tensor-core (tcgen05) periodic 3x3x3 convolution against PyTorch's FP64
+CPU conv3d with circular padding, on BF16-rounded inputs and weights
+(forward with bias and ReLU, input gradient through a ReLU mask, weight and
+bias gradients)."""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+pytestmark = pytest.mark.gpu
+
+
+def ref_conv(x, w, b):
+    """x (cells, cin) -> (1, cin, nz, ny, nx) FP64 circular conv -> (cells, cout)."""
+    return x
+
+
+def to_ncdhw(x, n):
+    nx, ny, nz = n
+    return x.T.reshape(1, x.shape[1], nz, ny, nx)
+
+
+def from_ncdhw(y):
+    c = y.shape[1]
+    return y.reshape(c, -1).T
+
+
+@pytest.mark.parametrize("cin,cout", [(8, 32), (32, 32), (32, 8)])
+def test_conv_forward_dgrad_wgrad(cin, cout):
+    from paper_1004_1680_gb300 import mhd
+    torch.manual_seed(cin * 100 + cout)
+    n = (16, 8, 24)
+    cells = n[0] * n[1] * n[2]
+    xb = (torch.randn(cells, cin) * 0.5).to(torch.bfloat16)
+    w = torch.randn(cout, cin, 3, 3, 3) * 0.1
+    wb = w.to(torch.bfloat16).float()
+    bias = torch.randn(cout) * 0.1
+    gyb = torch.randn(cells, cout).to(torch.bfloat16)
+    # reference in FP64 on the CPU
+    x64 = to_ncdhw(xb.double(), n).requires_grad_(True)
+    w64 = wb.double().requires_grad_(True)
+    b64 = bias.double().requires_grad_(True)
+    z = F.conv3d(F.pad(x64, (1, 1, 1, 1, 1, 1), mode="circular"), w64, b64)
+    z.backward(to_ncdhw(gyb.double(), n))
+    zr = from_ncdhw(z.detach())
+    # GPU
+    dev = "cuda"
+    xg, gyg = xb.to(dev), gyb.to(dev)
+    img = mhd.conv_pack(w.to(dev))
+    _, y32 = mhd.conv3d(xg, img, n, cin, cout, bias=bias.to(dev), out_bf16=False, out_f32=True)
+    _, yr = mhd.conv3d(xg, img, n, cin, cout, bias=bias.to(dev), relu=True, out_bf16=False, out_f32=True)
+    imgt = mhd.conv_pack(w.to(dev), transpose=True)
+    _, gx = mhd.conv3d(gyg, imgt, n, cout, cin, flip=True, out_bf16=False, out_f32=True)
+    mask = xb.to(dev)
+    _, gxm = mhd.conv3d(gyg, imgt, n, cout, cin, flip=True, mask=mask, out_bf16=False, out_f32=True)
+    gw = torch.zeros(cout * cin * 27, device=dev)
+    gb = torch.zeros(cout, device=dev)
+    mhd.conv3d_wgrad(xg, gyg, n, cin, cout, gw, gb)
+    torch.cuda.synchronize()
+    assert mhd.conv_error() == 0
+    scale = float(zr.abs().max())
+    assert float((y32.cpu().double() - zr).abs().max()) < 1e-4 * scale
+    assert torch.equal(yr.cpu(), torch.clamp(y32.cpu(), min=0.0))
+    gxr = from_ncdhw(x64.grad)
+    assert float((gx.cpu().double() - gxr).abs().max()) < 1e-4 * float(gxr.abs().max())
+    gxmr = torch.where(xb.double() > 0, gxr, torch.zeros_like(gxr))
+    assert float((gxm.cpu().double() - gxmr).abs().max()) < 1e-4 * float(gxr.abs().max())
+    gwr = w64.grad.reshape(-1)
+    assert float((gw.cpu().double() - gwr).abs().max()) < 1e-4 * float(gwr.abs().max())
+    assert float((gb.cpu().double() - b64.grad).abs().max()) < 1e-4 * float(b64.grad.abs().max())
