@@ -32,7 +32,7 @@ constexpr int kM = 128;       // cells per block (GEMM rows)
 constexpr int kKC = 32;       // k per staged chunk (two MMAs of K = 16)
 constexpr int kChunkBytes = kM * kKC * 2;  // 8 KiB
 constexpr uint32_t kTmemCols = 32;
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr long long kSpinLimit = 1LL << 22;  // about 0.5 s of polling
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
