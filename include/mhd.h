@@ -265,6 +265,49 @@ int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void *x, const v
 int mhd_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *gy,
                      float *gw, float *gb, void *stream);
 
+/* Restriction of a fine state (nx, ny, nz) to the grid coarser by r along
+ * every axis: cell quantities are r^3 block means, b_d the mean of the r^2
+ * fine faces tiling each coarse face (flux preserving: a divergence-free
+ * fine field restricts to a divergence-free coarse field). */
+int mhd_restrict(int nx, int ny, int nz, int r, const float *const fine[8], float *const coarse[8],
+                 void *stream);
+
+/* Network input: x[cell][q] = BF16((s_q[cell] - mu[q]) * inv_sigma[q]). */
+int mhd_cnn_normalize(int nx, int ny, int nz, const float *const s[8], const float mu[8],
+                      const float inv_sigma[8], void *x_bf16, void *stream);
+
+/* Network output y[cell][8] (FP32) -> correction d (8 SoA fields):
+ * d_q = scale[q] y_q for q < 5 with the box mean removed (conservation), and
+ * d_b = discrete curl of the edge potential A = scale[5] (y_5, y_6, y_7)
+ * (A_x on x-edges (i, j-1/2, k-1/2), A_y on (i-1/2, j, k-1/2), A_z on
+ * (i-1/2, j-1/2, k)), so div d_b = 0 up to rounding.  `sums` is 5 doubles
+ * of device scratch. */
+int mhd_cnn_project(int nx, int ny, int nz, const float *y, const float scale[6], float *const d[8],
+                    double *sums, void *stream);
+
+/* loss (device double) = sum_q weight[q] sum_cells (d_q - t_q)^2 and, if g
+ * is not NULL, g_q = 2 weight[q] (d_q - t_q). */
+int mhd_cnn_loss(int nx, int ny, int nz, const float *const d[8], const float *const t[8],
+                 const float weight[8], double *loss, float *const g[8], void *stream);
+
+/* Adjoint of mhd_cnn_project: the gradient with respect to y (BF16
+ * channels-last) of a loss whose gradient with respect to d is g. */
+int mhd_cnn_project_backward(int nx, int ny, int nz, const float *const g[8], const float scale[6],
+                             double *sums, void *gy_bf16, void *stream);
+
+/* Apply a correction d to a state s in place, keeping it physical: b += d_b
+ * (divergence-free, never scaled); the density correction is clipped at
+ * -rho/2; the cell correction (rho, m, e) is scaled by the largest of 1,
+ * 1/2, 1/4, 0 that keeps the thermal energy above half its uncorrected value,
+ * and if none does e is raised to that bound.  scratch: nx*ny*nz floats;
+ * nclip (device int, may be NULL) counts the cells where a limit acted. */
+int mhd_correct(int nx, int ny, int nz, float *const s[8], const float *const d[8], float *scratch,
+                int *nclip, void *stream);
+
+/* Adam step on `count` FP32 parameters (step counts from 1). */
+int mhd_adam(float *p, const float *g, float *m, float *v, int count, float lr, float beta1, float beta2,
+             float eps, int step, void *stream);
+
 /* Read and clear the flag raised by a convolution whose bounded tensor-core
  * wait gave up (MHD_E_TIMEOUT if set).  Synchronises the device. */
 int mhd_conv_error(int *flag);

@@ -66,6 +66,15 @@ SIGNATURES = {
     "mhd_conv3d": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.c_size_t, _P, _I, _I, _P, _P, _P, _P]),
     "mhd_conv3d_wgrad": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
     "mhd_conv_error": (_I, [ctypes.POINTER(ctypes.c_int)]),
+    "mhd_restrict": (_I, [_I, _I, _I, _I, _PP, _PP, _P]),
+    "mhd_cnn_normalize": (_I, [_I, _I, _I, _PP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                               _P, _P]),
+    "mhd_cnn_project": (_I, [_I, _I, _I, _P, ctypes.POINTER(ctypes.c_float), _PP, _P, _P]),
+    "mhd_cnn_loss": (_I, [_I, _I, _I, _PP, _PP, ctypes.POINTER(ctypes.c_float), _P, _PP, _P]),
+    "mhd_cnn_project_backward": (_I, [_I, _I, _I, _PP, ctypes.POINTER(ctypes.c_float), _P, _P, _P]),
+    "mhd_correct": (_I, [_I, _I, _I, _PP, _PP, _P, _P, _P]),
+    "mhd_adam": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I,
+                      _P]),
     "mhd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -354,3 +363,81 @@ def conv_error() -> int:
     if rc not in (MHD_OK, MHD_E_TIMEOUT):
         _check(rc)
     return f.value
+
+
+def _fields(t):
+    """8 field pointers of an (8, ...) tensor (None -> null array)."""
+    if t is None:
+        return ctypes.cast(0, _PP)
+    return _field_ptrs(t)
+
+
+def _floats(v):
+    v = [float(x) for x in v]
+    return (ctypes.c_float * len(v))(*v)
+
+
+def restrict(fine: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    """Restrict an (8, nz, ny, nx) FP32 CUDA state by r along every axis."""
+    lib = load()
+    nz, ny, nx = fine.shape[1:]
+    out = torch.empty((8, nz // r, ny // r, nx // r), dtype=torch.float32, device=fine.device)
+    _check(lib.mhd_restrict(nx, ny, nz, r, _fields(fine), _fields(out), _stream(stream)))
+    return out
+
+
+def cnn_normalize(state, mu, inv_sigma, out=None, stream=None):
+    lib = load()
+    nz, ny, nx = state.shape[1:]
+    if out is None:
+        out = torch.empty((nx * ny * nz, 8), dtype=torch.bfloat16, device=state.device)
+    _check(lib.mhd_cnn_normalize(nx, ny, nz, _fields(state), _floats(mu), _floats(inv_sigma), _ptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def cnn_project(y, n, scale, out=None, sums=None, stream=None):
+    lib = load()
+    nx, ny, nz = n
+    if out is None:
+        out = torch.empty((8, nz, ny, nx), dtype=torch.float32, device=y.device)
+    if sums is None:
+        sums = torch.empty(5, dtype=torch.float64, device=y.device)
+    _check(lib.mhd_cnn_project(nx, ny, nz, _ptr(y), _floats(scale), _fields(out), _ptr(sums), _stream(stream)))
+    return out
+
+
+def cnn_loss(d, t, weight, g=None, loss=None, stream=None):
+    lib = load()
+    nz, ny, nx = d.shape[1:]
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=d.device)
+    _check(lib.mhd_cnn_loss(nx, ny, nz, _fields(d), _fields(t), _floats(weight), _ptr(loss), _fields(g),
+                            _stream(stream)))
+    return loss
+
+
+def cnn_project_backward(g, scale, out=None, sums=None, stream=None):
+    lib = load()
+    nz, ny, nx = g.shape[1:]
+    if out is None:
+        out = torch.empty((nx * ny * nz, 8), dtype=torch.bfloat16, device=g.device)
+    if sums is None:
+        sums = torch.empty(5, dtype=torch.float64, device=g.device)
+    _check(lib.mhd_cnn_project_backward(nx, ny, nz, _fields(g), _floats(scale), _ptr(sums), _ptr(out),
+                                        _stream(stream)))
+    return out
+
+
+def correct(state, d, scratch=None, nclip=None, stream=None):
+    lib = load()
+    nz, ny, nx = state.shape[1:]
+    if scratch is None:
+        scratch = torch.empty(nx * ny * nz, dtype=torch.float32, device=state.device)
+    _check(lib.mhd_correct(nx, ny, nz, _fields(state), _fields(d), _ptr(scratch), _ptr(nclip), _stream(stream)))
+
+
+def adam(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    lib = load()
+    _check(lib.mhd_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), lr, beta1, beta2, eps, int(step),
+                        _stream(stream)))
