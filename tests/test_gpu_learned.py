@@ -45,7 +45,7 @@ def test_training_graph_against_fp64_autograd():
     torch.manual_seed(5)
     target = (torch.randn(8, n[2], n[1], n[0]) * 0.01).cuda()
     norm = learned.Norm(mu=[float(st[q].mean()) for q in range(8)],
-                        inv_sigma=[1.0 / float(st[q].std()) for q in range(8)],
+                        inv_sigma=[1.0 / max(float(st[q].std()), 1e-3) for q in range(8)],
                         out_scale=[0.01, 0.02, 0.02, 0.02, 0.05, 0.001],
                         loss_weight=[1.0 / cells] * 8)
     net = learned.CorrectionNet(seed=1, out_scale=1.0)
