@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100,
                    help="steps of the 256-box ensemble measurement (0: skip)")
+    p.add_argument("--learned-reps", type=int, default=20,
+                   help="timed applications of the 64^3 learned correction (0: skip)")
     return p.parse_args()
 
 
@@ -180,6 +182,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed alone: measured burst, else fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16 burst"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback bf16 burst"
+
+
 def ensemble_leg(args):
     """256 independent periodic boxes, per-axis sizes drawn from {32,48,64,96}
     (rng 2024), box b seeded 1000+b with its own rms Mach and beta; one batched
@@ -220,6 +231,69 @@ def ensemble_leg(args):
            "invalid_boxes_after_warmup": invalid_warm,
            "launch": "one CUDA graph per run; 1 launch per sweep for all boxes"}
     ens.close()
+    return out
+
+
+def learned_leg(args):
+    """Kernels of the learned coarse-grid correction on a 64^3 box: each
+    tensor-core convolution layer (forward, 2 * 27 * cin * cout flop per cell),
+    and one whole correction (normalise, 4 layers, projection, clipped
+    correction).  Weights are a random initialisation of the architecture;
+    the activations (<= 16.8 MB) are L2-resident, so the layers are timed
+    back to back."""
+    import torch
+
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    from paper_1004_1680_gb300 import learned, mhd
+    n = (64, 64, 64)
+    cells = n[0] * n[1] * n[2]
+    st = ic.turbulence(n, seed=args.seed, device="cuda", dtype=torch.float32)
+    net = learned.CorrectionNet(seed=0)
+    norm = learned.Norm(mu=[float(st[q].mean()) for q in range(8)],
+                        inv_sigma=[1.0 / max(float(st[q].std()), 1e-3) for q in range(8)],
+                        out_scale=[1e-3] * 5 + [1e-5], loss_weight=[1.0] * 8)
+    corr = learned.Corrector(net, norm, n)
+    mhd.cnn_normalize(st, norm.mu, norm.inv_sigma, out=corr.x)
+    stream = torch.cuda.current_stream()
+    layer_ms, layer_flop = [], []
+    h = corr.x
+    for li, (ci, co) in enumerate(learned.LAYERS):
+        last = li == len(learned.LAYERS) - 1
+        run = lambda: mhd.conv3d(h, net.img[li], n, ci, co, bias=net.b[li], relu=not last,  # noqa: E731
+                                 out_bf16=not last, out_f32=last)
+        for _ in range(3):
+            out = run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.learned_reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        layer_ms.append(e0.elapsed_time(e1) / args.learned_reps)
+        layer_flop.append(2.0 * 27 * ci * co * cells)
+        h = out[1] if last else out[0]
+    work = st.clone()
+    for _ in range(3):
+        corr.apply(work, corr.predict(st))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.learned_reps):
+        corr.apply(work, corr.predict(st))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if mhd.conv_error():
+        raise RuntimeError("a tensor-core wait gave up")
+    peak, peak_kind = bf16_peak()
+    tf = sum(layer_flop) / (sum(layer_ms) / 1e3) / 1e12
+    out = {"grid": "64^3", "layers": [f"{ci}->{co}" for ci, co in learned.LAYERS],
+           "layer_ms": layer_ms,
+           "layer_tflops": [f / (t / 1e3) / 1e12 for f, t in zip(layer_flop, layer_ms)],
+           "conv_flop_per_application": sum(layer_flop),
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                        "frac": tf / peak, "kernel": "conv3d (tcgen05 implicit GEMM)",
+                        "peak_kind": peak_kind},
+           "correction_ms": e0.elapsed_time(e1) / args.learned_reps,
+           "reps": args.learned_reps}
     return out
 
 
@@ -356,6 +430,10 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
         ens_out = ensemble_leg(args)
 
+    learned_out = None
+    if args.learned_reps > 0:
+        learned_out = learned_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, args.seed, args.cfl)
@@ -382,7 +460,8 @@ def run_ours(args, rank, world, local):
                "clocks": clk,
                "e2e": e2e,
                "cpu_baseline": cpu,
-               "ensemble": ens_out}
+               "ensemble": ens_out,
+               "learned_correction": learned_out}
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -7,7 +7,9 @@ package imports nothing from it.
 The arithmetic lives in ``mhd_oracle.c`` (plain loops, FP64, periodic
 indexing); this module compiles it with gcc, loads it with ctypes and adds the
 FP64 diagnostics (exactly rounded sums with ``math.fsum``) and the coarse-grid
-restriction, both written from their plain definitions.
+restriction, both written from their plain definitions.  ``cnn.py`` is the
+FP64 oracle of the learned coarse-grid correction (network, projection, loss,
+clipped correction, Adam), with PyTorch CPU operations as library primitives.
 
 State arrays are numpy float64 of shape (8, nz, ny, nx): fields rho, m_x, m_y,
 m_z, e, b_x, b_y, b_z; b_d[k, j, i] lives on the low face of cell (i, j, k)

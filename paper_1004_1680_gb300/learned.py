@@ -108,13 +108,15 @@ class Corrector:
         self.scratch = torch.empty(cells, dtype=torch.float32, device=dev)
 
     def predict(self, state: torch.Tensor) -> torch.Tensor:
+        """Correction for the coarse step that starts from `state` (the
+        network input is the state before the step, as in the training pairs)."""
         mhd.cnn_normalize(state, self.norm.mu, self.norm.inv_sigma, out=self.x)
         y, _ = self.net.forward(self.x, self.n)
         return mhd.cnn_project(y, self.n, self.norm.out_scale, out=self.d, sums=self.sums)
 
-    def apply(self, state: torch.Tensor, nclip=None):
-        d = self.predict(state)
-        mhd.correct(state, d, scratch=self.scratch, nclip=nclip)
+    def apply(self, stepped: torch.Tensor, d: torch.Tensor, nclip=None):
+        """Add a predicted correction to the state after the coarse step."""
+        mhd.correct(stepped, d, scratch=self.scratch, nclip=nclip)
 
 
 # --------------------------------------------------------------------------
@@ -186,6 +188,7 @@ def train(inputs, targets, norm: Norm, epochs: int, lr: float = 1e-3, seed: int 
     history = []
     t0 = time.perf_counter()
     for ep in range(epochs):
+        lr_ep = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * ep / max(1, epochs))))   # cosine decay
         order = rng.permutation(P)
         tot = 0.0
         for i in order:
@@ -195,7 +198,7 @@ def train(inputs, targets, norm: Norm, epochs: int, lr: float = 1e-3, seed: int 
             mhd.cnn_loss(d, targets[i], norm.loss_weight, g=g, loss=loss)
             mhd.cnn_project_backward(g, norm.out_scale, out=gy, sums=sums)
             net.backward(gy, acts, n)
-            net.adam(lr)
+            net.adam(lr_ep)
             tot += float(loss.item()) if (i == order[-1]) else 0.0
         # epoch loss on a fixed subset (no update)
         ev = 0.0
@@ -249,10 +252,13 @@ def evaluate(corrector: Corrector | None, seed: int, nsteps: int = 200, every: i
                 for _ in range(kk):
                     b.step(dt / kk)
             elif k == "learned64":
+                if corrector is not None:
+                    b.get_state(out=lstate)
+                    d = corrector.predict(lstate)
                 b.step(dt)
                 if corrector is not None:
                     b.get_state(out=lstate)
-                    corrector.apply(lstate, nclip=nclip)
+                    corrector.apply(lstate, d, nclip=nclip)
                     b.set_state(lstate)   # (its own time and CFL rate are not used)
             else:
                 b.step(dt)

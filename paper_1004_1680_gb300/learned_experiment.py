@@ -61,10 +61,12 @@ def main(argv=None):
     mean_err = {r: float(np.mean([x[0][r].mean() for x in res])) for r in runs}
     final_err = {r: float(np.mean([x[0][r][-1].mean() for x in res])) for r in runs}
     per_field = {r: np.mean([x[0][r].mean(axis=0) for x in res], axis=0).tolist() for r in runs}
+    curve = {r: np.mean([x[0][r].mean(axis=1) for x in res], axis=0).tolist() for r in runs}
     gpu = {r: float(np.mean([x[1][r] for x in res])) for r in runs + ["ref"]}
     out = {"train_pairs": args.train_seeds * args.steps_per_seed, "epochs": args.epochs, "train_s": train_s,
            "loss_history": hist, "eval_seeds": args.eval_seeds, "eval_steps": args.eval_steps,
            "mean_nrmse": mean_err, "final_nrmse": final_err, "per_field_nrmse": per_field,
+           "nrmse_every_20_steps": curve,
            "gpu_ms_per_run": gpu, "clipped_cells": [x[3] for x in res],
            "claim_lower_error_than_plain128": mean_err["learned64"] < mean_err["plain128"],
            "claim_less_gpu_time_than_plain128": gpu["learned64"] < gpu["plain128"]}
@@ -77,6 +79,10 @@ def main(argv=None):
     print("per-field mean NRMSE (rho, m_x, m_y, m_z, e, b_x, b_y, b_z):")
     for r in runs:
         print(f"  {r}: " + ", ".join(f"{v:.4f}" for v in per_field[r]))
+    print()
+    print("mean NRMSE after 20, 40, ... coarse steps:")
+    for r in runs:
+        print(f"  {r}: " + ", ".join(f"{v:.4f}" for v in curve[r]))
     print(f"training: {out['train_pairs']} pairs x {args.epochs} epochs in {train_s:.1f} s; "
           f"loss history {[round(h, 4) for h in hist]}")
     print(f"claim (learned 64^3 error < plain 128^3): {out['claim_lower_error_than_plain128']}; "

@@ -2,39 +2,18 @@
 output and every weight/bias gradient of the full training graph (network,
 conservative divergence-free projection, weighted MSE) against PyTorch FP64
 autograd of the same graph (circular conv3d as the library oracle), with the
-same BF16 rounding of weights and activations."""
-import numpy as np
+same BF16 rounding of weights and activations (oracle/cnn.py)."""
 import pytest
 import torch
-import torch.nn.functional as F
 
+from oracle import cnn
 from paper_1004_1680_gb300 import initial_conditions as ic
 
 pytestmark = pytest.mark.gpu
 
 
-def torch_pipeline(x_cells, W, b, n, scale, weight, target):
-    """FP64 reference of forward + projection + loss; x_cells (cells, 8)."""
-    nx, ny, nz = n
-    h = x_cells.T.reshape(1, 8, nz, ny, nx)
-    L = len(W)
-    for li in range(L):
-        z = F.conv3d(F.pad(h, (1, 1, 1, 1, 1, 1), mode="circular"), W[li], b[li])
-        if li < L - 1:
-            h = torch.relu(z).to(torch.bfloat16).to(torch.float64)   # BF16 activations as on the GPU
-        else:
-            h = z
-    y = h[0]                                                       # (8, nz, ny, nx)
-    d = [scale[q] * y[q] for q in range(5)]
-    d = [dq - dq.mean() for dq in d]
-    A = [scale[5] * y[5 + c] for c in range(3)]
-    up = lambda a, ax: torch.roll(a, shifts=-1, dims=ax)         # +1 along numpy axis
-    bx = (up(A[2], 1) - A[2]) * ny - (up(A[1], 0) - A[1]) * nz
-    by = (up(A[0], 0) - A[0]) * nz - (up(A[2], 2) - A[2]) * nx
-    bz = (up(A[1], 2) - A[1]) * nx - (up(A[0], 1) - A[0]) * ny
-    d = torch.stack(d + [bx, by, bz])
-    loss = sum(weight[q] * ((d[q] - target[q]) ** 2).sum() for q in range(8))
-    return y, d, loss
+def bf16_round(h):
+    return h.to(torch.bfloat16).to(torch.float64)     # BF16 activations as on the GPU
 
 
 def test_training_graph_against_fp64_autograd():
@@ -64,16 +43,22 @@ def test_training_graph_against_fp64_autograd():
     x64 = corr.x.cpu().double()
     W = [w.to(torch.bfloat16).double().cpu().requires_grad_(True) for w in net.W]
     b = [bb.double().cpu().requires_grad_(True) for bb in net.b]
-    yr, dr, lr = torch_pipeline(x64, W, b, n, norm.out_scale, norm.loss_weight, target.cpu().double())
+    yr, dr, lr = cnn.training_graph(x64.T.reshape(8, n[2], n[1], n[0]), W, b, norm.out_scale, norm.loss_weight,
+                                    target.cpu().double(), act_round=bf16_round)
     lr.backward()
     yg = y.cpu().double().T.reshape(8, n[2], n[1], n[0])
-    assert float((yg - yr.detach()).abs().max()) < 2e-2 * float(yr.abs().max())
+    yr = yr.detach()
+    assert float((yg - yr).abs().max()) < 2e-2 * float(yr.abs().max())
     assert float(loss.item()) == pytest.approx(float(lr.item()), rel=5e-2)
     for li in range(len(W)):
         gw, gwr = net.grads[li].cpu().double(), W[li].grad
         assert float((gw - gwr).abs().max()) < 5e-2 * float(gwr.abs().max()), li
+        # the last layer's bias gradient is analytically zero (the mean removal
+        # cancels a constant cell correction, a constant potential has no curl):
+        # compare against the layer's weight-gradient scale as well
         gb, gbr = net.grads[len(W) + li].cpu().double(), b[li].grad
-        assert float((gb - gbr).abs().max()) < 5e-2 * float(gbr.abs().max()) + 1e-12, li
+        tol = 5e-2 * float(gbr.abs().max()) + 1e-3 * float(gwr.abs().max())
+        assert float((gb - gbr).abs().max()) < tol, li
 
 
 def test_training_reduces_loss_on_solver_pairs():
