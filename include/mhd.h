@@ -237,9 +237,10 @@ int mhd_ens_autotune(mhd_ens_t *e, double cfl, int *xpath_out, int *segdiv_out);
 /* ---- Kernels of the learned coarse-grid correction ----------------------
  * (Not in the paper: a 3-D CNN that corrects a coarse step toward a
  * restricted fine solution.)  Activations are channels-last BF16
- * [cell][channel], cell = i + nx*(j + ny*k); channel counts are 8 or 32; the
- * box must hold a multiple of 128 cells.  All pointers are device memory,
- * all calls asynchronous on `stream`, no call allocates.
+ * [cell][channel], cell = i + nx*(j + ny*k); channel counts are 8 or 32.
+ * mhd_conv3d needs nx % 8 == 0 and ny % 16 == 0 (tiles of 8 x 16 x 1
+ * cells), mhd_conv3d_wgrad a multiple of 64 cells.  All pointers are device
+ * memory, all calls asynchronous on `stream`, no call allocates.
  *
  * Weights w[cout][cin][3][3][3] (FP32, cross-correlation: output cell
  * (i,j,k) sees input (i+kx-1, j+ky-1, k+kz-1), periodic) are packed into a

@@ -1,26 +1,33 @@
 // Periodic 3x3x3 convolution as an implicit GEMM on the 5th-generation tensor
 // cores (tcgen05), for the learned coarse-grid correction network.
 //
-// GEMM view: D[cell, n] = sum_k A[cell, k] B[n, k], k = tap * C + c over the
-// 27 taps of the stencil and the C input channels.  A is never materialised:
-// for each chunk of 32 k-values a block of 128 threads gathers the shifted
-// input rows of its 128 cells (channels-last BF16, periodic wrap) into shared
-// memory in the canonical K-major layout (8-row x 16-byte core matrices), one
-// elected thread issues two tcgen05.mma (M = 128, K = 16) into an FP32
-// accumulator in tensor memory, and a tcgen05.commit arrives on an mbarrier
-// once the tensor core has read the chunk (two chunk buffers alternate).  B
-// (the weights, packed once per call by conv_pack) sits in shared memory for
-// the whole block.  The epilogue reads the accumulator with tcgen05.ld, adds
-// the bias, applies ReLU or a gradient mask, and stores BF16 and/or FP32.
+// GEMM view: D[cell, o] = sum_k A[cell, k] W[o, k], k = (tap, channel) over
+// the 27 taps and the cin input channels (channels-last BF16 activations).
+// A is never materialised.  A block owns a tile of 8 x TY x 1 cells (TY = 32:
+// two 128-row accumulators; 16: one) and copies the tile's halo, (8+2) x
+// (TY+2) x 3 cells, once into shared memory with cp.async, stored as one plane
+// per 8-channel group (16 bytes per cell).  In that layout the canonical
+// K-major core matrix of 8 GEMM rows x 8 channels is 8 consecutive halo cells
+// along x, so the operand of tap t is the same halo addressed from a shifted
+// start: every tap is one descriptor offset, with no per-tap gather.  The
+// weights (packed once by conv_pack) stay in shared memory for the block's
+// lifetime; blocks are persistent and prefetch the next tile's halo into a
+// second buffer while the tensor core works.  Per tile, one thread per
+// accumulator issues its 27 x (cin / 16) tcgen05.mma (M = 128, N = 32 or 16,
+// K = 16; BF16 in, FP32 in TMEM) and a tcgen05.commit onto a shared
+// mbarrier.  The epilogue reads TMEM with tcgen05.ld, adds the bias, applies
+// ReLU (forward) or the ReLU mask of the saved activation (input gradient),
+// and writes BF16 and/or FP32 with 16-byte stores.
 //
-// The same kernel computes the input gradient (dgrad) with the taps flipped
-// and the weights packed transposed.
+// The input gradient is the same kernel with mirrored taps and the weights
+// packed transposed.
 //
 // Every mbarrier wait is bounded: on timeout the block records an error in
 // *err, waits (bounded) once more, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "mhd_launch.h"
 
@@ -28,10 +35,22 @@ namespace mhd {
 
 namespace {
 
-constexpr int kM = 128;       // cells per block (GEMM rows)
-constexpr int kKC = 32;       // k per staged chunk (two MMAs of K = 16)
-constexpr int kChunkBytes = kM * kKC * 2;  // 8 KiB
-constexpr uint32_t kTmemCols = 32;
+constexpr int kM = 128;       // GEMM rows per MMA (tile cells per accumulator)
+constexpr int kKC = 32;       // k per 32-wide chunk of the packed weight image
+constexpr int kTX = 8, kHX = kTX + 2, kHZ = 3;     // tile: 8 x TY x 1 cells, TY = 16 or 32
+
+// Halo of an 8 x TY x 1 tile: kHX x (TY + 2) x kHZ cells, one 16-byte channel
+// group per cell and plane, padded by 4 zeroed cells (read, times zero
+// weights, by the cin = 8 MMAs).
+template <int TY>
+struct Halo {
+  static constexpr int HY = TY + 2;
+  static constexpr int cells = kHX * HY * kHZ;      // 540 or 1020
+  static constexpr int plane_cells = cells + 4;
+  static constexpr int plane_bytes = plane_cells * 16;
+  static constexpr int rows = HY * kHZ;             // halo rows along x
+};
+constexpr uint32_t kTmemCols = 64;                 // two 32-column accumulators
 constexpr long long kSpinLimit = 1LL << 22;  // about 0.5 s of polling
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -78,29 +97,97 @@ __device__ __forceinline__ uint4 load16(const __nv_bfloat16* p) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 1) conv3d_tc_kernel(ConvArgs a) {
+__device__ __forceinline__ int wrap1(int i, int n) {  // i in [-1, n]
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Halo of a tile (the 8 x TY x 1 cells at (x0, y0, z0) and one cell around
+// them, periodic) into shared memory by asynchronous 16-byte copies: plane g
+// (channels 8g..8g+7), halo cell c at buf + g * plane_bytes + c * 16.  Warps
+// take whole halo rows (the y, z wrap is computed once per row); lanes take
+// the 16-byte pieces of a row.  One commit group.
+template <int G, int TY>
+__device__ __forceinline__ void load_halo(uint8_t* buf, const __nv_bfloat16* __restrict__ x, int x0, int y0, int z0,
+                                          int nx, int ny, int nz, int warp, int lane) {
+  using H = Halo<TY>;
+  constexpr int P = kHX * G;        // 16-byte pieces per halo row
+  constexpr int NW = TY / 4;        // warps per block (8 TY threads)
+  const uint32_t base = smem_addr(buf);
+  // this lane's pieces: (hx, g) and the wrapped x, fixed for the tile
+  const int l0 = lane, l1 = lane + 32;
+  const int xs0 = wrap1(x0 - 1 + l0 / G, nx), xs1 = wrap1(x0 - 1 + l1 / G, nx);
+  for (int r = warp; r < H::rows; r += NW) {
+    const int hy = r % H::HY, hz = r / H::HY;
+    const int row = nx * (wrap1(y0 - 1 + hy, ny) + ny * wrap1(z0 - 1 + hz, nz));
+    const int c = r * kHX;
+    if (l0 < P)
+      cp_async16(base + (l0 % G) * H::plane_bytes + (c + l0 / G) * 16,
+                 x + (size_t)(row + xs0) * (8 * G) + (l0 % G) * 8);
+    if (P > 32 && l1 < P)
+      cp_async16(base + (l1 % G) * H::plane_bytes + (c + l1 / G) * 16,
+                 x + (size_t)(row + xs1) * (8 * G) + (l1 % G) * 8);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// halo cell of output cell (0, 0) shifted by tap t = (kz * 3 + ky) * 3 + kx
+template <int TY>
+__host__ __device__ constexpr int tap_offset(int t) {
+  return ((t / 9) * Halo<TY>::HY + (t / 3) % 3) * kHX + t % 3;
+}
+
+// G = cin / 8 channel groups, tiles of 8 x TY x 1 cells (TY / 16 accumulators
+// of 128 rows).  Persistent: each block copies the weights once and loops
+// over tiles; the next tile's halo is copied (cp.async) into the second
+// buffer while the tensor core works on the current one.
+template <int G, int TY>
+__global__ void __launch_bounds__(8 * TY, 1) conv3d_tc_kernel(ConvArgs a) {
+  using H = Halo<TY>;
+  constexpr int NT = 8 * TY, NACC = TY / 16;
+  constexpr int kBuf = G * H::plane_bytes;  // one halo buffer
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int C = a.cin;           // input channels per cell (8 or 32)
   const int Kp = a.kchunks * kKC;
   const int bBytes = a.npad * Kp * 2;
   uint8_t* sB = smem;
-  uint8_t* sA = smem + ((bBytes + 1023) & ~1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 2 * kChunkBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint8_t* sH = smem + ((bBytes + 1023) & ~1023);  // two halo buffers
+  float* sBias = reinterpret_cast<float*>(sH + 2 * kBuf);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sBias + 32);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
 
-  // weights: a straight copy of the packed image
-  for (int i = tid; i < bBytes / 16; i += blockDim.x)
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tiles_x = nx / kTX, tiles_y = ny / TY;
+  const int ntiles = tiles_x * tiles_y * nz;
+  int tile = blockIdx.x;
+  if (tile < ntiles)
+    load_halo<G, TY>(sH, a.x, (tile % tiles_x) * kTX, ((tile / tiles_x) % tiles_y) * TY, tile / (tiles_x * tiles_y),
+                     nx, ny, nz, warp, lane);
+
+  // weights: a straight copy of the packed image, once per block
+  for (int i = tid; i < bBytes / 16; i += NT)
     reinterpret_cast<uint4*>(sB)[i] = __ldg(reinterpret_cast<const uint4*>(a.wpack) + i);
+  constexpr int kPad = H::plane_cells - H::cells;
+  for (int i = tid; i < 2 * G * kPad; i += NT)
+    *reinterpret_cast<uint4*>(sH + (i / kPad) * H::plane_bytes + (H::cells + i % kPad) * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 32) sBias[tid] = (a.bias && tid < a.cout) ? __ldg(a.bias + tid) : 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])) : "memory");
+  if (tid == 0) {  // one arrival per accumulator's issuing thread
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(NACC) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -109,67 +196,78 @@ __global__ void __launch_bounds__(128, 1) conv3d_tc_kernel(ConvArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // this thread's row: cell of the tile
-  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
-  const int cell = blockIdx.x * kM + tid;
-  const int x = cell % nx, y = (cell / nx) % ny, z = cell / (nx * ny);
-  const int sgn = a.flip ? -1 : 1;
   const uint32_t idesc = make_idesc(kM, a.npad);
-  const uint32_t sbo_a = (kKC / 8) * 128, sbo_b = (Kp / 8) * 128;
+  const uint32_t sbo_b = (Kp / 8) * 128;
+  const int co_n = a.cout;
   bool ok = true;
 
-  for (int c = 0; c < a.kchunks; c++) {
-    const int buf = c & 1;
-    if (c >= 2 && ok) ok = mbar_wait(smem_addr(&bars[buf]), ((c - 2) >> 1) & 1);
-    uint8_t* A = sA + buf * kChunkBytes;
-    // gather: 4 core matrices (8 k-values each) of this row
-    for (int j = 0; j < kKC / 8; j++) {
-      const int k = c * kKC + j * 8;
-      const int tap = k / C, ch = k % C;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (tap < 27) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int sx = (x + sgn * dx + nx) % nx, sy = (y + sgn * dy + ny) % ny, sz = (z + sgn * dz + nz) % nz;
-        const int src = sx + nx * (sy + ny * sz);
-        v = load16(a.x + (size_t)src * C + ch);
-      }
-      *reinterpret_cast<uint4*>(A + (tid >> 3) * sbo_a + j * 128 + (tid & 7) * 16) = v;
-    }
+  for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+    uint8_t* cur = sH + (it & 1) * kBuf;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0 && ok) {
+    // lane 0 of warp 4 q issues accumulator q's MMAs and commits them
+    if ((tid & 127) == 0 && ok) {
+      const int q = tid >> 7;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int s = 0; s < 2; s++) {
-        const uint64_t adesc = make_desc(smem_addr(A) + s * 256, 128, sbo_a);
-        const uint64_t bdesc = make_desc(smem_addr(sB) + (c * (kKC / 8) + s * 2) * 128, 128, sbo_b);
-        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-            : "memory");
+      // GEMM row m of accumulator q = tile cell (m % 8, 16 q + m / 8): the rows
+      // of a core matrix are 8 consecutive halo cells along x (16 bytes
+      // apart), 8-row groups are one halo row apart (SBO = kHX * 16); tap t
+      // reads the halo shifted by its offset (the mirrored tap for the input
+      // gradient).  Descriptor address fields are in 16-byte units, so shifts
+      // add to the descriptor.
+      const uint64_t a0 = make_desc(smem_addr(cur), G == 4 ? H::plane_bytes : 16, kHX * 16);
+      const uint32_t b_addr = smem_addr(sB);
+#pragma unroll
+      for (int t = 0; t < 27; t++) {
+        const int off = a.flip ? tap_offset<TY>(26 - t) : tap_offset<TY>(t);
+#pragma unroll
+        for (int h = 0; h < (G == 4 ? 2 : 1); h++) {
+          const uint64_t bdesc = (G == 4) ? make_desc(b_addr + (t * 4 + 2 * h) * 128, 128, sbo_b)
+                                          : make_desc(b_addr + t * 128, (27 - t) * 128, sbo_b);
+          const uint32_t acc = (t > 0 || h > 0) ? 1u : 0u;
+          // G = 4: k = 16 channels 16h..16h+15 (planes 2h, 2h+1); G = 1: the
+          // 8 channels of tap t, then 8 whose weights are the zero k-group 27
+          const uint64_t adesc =
+              a0 + (uint64_t)(off + q * (16 * kHX) + (G == 4 ? h * (2 * H::plane_bytes / 16) : 0));
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + q * 32),
+              "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+              : "memory");
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(&bars[buf]))
+                       smem_addr(bar))
                    : "memory");
     }
-  }
-  const int last = a.kchunks - 1;
-  if (ok) ok = mbar_wait(smem_addr(&bars[last & 1]), (last >> 1) & 1);
-  if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
-    // give in-flight tensor-core work a bounded chance to finish before freeing
-    mbar_wait(smem_addr(&bars[last & 1]), (last >> 1) & 1);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  ok = __syncthreads_and(ok);  // the epilogue's tcgen05.ld is warp-collective
+    // the other buffer was last read by the previous tile's MMAs, which completed
+    const int next = tile + gridDim.x;
+    if (next < ntiles)
+      load_halo<G, TY>(sH + ((it + 1) & 1) * kBuf, a.x, (next % tiles_x) * kTX, ((next / tiles_x) % tiles_y) * TY,
+                       next / (tiles_x * tiles_y), nx, ny, nz, warp, lane);
 
-  if (ok) {
-    // epilogue: row `tid` of the accumulator = TMEM lane tid, columns = channels
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    if (ok) ok = mbar_wait(smem_addr(bar), it & 1);
+    if (!ok) {
+      if ((tid & 127) == 0) atomicExch(a.err, 1);
+      // give in-flight tensor-core work a bounded chance to finish before freeing
+      mbar_wait(smem_addr(bar), it & 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok);  // the epilogue's tcgen05.ld is warp-collective
+    if (!ok) break;
+
+    // epilogue: warp w reads accumulator w / 4, TMEM lanes 32 (w % 4) ..; its
+    // lane holds GEMM row 32 (w % 4) + lane, columns = output channels
+    const int q = warp >> 2, row = 32 * (warp & 3) + lane;
+    const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * TY, z0 = tile / (tiles_x * tiles_y);
+    const int cell = (x0 + (row & 7)) + nx * ((y0 + 16 * q + (row >> 3)) + ny * z0);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + q * 32;
     float acc[32];
     uint32_t r[16];
-    for (int half = 0; half < a.npad / 16; half++) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      if (half >= a.npad / 16) break;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -179,20 +277,44 @@ __global__ void __launch_bounds__(128, 1) conv3d_tc_kernel(ConvArgs a) {
 #pragma unroll
       for (int i = 0; i < 16; i++) acc[half * 16 + i] = __uint_as_float(r[i]);
     }
-    const int co_n = a.cout;
-    for (int co = 0; co < co_n; co++) {
-      float v = acc[co] + (a.bias ? __ldg(a.bias + co) : 0.f);
-      if (a.relu) v = fmaxf(v, 0.f);
-      if (a.mask) v = (__bfloat162float(a.mask[(size_t)cell * co_n + co]) > 0.f) ? v : 0.f;
-      if (a.y) a.y[(size_t)cell * co_n + co] = __float2bfloat16_rn(v);
-      if (a.y32) a.y32[(size_t)cell * co_n + co] = v;
+    // 8 channels (16 bytes of BF16) at a time; cout is 8 or 32
+#pragma unroll
+    for (int c8 = 0; c8 < 4; c8++) {
+      if (c8 >= co_n / 8) break;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        v[i] = acc[c8 * 8 + i] + sBias[c8 * 8 + i];
+        if (a.relu) v[i] = fmaxf(v[i], 0.f);
+      }
+      if (a.mask) {
+        const uint4 mk = load16(a.mask + (size_t)cell * co_n + c8 * 8);
+        const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const float m = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mw[i / 2] >> (16 * (i & 1)))));
+          v[i] = m > 0.f ? v[i] : 0.f;
+        }
+      }
+      if (a.y)
+        *reinterpret_cast<uint4*>(a.y + (size_t)cell * co_n + c8 * 8) =
+            make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                       pack_bf16x2(v[6], v[7]));
+      if (a.y32) {
+        float4* o = reinterpret_cast<float4*>(a.y32 + (size_t)cell * co_n + c8 * 8);
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
     }
+    // TMEM read before the next tile's MMAs overwrite it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  (void)lane;
 }
 
 // Pack conv weights w[cout][cin][27] (FP32, PyTorch order, tap = (kz*3+ky)*3+kx)
@@ -282,14 +404,77 @@ cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, c
 
 int conv_npad(int n) { return n <= 16 ? 16 : 32; }
 int conv_kchunks(int c) { return (27 * c + kKC - 1) / kKC; }
-size_t conv_smem_bytes(int npad, int kchunks) {
+size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty) {
   const size_t b = (size_t)npad * kchunks * kKC * 2;
-  return ((b + 1023) & ~(size_t)1023) + 2 * kChunkBytes + 64;
+  const size_t plane = ty == 32 ? Halo<32>::plane_bytes : Halo<16>::plane_bytes;
+  return ((b + 1023) & ~(size_t)1023) + 2 * (size_t)(cin / 8) * plane + 32 * sizeof(float) + 64;
 }
 
+namespace {
+template <int G, int TY>
+cudaError_t prepare_one() {
+  cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<G, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)conv_smem_bytes(32, conv_kchunks(8 * G), 8 * G, TY));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv3d_tc_kernel<G, TY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+// Resident blocks per device for each kernel variant and shared-memory size,
+// found once: a launch then costs no device queries.
+constexpr int kCacheDevices = 64, kCacheSizes = 16;
+struct GridCache {
+  const void* fn[kCacheSizes];
+  size_t smem[kCacheSizes];
+  int blocks[kCacheSizes];
+  int used;
+};
+GridCache g_grid[kCacheDevices];
+std::mutex g_grid_lock;
+
+template <int G, int TY>
+cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(conv3d_tc_kernel<G, TY>);
+  const size_t smem = conv_smem_bytes(a.npad, a.kchunks, a.cin, TY);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kCacheDevices) return cudaErrorInvalidDevice;
+  int cap = 0;
+  {
+    std::lock_guard<std::mutex> g(g_grid_lock);
+    GridCache& c = g_grid[dev];
+    for (int i = 0; i < c.used && !cap; i++)
+      if (c.fn[i] == fn && c.smem[i] == smem) cap = c.blocks[i];
+    if (!cap) {
+      int sms = 0, per_sm = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3d_tc_kernel<G, TY>, 8 * TY, smem);
+      if (e != cudaSuccess) return e;
+      cap = sms * (per_sm > 0 ? per_sm : 1);
+      if (c.used < kCacheSizes) {
+        c.fn[c.used] = fn;
+        c.smem[c.used] = smem;
+        c.blocks[c.used] = cap;
+        c.used++;
+      }
+    }
+  }
+  const long long tiles = (long long)(a.n[0] / kTX) * (a.n[1] / TY) * a.n[2];
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+  conv3d_tc_kernel<G, TY><<<grid, 8 * TY, smem, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t prepare_conv_kernels() {
-  return cudaFuncSetAttribute(conv3d_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)conv_smem_bytes(32, conv_kchunks(32)));
+  cudaError_t e = prepare_one<4, 32>();
+  if (e == cudaSuccess) e = prepare_one<4, 16>();
+  if (e == cudaSuccess) e = prepare_one<1, 32>();
+  if (e == cudaSuccess) e = prepare_one<1, 16>();
+  return e;
 }
 
 cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s) {
@@ -300,10 +485,12 @@ cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, u
   return cudaGetLastError();
 }
 
+// Tiles of 8 x 32 x 1 cells (two accumulators, 8 warps) when ny allows,
+// else 8 x 16 x 1.
 cudaError_t launch_conv3d(const ConvArgs& a, cudaStream_t s) {
-  const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
-  conv3d_tc_kernel<<<(unsigned)(cells / kM), kM, conv_smem_bytes(a.npad, a.kchunks), s>>>(a);
-  return cudaGetLastError();
+  const bool wide = a.n[1] % 32 == 0;
+  if (a.cin == 32) return wide ? launch_variant<4, 32>(a, s) : launch_variant<4, 16>(a, s);
+  return wide ? launch_variant<1, 32>(a, s) : launch_variant<1, 16>(a, s);
 }
 
 }  // namespace mhd

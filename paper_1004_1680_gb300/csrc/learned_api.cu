@@ -3,6 +3,7 @@
 // gradient, weight packing, and the error flag of the bounded waits.
 #include <cuda_bf16.h>
 
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -61,10 +62,14 @@ int mhd_conv_pack(const float* w, int cin, int cout, int transpose, void* img, v
 int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void* x, const void* img, size_t img_bytes,
                const float* bias, int relu, int flip, const void* mask, void* y_bf16, float* y_f32, void* stream) {
   const long long cells = (long long)nx * ny * nz;
-  if (nx < 1 || ny < 1 || nz < 1 || cells % 128 || cells >= (1LL << 31) || !valid_channels(cin) ||
+  if (nx < 8 || ny < 16 || nz < 1 || nx % 8 || ny % 16 || cells >= (1LL << 31) || !valid_channels(cin) ||
       !valid_channels(cout) || !x || !img || (!y_bf16 && !y_f32))
     return mhd::set_error(MHD_E_ARG, "mhd_conv3d",
-                          "need cells % 128 == 0, channels in {8, 32}, input, weights and an output");
+                          "need nx % 8 == 0, ny % 16 == 0, channels in {8, 32}, input, weights and an output");
+  // 16-byte copies and stores: activations, mask and outputs 16-byte aligned
+  const auto mis = [](const void* p) { return ((uintptr_t)p & 15) != 0; };
+  if (mis(x) || mis(img) || mis(mask) || mis(y_bf16) || mis(y_f32))
+    return mhd::set_error(MHD_E_ARG, "mhd_conv3d", "buffers must be 16-byte aligned");
   // the blocks copy npad x kchunks*32 BF16 weights: the image must be exactly that
   if (img_bytes != (size_t)mhd::conv_npad(cout) * mhd::conv_kchunks(cin) * 32 * 2)
     return mhd::set_error(MHD_E_ARG, "mhd_conv3d", "weight image size does not match cin/cout");

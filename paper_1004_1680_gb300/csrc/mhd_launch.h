@@ -124,7 +124,7 @@ struct ConvArgs {
   float* y32;                 // output [cell][cout] FP32, or nullptr
   const __nv_bfloat16* mask;  // zero outputs where mask[cell][co] <= 0 (ReLU backward), or nullptr
   int n[3];
-  int cin;                    // channels gathered per cell (the GEMM's C)
+  int cin;                    // input channels per cell (8 or 32)
   int cout;                   // channels written per cell
   int npad, kchunks;          // MMA N and number of 32-wide k chunks
   int relu;
@@ -133,7 +133,7 @@ struct ConvArgs {
 };
 int conv_npad(int n);
 int conv_kchunks(int c);
-size_t conv_smem_bytes(int npad, int kchunks);
+size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty);
 cudaError_t prepare_conv_kernels();
 cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s);
 cudaError_t launch_conv3d(const ConvArgs& a, cudaStream_t s);

@@ -348,6 +348,14 @@ def conv3d(x: torch.Tensor, img: torch.Tensor, n, cin: int, cout: int, bias=None
     return yb, yf
 
 
+def conv3d_into(x: torch.Tensor, img: torch.Tensor, n, cin: int, cout: int, y_bf16=None, y_f32=None, bias=None,
+                relu=False, flip=False, mask=None, stream=None):
+    """conv3d writing into caller-provided outputs (no allocation)."""
+    lib = load()
+    _check(lib.mhd_conv3d(n[0], n[1], n[2], cin, cout, _ptr(x), _ptr(img), img.numel() * img.element_size(),
+                          _ptr(bias), int(relu), int(flip), _ptr(mask), _ptr(y_bf16), _ptr(y_f32), _stream(stream)))
+
+
 def conv3d_wgrad(x: torch.Tensor, gy: torch.Tensor, n, cin: int, cout: int, gw: torch.Tensor, gb=None,
                  stream=None):
     """Accumulate the weight (and bias) gradient into gw (cout*cin*27) and gb."""

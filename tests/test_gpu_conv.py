@@ -10,11 +10,6 @@ import torch.nn.functional as F
 pytestmark = pytest.mark.gpu
 
 
-def ref_conv(x, w, b):
-    """x (cells, cin) -> (1, cin, nz, ny, nx) FP64 circular conv -> (cells, cout)."""
-    return x
-
-
 def to_ncdhw(x, n):
     nx, ny, nz = n
     return x.T.reshape(1, x.shape[1], nz, ny, nx)
@@ -29,7 +24,7 @@ def from_ncdhw(y):
 def test_conv_forward_dgrad_wgrad(cin, cout):
     from paper_1004_1680_gb300 import mhd
     torch.manual_seed(cin * 100 + cout)
-    n = (16, 8, 24)
+    n = (24, 32, 6)      # 3 x 2 x 6 tiles of 8 x 16 x 1, periodic wrap on every face
     cells = n[0] * n[1] * n[2]
     xb = (torch.randn(cells, cin) * 0.5).to(torch.bfloat16)
     w = torch.randn(cout, cin, 3, 3, 3) * 0.1
@@ -68,3 +63,49 @@ def test_conv_forward_dgrad_wgrad(cin, cout):
     gwr = w64.grad.reshape(-1)
     assert float((gw.cpu().double() - gwr).abs().max()) < 1e-4 * float(gwr.abs().max())
     assert float((gb.cpu().double() - b64.grad).abs().max()) < 1e-4 * float(b64.grad.abs().max())
+
+
+def sampled_conv(x, w, n, cells, flip=False):
+    """FP64 output of the circular cross-correlation at the given cells only:
+    y[c, o] = sum_{ci, taps} w[o, ci, tap] x[c + s * offset(tap), ci]."""
+    nx, ny, nz = n
+    i, j, k = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    s = -1 if flip else 1
+    out = np.zeros((len(cells), w.shape[0]))
+    for kz in range(3):
+        for ky in range(3):
+            for kx in range(3):
+                src = ((i + s * (kx - 1)) % nx) + nx * (((j + s * (ky - 1)) % ny) + ny * ((k + s * (kz - 1)) % nz))
+                out += x[src] @ w[:, :, kz, ky, kx].T
+    return out
+
+
+@pytest.mark.parametrize("cin,cout", [(8, 32), (32, 32), (32, 8)])
+def test_conv_64_cubed_sampled(cin, cout):
+    """The 64^3 configuration the correction runs on (2048 tiles: every block
+    loops over several tiles with the next halo prefetched), forward and
+    input gradient, at 4096 sampled cells computed one by one in FP64."""
+    from paper_1004_1680_gb300 import mhd
+    n = (64, 64, 64)
+    N = n[0] * n[1] * n[2]
+    g = torch.Generator().manual_seed(cin + 7 * cout)
+    xb = (torch.randn(N, cin, generator=g) * 0.5).to(torch.bfloat16)
+    gyb = torch.randn(N, cout, generator=g).to(torch.bfloat16)
+    w = torch.randn(cout, cin, 3, 3, 3, generator=g) * 0.1
+    bias = torch.randn(cout, generator=g) * 0.1
+    img = mhd.conv_pack(w.cuda())
+    imgt = mhd.conv_pack(w.cuda(), transpose=True)
+    _, y = mhd.conv3d(xb.cuda(), img, n, cin, cout, bias=bias.cuda(), out_bf16=False, out_f32=True)
+    _, gx = mhd.conv3d(gyb.cuda(), imgt, n, cout, cin, flip=True, out_bf16=False, out_f32=True)
+    torch.cuda.synchronize()
+    assert mhd.conv_error() == 0
+    rng = np.random.default_rng(cin * cout)
+    cells = np.concatenate([rng.integers(0, N, 4000), [0, N - 1, 63, 64 * 64 - 1, N - 64 * 64]])
+    wb = w.to(torch.bfloat16).double().numpy()
+    ref = sampled_conv(xb.double().numpy(), wb, n, cells) + bias.double().numpy()
+    assert np.max(np.abs(y.cpu().double().numpy()[cells] - ref)) < 1e-4 * np.max(np.abs(ref))
+    wt = np.transpose(wb, (1, 0, 2, 3, 4))          # input gradient: transposed, mirrored taps
+    refg = sampled_conv(gyb.double().numpy(), wt, n, cells, flip=True)
+    assert np.max(np.abs(gx.cpu().double().numpy()[cells] - refg)) < 1e-4 * np.max(np.abs(refg))
+    # every cell written (no tile skipped): finite everywhere
+    assert bool(torch.isfinite(y).all()) and bool(torch.isfinite(gx).all())

@@ -18,7 +18,7 @@ def bf16_round(h):
 
 def test_training_graph_against_fp64_autograd():
     from paper_1004_1680_gb300 import learned, mhd
-    n = (16, 8, 8)
+    n = (16, 16, 4)
     cells = n[0] * n[1] * n[2]
     st = ic.turbulence(n, seed=4, dtype=torch.float64, kmin=1.0, kmax=2.0).to(torch.float32).contiguous().cuda()
     torch.manual_seed(5)

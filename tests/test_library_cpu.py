@@ -58,3 +58,25 @@ def test_null_handle_is_an_argument_error(lib):
     dt = ctypes.c_double()
     assert lib.mhd_cfl_dt(None, 0.7, ctypes.byref(dt)) == M.MHD_E_ARG
     lib.mhd_destroy(None)
+
+
+@pytest.mark.parametrize("dims,cin,cout", [((12, 16, 4), 32, 32), ((8, 24, 4), 32, 32), ((8, 16, 0), 8, 32),
+                                           ((8, 16, 4), 16, 32), ((8, 16, 4), 32, 64)])
+def test_conv_rejects_unsupported_shapes(lib, dims, cin, cout):
+    """Tiles are 8 x 16 x 1 cells and channels 8 or 32: anything else is an
+    argument error, reported before any device work."""
+    dummy = ctypes.c_void_p(16)
+    nbytes = lib.mhd_conv_pack_bytes(cin, cout, 0)
+    rc = lib.mhd_conv3d(dims[0], dims[1], dims[2], cin, cout, dummy, dummy, nbytes, None, 0, 0, None,
+                        dummy, None, None)
+    assert rc == M.MHD_E_ARG
+    assert b"mhd_conv3d" in lib.mhd_last_error()
+
+
+def test_conv_pack_sizes(lib):
+    # Npad x (27 cin rounded up to 32) BF16: N = 32 for 32 outputs, 16 for 8
+    assert lib.mhd_conv_pack_bytes(32, 32, 0) == 32 * 864 * 2
+    assert lib.mhd_conv_pack_bytes(8, 32, 0) == 32 * 224 * 2
+    assert lib.mhd_conv_pack_bytes(32, 8, 0) == 16 * 864 * 2
+    assert lib.mhd_conv_pack_bytes(32, 8, 1) == 32 * 224 * 2
+    assert lib.mhd_conv_pack_bytes(16, 8, 0) == 0
