@@ -67,61 +67,117 @@ __device__ __forceinline__ float vanleer_half(float a, float b) {
   return keep_if_positive(ab, ab * fast_rcp(a + b));
 }
 
-// van Leer limiter of Section II.B: 2ab/(a+b) when a and b have the same
-// sign, else 0 (a+b cannot vanish when ab > 0; otherwise the quotient is
-// discarded by the select).
-__device__ __forceinline__ float vanleer(float a, float b) {
-  const float ab = a * b;
-  return keep_if_positive(ab, __fdividef(2.f * ab, a + b));
+// ---------------------------------------------------------------------------
+// FP32 arithmetic on one value (float) or on two independent values at once
+// (float2: Blackwell's packed FP32 instructions).  Every operation is rounded
+// explicitly (no multiply-add contraction left to the compiler), so a pencil
+// marched alone gives bitwise the same result as the same pencil marched
+// beside a neighbour.
+__device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float v_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float v_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float v_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float v_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ float v_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ float v_keep(float x, float q) { return keep_if_positive(x, q); }
+
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b = fma(b, -1, a): the product is exact, so one rounding as in __fsub_rn
+__device__ __forceinline__ float2 v_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 v_div(float2 a, float2 b) {
+  return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+}
+__device__ __forceinline__ float2 v_sqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 v_abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 v_keep(float2 x, float2 q) {
+  return make_float2(keep_if_positive(x.x, q.x), keep_if_positive(x.y, q.y));
+}
+
+template <class T>
+__device__ __forceinline__ T v_const(float s);
+template <>
+__device__ __forceinline__ float v_const<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ float2 v_const<float2>(float s) { return make_float2(s, s); }
+
+// Half the van Leer limiter of Section II.B: phi(a,b)/2 = ab/(a+b) when a and
+// b have the same sign, else 0 (a+b cannot vanish when ab > 0; otherwise the
+// quotient is discarded by the select).
+template <class T>
+__device__ __forceinline__ T vanleer_half_t(T a, T b) {
+  const T ab = v_mul(a, b);
+  return v_keep(ab, v_div(ab, v_add(a, b)));
 }
 
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame
 // (u = (rho, m_d, m_t1, m_t2, e), b = cell-centred (b_d, b_t1, b_t2)), and the
 // relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
 // bounds the fastest local wave speed (Section II.B, relaxing TVD).
-// Returns the right and left movers FR = (cu + F)/2, FL = (cu - F)/2.
-__device__ __forceinline__ void split_flux(const float u[5], const float b[3], float gamma,
-                                           float FR[5], float FL[5]) {
-  float rinv = __fdividef(1.f, u[0]);
-  float vd = u[1] * rinv, v1 = u[2] * rinv, v2 = u[3] * rinv;
-  float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-  float kin = 0.5f * (u[1] * vd + u[2] * v1 + u[3] * v2);
-  float p = (gamma - 1.f) * (u[4] - kin - 0.5f * b2);
-  float pstar = p + 0.5f * b2;
-  float bv = b[0] * vd + b[1] * v1 + b[2] * v2;
-  float F[5];
+// Returns the right and left movers FR = (cu + F)/2, FL = FR - F = (cu - F)/2.
+template <class T>
+__device__ __forceinline__ void split_flux_t(const T u[5], const T b[3], float gamma, T FR[5], T FL[5]) {
+  const T half = v_const<T>(0.5f);
+  const T rinv = v_div(v_const<T>(1.f), u[0]);
+  const T vd = v_mul(u[1], rinv), v1 = v_mul(u[2], rinv), v2 = v_mul(u[3], rinv);
+  const T b2 = v_fma(b[0], b[0], v_fma(b[1], b[1], v_mul(b[2], b[2])));
+  const T kin = v_mul(half, v_fma(u[1], vd, v_fma(u[2], v1, v_mul(u[3], v2))));
+  const T p = v_mul(v_const<T>(gamma - 1.f), v_fma(v_const<T>(-0.5f), b2, v_sub(u[4], kin)));
+  const T pstar = v_fma(half, b2, p);
+  const T bv = v_fma(b[0], vd, v_fma(b[1], v1, v_mul(b[2], v2)));
+  const T nb0 = v_mul(b[0], v_const<T>(-1.f));
+  T F[5];
   F[0] = u[1];
-  F[1] = u[1] * vd + pstar - b[0] * b[0];
-  F[2] = u[2] * vd - b[0] * b[1];
-  F[3] = u[3] * vd - b[0] * b[2];
-  F[4] = (u[4] + pstar) * vd - b[0] * bv;
-  float c = fabsf(vd) + sqrtf((gamma * p + b2) * rinv);
+  F[1] = v_fma(u[1], vd, v_fma(nb0, b[0], pstar));
+  F[2] = v_fma(u[2], vd, v_mul(nb0, b[1]));
+  F[3] = v_fma(u[3], vd, v_mul(nb0, b[2]));
+  F[4] = v_fma(v_add(u[4], pstar), vd, v_mul(nb0, bv));
+  const T c = v_add(v_abs(vd), v_sqrt(v_mul(v_fma(v_const<T>(gamma), p, b2), rinv)));
+  const T hc = v_mul(half, c);
 #pragma unroll
   for (int q = 0; q < 5; q++) {
-    float cu = c * u[q];
-    FR[q] = 0.5f * (cu + F[q]);
-    FL[q] = 0.5f * (cu - F[q]);
+    FR[q] = v_fma(hc, u[q], v_mul(half, F[q]));
+    FL[q] = v_sub(FR[q], F[q]);
   }
 }
 
 // Largest signal rate of one cell, max_d (|v_d| + c_f*) * n_d, in the global
 // frame (v, b indexed by axis).  Invalid cells (NaN, rho <= 0, p <= 0) report
-// +inf so that a max-reduction flags them.
+// +inf so that a max-reduction flags them.  Explicitly rounded (see below).
 __device__ __forceinline__ float cell_rate(float rho, const float m[3], float e, const float b[3],
                                            float gamma, const int n[3]) {
-  float rinv = fast_rcp(rho);
-  float v0 = m[0] * rinv, v1 = m[1] * rinv, v2 = m[2] * rinv;
-  float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-  float kin = 0.5f * (m[0] * v0 + m[1] * v1 + m[2] * v2);
-  float p = (gamma - 1.f) * (e - kin - 0.5f * b2);
-  float cf = fast_sqrt((gamma * p + b2) * rinv);
-  float r = fmaxf(fmaxf((fabsf(v0) + cf) * n[0], (fabsf(v1) + cf) * n[1]), (fabsf(v2) + cf) * n[2]);
-  bool ok = (rho > 0.f) && (p > 0.f) && (r <= 3.0e38f);
+  const float rinv = fast_rcp(rho);
+  const float v0 = __fmul_rn(m[0], rinv), v1 = __fmul_rn(m[1], rinv), v2 = __fmul_rn(m[2], rinv);
+  const float b2 = __fmaf_rn(b[0], b[0], __fmaf_rn(b[1], b[1], __fmul_rn(b[2], b[2])));
+  const float kin = __fmul_rn(0.5f, __fmaf_rn(m[0], v0, __fmaf_rn(m[1], v1, __fmul_rn(m[2], v2))));
+  const float p = __fmul_rn(gamma - 1.f, __fmaf_rn(-0.5f, b2, __fsub_rn(e, kin)));
+  const float cf = fast_sqrt(__fmul_rn(__fmaf_rn(gamma, p, b2), rinv));
+  const float r = fmaxf(fmaxf(__fmul_rn(__fadd_rn(fabsf(v0), cf), (float)n[0]),
+                              __fmul_rn(__fadd_rn(fabsf(v1), cf), (float)n[1])),
+                        __fmul_rn(__fadd_rn(fabsf(v2), cf), (float)n[2]));
+  const bool ok = (rho > 0.f) && (p > 0.f) && (r <= 3.0e38f);
   return ok ? r : __int_as_float(0x7f800000);
 }
 
+// Optional pressure floor on a finished cell u = (rho, m_d, m_t1, m_t2, e)
+// with cell-centred field b: e >= kinetic + magnetic + p_floor / (gamma - 1).
+__device__ __forceinline__ float floored_energy(const float u[5], const float b[3], float gamma, float p_floor) {
+  const float kin = __fdiv_rn(__fmul_rn(0.5f, __fmaf_rn(u[1], u[1], __fmaf_rn(u[2], u[2], __fmul_rn(u[3], u[3])))),
+                              u[0]);
+  const float mag = __fmul_rn(0.5f, __fmaf_rn(b[0], b[0], __fmaf_rn(b[1], b[1], __fmul_rn(b[2], b[2]))));
+  return fmaxf(u[4], __fadd_rn(__fadd_rn(kin, mag), __fdiv_rn(p_floor, gamma - 1.f)));
+}
+
+// cell-centred field component: mean of two faces
+__device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_rn(0.5f, __fadd_rn(lo, hi)); }
+__device__ __forceinline__ float2 face_mean(float2 lo, float2 hi) {
+  return __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(lo, hi));
+}
+
 // ---------------------------------------------------------------------------
-// Fluid marching pipeline.
+// Fluid marching pipeline, for one pencil (T = float) or two (T = float2).
 //
 // A thread walks its periodic pencil one position t at a time, receiving the
 // raw state U_t and the frozen cell-centred field b_t.  At step t it forms
@@ -132,44 +188,47 @@ __device__ __forceinline__ float cell_rate(float rho, const float m[3], float e,
 //             Unew(t-3)    = U(t-3) - tau/h (F2(t-5/2) - F2(t-7/2))
 // so Unew at position t-3 is produced at step t (the 7-point stencil of
 // Section II.B).  Every intermediate value is held in registers.
-struct FluidPipe {
-  float U1[5], U2[5], U3[5];  // raw U at t-1, t-2, t-3
-  float b1[3];                // frozen b at t-1
-  float FR1[5];               // stage-1 right mover at t-1
-  float f1m[5];               // stage-1 interface flux at t-3/2
-  float Rh2[5], Rh3[5], Rh4[5];  // stage-2 right movers at t-2, t-3, t-4
-  float Lh2[5], Lh3[5];          // stage-2 left movers at t-2, t-3
-  float F2m[5];               // stage-2 interface flux at t-7/2
+template <class T>
+struct FluidPipeT {
+  T U1[5], U2[5], U3[5];  // raw U at t-1, t-2, t-3
+  T b1[3];                // frozen b at t-1
+  T FR1[5];               // stage-1 right mover at t-1
+  T f1m[5];               // stage-1 interface flux at t-3/2
+  T Rh2[5], Rh3[5], Rh4[5];  // stage-2 right movers at t-2, t-3, t-4
+  T Lh2[5], Lh3[5];          // stage-2 left movers at t-2, t-3
+  T F2m[5];               // stage-2 interface flux at t-7/2
 
   __device__ __forceinline__ void init() {
+    const T z = v_const<T>(0.f);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = 0.f;
-      Rh2[q] = Rh3[q] = Rh4[q] = Lh2[q] = Lh3[q] = F2m[q] = 0.f;
+      U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = z;
+      Rh2[q] = Rh3[q] = Rh4[q] = Lh2[q] = Lh3[q] = F2m[q] = z;
     }
-    b1[0] = b1[1] = b1[2] = 0.f;
+    b1[0] = b1[1] = b1[2] = z;
   }
 
   // Consume position t; write Unew(t-3) into out.  c_half = tau/(2h),
   // c_full = tau/h.
-  __device__ __forceinline__ void step(const float U[5], const float b[3], float gamma,
-                                       float c_half, float c_full, float out[5]) {
-    float FR[5], FL[5];
-    split_flux(U, b, gamma, FR, FL);
-    float Uh[5], f1[5];
+  __device__ __forceinline__ void step(const T U[5], const T b[3], float gamma, float c_half, float c_full,
+                                       T out[5]) {
+    T FR[5], FL[5];
+    split_flux_t(U, b, gamma, FR, FL);
+    const T nch = v_const<T>(-c_half), ncf = v_const<T>(-c_full);
+    T Uh[5], f1[5];
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      f1[q] = FR1[q] - FL[q];
-      Uh[q] = U1[q] - c_half * (f1[q] - f1m[q]);
+      f1[q] = v_sub(FR1[q], FL[q]);
+      Uh[q] = v_fma(nch, v_sub(f1[q], f1m[q]), U1[q]);
     }
-    float Rh[5], Lh[5];
-    split_flux(Uh, b1, gamma, Rh, Lh);
+    T Rh[5], Lh[5];
+    split_flux_t(Uh, b1, gamma, Rh, Lh);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      float right = Rh3[q] + 0.5f * vanleer(Rh3[q] - Rh4[q], Rh2[q] - Rh3[q]);
-      float left = Lh2[q] - 0.5f * vanleer(Lh2[q] - Lh3[q], Lh[q] - Lh2[q]);
-      float F2 = right - left;
-      out[q] = U3[q] - c_full * (F2 - F2m[q]);
+      const T right = v_add(Rh3[q], vanleer_half_t(v_sub(Rh3[q], Rh4[q]), v_sub(Rh2[q], Rh3[q])));
+      const T left = v_sub(Lh2[q], vanleer_half_t(v_sub(Lh2[q], Lh3[q]), v_sub(Lh[q], Lh2[q])));
+      const T F2 = v_sub(right, left);
+      out[q] = v_fma(ncf, v_sub(F2, F2m[q]), U3[q]);
       F2m[q] = F2;
       // shift the windows
       U3[q] = U2[q];
@@ -188,6 +247,7 @@ struct FluidPipe {
     b1[2] = b[2];
   }
 };
+using FluidPipe = FluidPipeT<float>;
 
 // ---------------------------------------------------------------------------
 // Magnetic advection pipeline for one transverse component q = b_t along the

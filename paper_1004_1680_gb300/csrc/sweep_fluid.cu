@@ -153,9 +153,9 @@ fluid_sweep_kernel(FluidArgs a) {
 #pragma unroll
       for (int j = 0; j < CH; j++) {
         // cell-centred field: mean of the low and high face of the cell
-        B[j][0] = 0.5f * (bdn[j] + bdn[j + 1]);
-        B[j][1] = 0.5f * (B[j][1] + t1n[j]);
-        B[j][2] = 0.5f * (B[j][2] + t2n[j]);
+        B[j][0] = face_mean(bdn[j], bdn[j + 1]);
+        B[j][1] = face_mean(B[j][1], t1n[j]);
+        B[j][2] = face_mean(B[j][2], t2n[j]);
       }
     }
 #pragma unroll
@@ -166,9 +166,9 @@ fluid_sweep_kernel(FluidArgs a) {
         for (int q = 0; q < 5; q++) Uj[q] = row[q * kXTile + j];
         const float hi = (j + 1 < CH) ? row[5 * kXTile + j + 1] : bd_next;
         // cell-centred field: mean of the low and high face of the cell
-        Bj[0] = 0.5f * (row[5 * kXTile + j] + hi);
-        Bj[1] = 0.5f * (row[6 * kXTile + j] + row[7 * kXTile + j]);
-        Bj[2] = 0.5f * (row[8 * kXTile + j] + row[9 * kXTile + j]);
+        Bj[0] = face_mean(row[5 * kXTile + j], hi);
+        Bj[1] = face_mean(row[6 * kXTile + j], row[7 * kXTile + j]);
+        Bj[2] = face_mean(row[8 * kXTile + j], row[9 * kXTile + j]);
       } else {
 #pragma unroll
         for (int q = 0; q < 5; q++) Uj[q] = U[j][q];
@@ -182,11 +182,7 @@ fluid_sweep_kernel(FluidArgs a) {
       const int po = t - 3;  // position of the finished cell
       if (active && po >= s0 && po < s1) {
         const int cell = base + po * sD;  // po is inside [s0, s1)
-        if (FLOOR) {  // optional: raise e so that p >= p_floor (b_c of this cell is bc3)
-          const float kin = 0.5f * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) / o[0];
-          const float mag = 0.5f * (bc3[0] * bc3[0] + bc3[1] * bc3[1] + bc3[2] * bc3[2]);
-          o[4] = fmaxf(o[4], kin + mag + a.p_floor / (gamma - 1.f));
-        }
+        if (FLOOR) o[4] = floored_energy(o, bc3, gamma, a.p_floor);  // optional (b_c of this cell is bc3)
         o_rho[cell] = o[0];
         o_md[cell] = o[1];
         o_m1[cell] = o[2];
