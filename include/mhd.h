@@ -92,6 +92,24 @@ int mhd_step(mhd_t *m, double dt_full);
  * p <= 0) gets dt = 0; mhd_cfl_dt afterwards reports MHD_E_STATE. */
 int mhd_run(mhd_t *m, int nsteps, double cfl);
 
+/* Pipelined host-to-host runs (the paper times the update alone and leaves
+ * the host round trip out, Section III; a caller that streams states through
+ * the GPU needs it).  mhd_submit enqueues: copy the host state `in` (8 field
+ * pointers as in mhd_set_state) to the device, recompute its CFL rate and
+ * reset the time (as mhd_set_state), run nsteps steps (as mhd_run), copy the
+ * result to the host buffers `out`; it returns without waiting.  The copies
+ * run on two copy streams of the box and overlap the steps of the neighbouring
+ * submissions: the steps of submission k run while the input of k+1 and the
+ * output of k-1 move (three staging copies of the state, allocated on first
+ * use).  `in` must stay unchanged and `out` unread until mhd_drain; pinned
+ * host memory is needed for the copies to be asynchronous.  Any other call on
+ * the box is ordered after the submitted copies.  Returns MHD_E_ARG for NULL
+ * pointers, nsteps < 0 or cfl <= 0. */
+int mhd_submit(mhd_t *m, const float *const in[8], float *const out[8], int nsteps, double cfl);
+
+/* Wait until every submitted run has its result in the host buffers. */
+int mhd_drain(mhd_t *m);
+
 /* Simulation time accumulated by mhd_step / mhd_run since mhd_set_state.
  * Synchronises the stream. */
 int mhd_time(const mhd_t *m, double *t);

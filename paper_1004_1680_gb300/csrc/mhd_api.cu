@@ -74,6 +74,16 @@ struct mhd_s {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
   size_t ev_used = 0;
+  // pipelined host runs (mhd_submit / mhd_drain): three staging sets of the 8
+  // fields, an input and an output copy stream, and per slot the events
+  // "input landed" and "its arrays are no longer read by an output copy"
+  float* stage_arena = nullptr;
+  float* slot[3][8];
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[3] = {}, ev_free[3] = {}, ev_done = nullptr, ev_out = nullptr;
+  bool slot_used[3] = {false, false, false};
+  int next_slot = 0;
+  bool pipe_pending = false;  // an output copy may still be in flight
 };
 
 namespace {
@@ -233,6 +243,63 @@ int full_step(mhd_s* m) {
   return MHD_OK;
 }
 
+// Later work on the box's stream waits for the output copies of mhd_submit
+// (the box's arrays rotate through the staging sets).
+int join_pipeline(mhd_s* m) {
+  if (!m->pipe_pending) return MHD_OK;
+  CK(cudaEventRecord(m->ev_out, m->s_out));
+  CK(cudaStreamWaitEvent(m->stream, m->ev_out, 0));
+  return MHD_OK;
+}
+
+void free_pipeline(mhd_s* m) {
+  if (m->s_in) cudaStreamSynchronize(m->s_in);
+  if (m->s_out) cudaStreamSynchronize(m->s_out);
+  for (int j = 0; j < 3; j++) {
+    if (m->ev_in[j]) cudaEventDestroy(m->ev_in[j]);
+    if (m->ev_free[j]) cudaEventDestroy(m->ev_free[j]);
+  }
+  if (m->ev_done) cudaEventDestroy(m->ev_done);
+  if (m->ev_out) cudaEventDestroy(m->ev_out);
+  if (m->s_in) cudaStreamDestroy(m->s_in);
+  if (m->s_out) cudaStreamDestroy(m->s_out);
+  cudaFree(m->stage_arena);
+}
+
+int make_pipeline(mhd_s* m) {
+  if (m->stage_arena) return MHD_OK;
+  cudaError_t e = cudaMalloc(&m->stage_arena, sizeof(float) * (size_t)m->N * 24);
+  if (e != cudaSuccess) {
+    m->stage_arena = nullptr;
+    return cuda_fail(e, "cudaMalloc(staging)");
+  }
+  for (int j = 0; j < 3; j++)
+    for (int q = 0; q < 8; q++) m->slot[j][q] = m->stage_arena + (size_t)m->N * (8 * j + q);
+  if ((e = cudaStreamCreateWithFlags(&m->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&m->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&m->ev_done, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "pipeline streams");
+  for (int j = 0; j < 3; j++)
+    if ((e = cudaEventCreateWithFlags(&m->ev_in[j], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&m->ev_free[j], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "pipeline events");
+  return MHD_OK;
+}
+
+int run_steps(mhd_s* m, int nsteps, double cfl) {
+  for (int s = 0; s < nsteps; s++) {
+    int rc = traced(m, MHD_K_CONTROL, [&] {
+      CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
+                                  &m->sc->time, cfl, 0.0, m->stream));
+      return MHD_OK;
+    });
+    if (!rc) rc = full_step(m);
+    if (rc) return rc;
+  }
+  return ensure_layout(m, 0);  // consecutive steps share their x-sweep layout
+}
+
 bool check_box(const mhd_t* m) {
   if (!m) {
     fail(MHD_E_ARG, "null mhd_t");
@@ -316,6 +383,7 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
 
 void mhd_destroy(mhd_t* m) {
   if (!m) return;
+  free_pipeline(m);
   drop_events(m);
   cudaFree(m->arena);
   cudaFree(m->sc);
@@ -333,6 +401,7 @@ int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
   if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  if (int rc = join_pipeline(m)) return rc;
   const size_t bytes = sizeof(float) * (size_t)m->N;
   if (m->layout) {  // back to the plain layout (the old state is overwritten)
     std::swap(m->cur[1], m->cur[2]);
@@ -358,6 +427,7 @@ int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   const size_t bytes = sizeof(float) * (size_t)m->N;
   if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
+  if (int rc = join_pipeline(const_cast<mhd_s*>(m))) return rc;
   for (int q = 0; q < 8; q++)
     CK(cudaMemcpyAsync(f[q], m->cur[q], bytes,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
@@ -384,6 +454,7 @@ int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
 int mhd_step(mhd_t* m, double dt_full) {
   if (!check_box(m)) return MHD_E_ARG;
   if (!(dt_full >= 0.0) || !std::isfinite(dt_full)) return fail(MHD_E_ARG, "dt must be finite and >= 0");
+  if (int rc = join_pipeline(m)) return rc;
   int rc = traced(m, MHD_K_CONTROL, [&] {
     CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
                                 &m->sc->time, -1.0, 0.5 * dt_full, m->stream));
@@ -396,16 +467,58 @@ int mhd_step(mhd_t* m, double dt_full) {
 int mhd_run(mhd_t* m, int nsteps, double cfl) {
   if (!check_box(m)) return MHD_E_ARG;
   if (nsteps < 0 || !(cfl > 0.0)) return fail(MHD_E_ARG, "need nsteps >= 0 and cfl > 0");
-  for (int s = 0; s < nsteps; s++) {
-    int rc = traced(m, MHD_K_CONTROL, [&] {
-      CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
-                                  &m->sc->time, cfl, 0.0, m->stream));
-      return MHD_OK;
-    });
-    if (!rc) rc = full_step(m);
-    if (rc) return rc;
-  }
-  return ensure_layout(m, 0);  // consecutive steps share their x-sweep layout
+  if (int rc = join_pipeline(m)) return rc;
+  return run_steps(m, nsteps, cfl);
+}
+
+// Pipelined host runs.  Submission k uses staging slot j = k mod 3:
+//   s_in:   wait until slot j's arrays are no longer read (ev_free[j]), copy
+//           the host input into them, record ev_in[j];
+//   stream: wait ev_in[j], adopt slot j's arrays as the state (the arrays of
+//           the previous result move into slot j; ev_free[j], recorded on
+//           s_out now, marks the end of that result's output copy), reset the
+//           CFL rate and time, run nsteps, record ev_done;
+//   s_out:  wait ev_done, copy the state out to the host.
+// So the steps of submission k overlap the input copy of k+1 and the output
+// copy of k-1.
+int mhd_submit(mhd_t* m, const float* const in[8], float* const out[8], int nsteps, double cfl) {
+  if (!check_box(m) || !in || !out) return fail(MHD_E_ARG, "null argument");
+  for (int q = 0; q < 8; q++)
+    if (!in[q] || !out[q]) return fail(MHD_E_ARG, "null field pointer");
+  if (nsteps < 0 || !(cfl > 0.0)) return fail(MHD_E_ARG, "need nsteps >= 0 and cfl > 0");
+  if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
+  if (int rc = make_pipeline(m)) return rc;
+  const size_t bytes = sizeof(float) * (size_t)m->N;
+  const int j = m->next_slot;
+  m->next_slot = (j + 1) % 3;
+  if (m->slot_used[j]) CK(cudaStreamWaitEvent(m->s_in, m->ev_free[j], 0));
+  m->slot_used[j] = true;
+  for (int q = 0; q < 8; q++) CK(cudaMemcpyAsync(m->slot[j][q], in[q], bytes, cudaMemcpyHostToDevice, m->s_in));
+  CK(cudaEventRecord(m->ev_in[j], m->s_in));
+  CK(cudaStreamWaitEvent(m->stream, m->ev_in[j], 0));
+  for (int q = 0; q < 8; q++) std::swap(m->cur[q], m->slot[j][q]);
+  CK(cudaEventRecord(m->ev_free[j], m->s_out));
+  CK(cudaMemsetAsync(m->sc, 0, sizeof(Scalars), m->stream));
+  m->rcur = 0;
+  const float* cf[8];
+  field_ptrs(m, cf);
+  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[0], m->stream));
+  if (int rc = run_steps(m, nsteps, cfl)) return rc;
+  CK(cudaEventRecord(m->ev_done, m->stream));
+  CK(cudaStreamWaitEvent(m->s_out, m->ev_done, 0));
+  for (int q = 0; q < 8; q++) CK(cudaMemcpyAsync(out[q], m->cur[q], bytes, cudaMemcpyDeviceToHost, m->s_out));
+  m->pipe_pending = true;
+  return MHD_OK;
+}
+
+int mhd_drain(mhd_t* m) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (!m->pipe_pending) return MHD_OK;
+  if (int rc = join_pipeline(m)) return rc;
+  CK(cudaStreamSynchronize(m->s_out));
+  CK(cudaStreamSynchronize(m->stream));
+  m->pipe_pending = false;
+  return MHD_OK;
 }
 
 int mhd_time(const mhd_t* m, double* t) {
@@ -421,6 +534,7 @@ int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
     return fail(MHD_E_ARG, "bad axis/kind/tau");
   // a single sweep does not advance the simulation time; afterwards the CFL
   // rate is recomputed for the new state
+  if (int rc = join_pipeline(m)) return rc;
   CK(mhd::launch_set_tau(&m->sc->tau, tau, m->stream));
   int rc = kind == 0 ? fluid(m, axis, false) : magnetic(m, axis);
   if (!rc) rc = ensure_layout(m, 0);
@@ -460,6 +574,7 @@ int mhd_set_pressure_floor(mhd_t* m, double p_floor) {
 
 int mhd_diagnostics(mhd_t* m, double out[10]) {
   if (!check_box(m) || !out) return fail(MHD_E_ARG, "null argument");
+  if (int rc = join_pipeline(m)) return rc;
   const float* cf[8];
   field_ptrs(m, cf);
   CK(mhd::launch_diagnostics(cf, m->box, m->gamma, m->diag_partial, m->sc->diag, m->stream));

@@ -40,6 +40,8 @@ SIGNATURES = {
     "mhd_cfl_dt": (_I, [_P, _D, _DP]),
     "mhd_step": (_I, [_P, _D]),
     "mhd_run": (_I, [_P, _I, _D]),
+    "mhd_submit": (_I, [_P, _PP, _PP, _I, _D]),
+    "mhd_drain": (_I, [_P]),
     "mhd_time": (_I, [_P, _DP]),
     "mhd_sweep": (_I, [_P, _I, _I, _D]),
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
@@ -181,6 +183,21 @@ class Box:
             raise ValueError("bad output tensor")
         _check(self.lib.mhd_get_state(self.h, _field_ptrs(out), 1 if out.is_cuda else 0))
         return out
+
+    def submit(self, state_in: torch.Tensor, state_out: torch.Tensor, nsteps: int = 1, cfl: float = 0.7):
+        """Pipelined host run: copy the host state in, run nsteps (device CFL),
+        copy the result into the host tensor state_out; returns at once (see
+        drain).  Both tensors: contiguous float32 (8, nz, ny, nx), pinned."""
+        for t in (state_in, state_out):
+            if t.shape != self.shape or t.dtype != torch.float32 or not t.is_contiguous() or t.is_cuda:
+                raise ValueError(f"host state must be contiguous float32 {self.shape}")
+        _check(self.lib.mhd_submit(self.h, _field_ptrs(state_in), _field_ptrs(state_out), int(nsteps), float(cfl)))
+        self._pending = getattr(self, "_pending", []) + [(state_in, state_out)]
+
+    def drain(self):
+        """Wait until every submitted run's result is in its host tensor."""
+        _check(self.lib.mhd_drain(self.h))
+        self._pending = []
 
     def cfl_dt(self, cfl: float = 0.7) -> float:
         dt = ctypes.c_double()

@@ -80,3 +80,9 @@ def test_conv_pack_sizes(lib):
     assert lib.mhd_conv_pack_bytes(32, 8, 0) == 16 * 864 * 2
     assert lib.mhd_conv_pack_bytes(32, 8, 1) == 32 * 224 * 2
     assert lib.mhd_conv_pack_bytes(16, 8, 0) == 0
+
+
+def test_submit_rejects_null_handle(lib):
+    ptrs = (ctypes.c_void_p * 8)()
+    assert lib.mhd_submit(None, ptrs, ptrs, 1, 0.7) == M.MHD_E_ARG
+    assert lib.mhd_drain(None) == M.MHD_E_ARG
