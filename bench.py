@@ -191,7 +191,7 @@ def bf16_peak():
         return 1900.0, "fallback bf16 burst"
 
 
-def ensemble_leg(args):
+def ensemble_leg(args, world=1):
     """256 independent periodic boxes, per-axis sizes drawn from {32,48,64,96}
     (rng 2024), box b seeded 1000+b with its own rms Mach and beta; one batched
     launch per sweep, per-box CFL dt, the run replayed as one CUDA graph."""
@@ -217,14 +217,16 @@ def ensemble_leg(args):
     invalid_warm = int(np.sum(ens.cfl_dt_safe(args.cfl) == 0.0))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record(ens.stream)
     ens.run(args.ensemble_steps, args.cfl)
     e1.record(ens.stream)
     torch.cuda.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
+    secs = max_over_ranks([e0.elapsed_time(e1) / 1e3], world)[0]
     invalid = int(np.sum(ens.cfl_dt_safe(args.cfl) == 0.0))
-    out = {"value": cells * args.ensemble_steps / secs, "unit": UNIT, "boxes": len(dims),
+    out = {"value": whole_job_rate(cells * args.ensemble_steps, world, secs), "unit": UNIT, "boxes": len(dims),
            "cells": cells, "steps": args.ensemble_steps, "ms_per_step": 1e3 * secs / args.ensemble_steps,
            "tuning": {"xpath": xp, "segdiv": sd}, "pressure_floor": P_FLOOR_ENSEMBLE,
            "invalid_boxes": invalid,
@@ -303,6 +305,23 @@ def learned_leg(args):
            "timing": "CUDA graph of the repeated calls (device time only)",
            "reps": args.learned_reps}
     return out
+
+
+def max_over_ranks(values, world, device="cuda"):
+    """Each rank's timings -> the maximum over ranks of each (the slowest
+    rank sets the whole job's time); identity for a single rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, secs):
+    """Units processed by all ranks together (replicas: each rank the same
+    amount) over the slowest rank's time."""
+    return units_per_rank * world / secs
 
 
 def run_reference(args, rank, world):
@@ -384,11 +403,8 @@ def run_ours(args, rank, world, local):
     box.cfl_dt(args.cfl)               # state still valid after the timed run
     prof = box.profile_read()
     box.profile(0)
-    if world > 1:
-        t = torch.tensor([secs], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
-    value = N * args.steps * world / secs
+    secs = max_over_ranks([secs], world)[0]
+    value = whole_job_rate(N * args.steps, world, secs)
 
     # per-kernel roofline of the dominant kernel family
     fam = {"fluid": [prof[k] for k in ("fluid_x", "fluid_y", "fluid_z")],
@@ -436,22 +452,20 @@ def run_ours(args, rank, world, local):
             box.get_state(out_host)      # D2H of the 8 fields (synchronises)
         torch.cuda.synchronize()
         ss = time.perf_counter() - w1
-        if world > 1:
-            t = torch.tensor([es, ss], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            es, ss = float(t[0].item()), float(t[1].item())
-        e2e = {"value": N * args.e2e_steps * world / es, "unit": UNIT,
+        es, ss = max_over_ranks([es, ss], world)
+        e2e = {"value": whole_job_rate(N * args.e2e_steps, world, es), "unit": UNIT,
                "h2d_bytes_per_step": 8 * 4 * N, "d2h_bytes_per_step": 8 * 4 * N,
                "ms_per_step": 1e3 * es / args.e2e_steps,
                "api": "mhd_submit x steps + mhd_drain (pinned host in/out, wall clock)",
-               "sync": {"value": N * args.e2e_steps * world / ss, "ms_per_step": 1e3 * ss / args.e2e_steps,
+               "sync": {"value": whole_job_rate(N * args.e2e_steps, world, ss),
+                        "ms_per_step": 1e3 * ss / args.e2e_steps,
                         "api": "mhd_set_state + mhd_run(1) + mhd_get_state per step"}}
 
     ens_out = None
     if args.ensemble_steps > 0:
         box.close()
         torch.cuda.empty_cache()
-        ens_out = ensemble_leg(args)
+        ens_out = ensemble_leg(args, world)
 
     learned_out = None
     if args.learned_reps > 0:
