@@ -68,6 +68,12 @@ def _load():
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_pressure_floor.argtypes = [ctypes.c_double]
+            lib.orc_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.orc_set_scheme.restype = ctypes.c_int
+            lib.orc_limiter.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_limiter.restype = ctypes.c_double
+            lib.orc_freezing_speed.argtypes = [dp, dp, ctypes.c_double]
+            lib.orc_freezing_speed.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -100,6 +106,29 @@ def set_threads(t: int) -> None:
 def set_pressure_floor(p_floor: float) -> None:
     """Optional floor on the gas pressure after each fluid sweep (0 = off)."""
     _load().orc_set_pressure_floor(float(p_floor))
+
+
+LIMITERS = {"vanleer": 0, "minmod": 1, "superbee": 2}
+FREEZING = {"bound": 0, "fast": 1}
+
+
+def set_scheme(limiter: str = "vanleer", freezing: str = "bound") -> None:
+    """Scheme variant for the following sweeps (the paper's scheme is
+    van Leer with the bound freezing speed; the others are ablations)."""
+    if _load().orc_set_scheme(LIMITERS[limiter], FREEZING[freezing]):
+        raise ValueError("bad scheme")
+
+
+def limiter(a: float, b: float) -> float:
+    """phi(a, b) of the current limiter."""
+    return _load().orc_limiter(float(a), float(b))
+
+
+def freezing_speed(u, b, gamma: float) -> float:
+    """Freezing speed of one cell, u = (rho, m_d, m_t1, m_t2, e), b = (b_d, b_t1, b_t2)."""
+    ua = (ctypes.c_double * 5)(*[float(x) for x in u])
+    ba = (ctypes.c_double * 3)(*[float(x) for x in b])
+    return _load().orc_freezing_speed(ua, ba, float(gamma))
 
 
 def fluid_sweep(state: np.ndarray, d: int, tau: float, gamma: float) -> None:

@@ -69,10 +69,39 @@ static long at(const int n[3], const int c[3]) {
            (long)n[0] * ((long)wrap(c[1], n[1]) + (long)n[1] * (long)wrap(c[2], n[2]));
 }
 
-/* van Leer limiter of Section II.B: harmonic mean of two slopes of equal sign */
-static double vanleer(double a, double b) {
-    return (a * b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+/* Scheme variants, ablations of the paper's scheme (which is limiter 0,
+ * freezing 0):
+ *   limiter 0 = van Leer (Section II.B), 1 = minmod, 2 = superbee
+ *     (the two limiters that bound the second-order TVD region of Sweby's
+ *     diagram from below and from above);
+ *   freezing 0 = the bound |v_d| + sqrt((gamma p + |b_c|^2)/rho),
+ *   freezing 1 = |v_d| + the fast magnetosonic speed along d,
+ *     c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2)) / 2, s = a^2 + v_A^2,
+ *     a^2 = gamma p / rho, v_A^2 = |b_c|^2 / rho, v_Ad^2 = b_d^2 / rho
+ *     (the smallest freezing speed the relaxation scheme allows).
+ * The CFL rate keeps the bound in every variant. */
+static int g_limiter = 0, g_freezing = 0;
+int orc_set_scheme(int limiter, int freezing) {
+    if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 1) return 1;
+    g_limiter = limiter;
+    g_freezing = freezing;
+    return 0;
 }
+
+/* Slope limiter phi(a, b) of two neighbouring differences: 0 unless they
+ * have the same sign; van Leer 2ab/(a+b) (Section II.B); minmod, the one of
+ * smaller magnitude; superbee, sign(a) max(min(2|a|,|b|), min(|a|,2|b|)). */
+double orc_limiter(double a, double b) {
+    if (!(a * b > 0.0)) return 0.0;
+    if (g_limiter == 1) return fabs(a) < fabs(b) ? a : b;
+    if (g_limiter == 2) {
+        double A = fabs(a), B = fabs(b);
+        double m = fmax(fmin(2.0 * A, B), fmin(A, 2.0 * B));
+        return a > 0.0 ? m : -m;
+    }
+    return 2.0 * a * b / (a + b);
+}
+
 
 /*
  * Flux of Eq. 2-3 projected on the sweep axis, in the sweep's local frame
@@ -94,7 +123,21 @@ static void flux_and_speed(const double u[5], const double b[3], double gamma,
     F[2] = u[2] * vd - b[0] * b[1];
     F[3] = u[3] * vd - b[0] * b[2];
     F[4] = (u[4] + pstar) * vd - b[0] * bv;
-    *c = fabs(vd) + sqrt((gamma * p + b2) / rho);
+    if (g_freezing == 1) {
+        double a2 = gamma * p / rho, va2 = b2 / rho, vad2 = b[0] * b[0] / rho;
+        double sum = a2 + va2, disc = sum * sum - 4.0 * a2 * vad2;
+        *c = fabs(vd) + sqrt(0.5 * (sum + sqrt(disc > 0.0 ? disc : 0.0)));
+    } else {
+        *c = fabs(vd) + sqrt((gamma * p + b2) / rho);
+    }
+}
+
+/* The freezing speed of one cell state (u, b in the sweep's local frame),
+ * for the tests. */
+double orc_freezing_speed(const double u[5], const double b[3], double gamma) {
+    double F[5], c;
+    flux_and_speed(u, b, gamma, F, &c);
+    return c;
 }
 
 /*
@@ -144,8 +187,8 @@ static void fluid_pencil(int n, double h, double tau, double gamma,
         const double *R = FR + q * n, *L = FL + q * n;
         for (i = 0; i < n; i++) {
             int im = wrap(i - 1, n), ip = wrap(i + 1, n), ipp = wrap(i + 2, n);
-            double right = R[i] + 0.5 * vanleer(R[i] - R[im], R[ip] - R[i]);
-            double left = L[ip] - 0.5 * vanleer(L[ip] - L[i], L[ipp] - L[ip]);
+            double right = R[i] + 0.5 * orc_limiter(R[i] - R[im], R[ip] - R[i]);
+            double left = L[ip] - 0.5 * orc_limiter(L[ip] - L[i], L[ipp] - L[ip]);
             fl[q * n + i] = right - left;
         }
     }
@@ -181,9 +224,9 @@ static void advect_flux(int n, double h, double tau, const double *q,
     for (i = 0; i < n; i++) {
         int im = wrap(i - 1, n), ip = wrap(i + 1, n), ipp = wrap(i + 2, n);
         if (ub[i] >= 0.0)
-            f[i] = ub[i] * (qh[i] + 0.5 * vanleer(qh[i] - qh[im], qh[ip] - qh[i]));
+            f[i] = ub[i] * (qh[i] + 0.5 * orc_limiter(qh[i] - qh[im], qh[ip] - qh[i]));
         else
-            f[i] = ub[i] * (qh[ip] - 0.5 * vanleer(qh[ip] - qh[i], qh[ipp] - qh[ip]));
+            f[i] = ub[i] * (qh[ip] - 0.5 * orc_limiter(qh[ip] - qh[i], qh[ipp] - qh[ip]));
     }
 }
 

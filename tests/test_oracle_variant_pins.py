@@ -1,0 +1,152 @@
+"""Pins of the oracle's scheme variants (ablations of the paper's scheme):
+the minmod and superbee limiters against the defining properties of
+second-order TVD limiters (Sweby's region: minmod its lower edge, superbee
+its upper edge, van Leer inside), advection behaviour that follows from them
+(TVD, second order on a smooth profile, edge sharpness ordered superbee <
+van Leer < minmod), and the exact fast magnetosonic freezing speed against
+its dispersion relation and limiting cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1004_1680_gb300 import initial_conditions as ic
+from tests.test_oracle_pins import G, _advect, order
+
+
+@pytest.fixture
+def scheme(oracle_lib):
+    yield oracle.set_scheme
+    oracle.set_scheme("vanleer", "bound")
+
+
+def phis(a, b):
+    out = {}
+    for lim in ("minmod", "vanleer", "superbee"):
+        oracle.set_scheme(lim)
+        out[lim] = oracle.limiter(a, b)
+    return out
+
+
+def test_limiter_region(scheme):
+    rng = np.random.default_rng(0)
+    for _ in range(500):
+        a = rng.normal() * 10.0 ** rng.uniform(-3, 3)
+        r = 10.0 ** rng.uniform(-3, 3) * (1 if rng.random() < 0.8 else -1)
+        b = r * a
+        p = phis(a, b)
+        if r <= 0:
+            assert all(v == 0.0 for v in p.values())
+            continue
+        # in units of a: phi(r) of Sweby's diagram
+        m, v, s = p["minmod"] / a, p["vanleer"] / a, p["superbee"] / a
+        assert m == pytest.approx(min(1.0, r), rel=1e-14)                 # lower edge
+        assert s == pytest.approx(max(min(2 * r, 1.0), min(r, 2.0)), rel=1e-14)  # upper edge
+        assert m <= v * (1 + 1e-14) and v <= s * (1 + 1e-14)              # van Leer inside
+        assert s <= min(2 * r, 2.0) * (1 + 1e-14)                          # TVD bound
+    for lim in ("minmod", "vanleer", "superbee"):
+        oracle.set_scheme(lim)
+        for a in (1e-3, 0.5, -7.0):
+            assert oracle.limiter(a, a) == pytest.approx(a, rel=1e-15)        # linear data: exact slope
+            assert oracle.limiter(a, 3 * a) == oracle.limiter(3 * a, a)       # symmetric
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee"])
+def test_step_advection_is_tvd(scheme, lim):
+    scheme(lim)
+
+    def prof(x, n):
+        return np.where((x > 0.25) & (x < 0.6), 2.0, -1.0)
+    s0, s = _advect(prof, 128, periods=0.37)
+    b0, b1 = s0[6].ravel(), s[6].ravel()
+    assert b1.max() <= b0.max() + 1e-13 and b1.min() >= b0.min() - 1e-13
+    tv = lambda f: np.sum(np.abs(np.diff(np.append(f, f[0]))))  # noqa: E731
+    assert tv(b1) <= tv(b0) + 1e-12
+    assert math.fsum(b1) == pytest.approx(math.fsum(b0), rel=1e-14)
+
+
+def test_edge_sharpness_ordering(scheme):
+    """Cells inside the 10-90 % band of a step after advection: superbee keeps
+    the sharpest edge, minmod the most diffused, van Leer in between."""
+    def prof(x, n):
+        return np.where((x > 0.25) & (x < 0.6), 1.0, 0.0)
+    width = {}
+    for lim in ("minmod", "vanleer", "superbee"):
+        scheme(lim)
+        _, s = _advect(prof, 256, periods=1.0)
+        b = s[6].ravel()
+        width[lim] = int(np.sum((b > 0.1) & (b < 0.9)))
+    assert width["superbee"] < width["vanleer"] < width["minmod"]
+
+
+@pytest.mark.parametrize("lim,min_order", [("minmod", 1.8), ("superbee", 1.4)])
+def test_smooth_advection_converges(scheme, lim, min_order):
+    scheme(lim)
+
+    def prof(x, n):
+        return 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.sinc(1.0 / n)
+    errs = []
+    for n in (64, 128, 256):
+        s0, s = _advect(prof, n)
+        errs.append(np.mean(np.abs(s[6] - s0[6])))
+    assert order(errs[1], errs[2]) > min_order
+
+
+def test_fast_freezing_speed(scheme):
+    scheme("vanleer", "fast")
+    rho, p = 1.3, 0.7
+    a2 = G * p / rho
+    for v, b in [((0.2, -0.1, 0.4), (0.0, 0.6, -0.3)),     # b perpendicular to d
+                 ((-0.5, 0.0, 0.0), (0.9, 0.0, 0.0)),      # b along d
+                 ((0.1, 0.3, -0.2), (0.5, -0.4, 0.7))]:    # oblique
+        m = [rho * x for x in v]
+        bb = sum(x * x for x in b)
+        e = 0.5 * rho * sum(x * x for x in v) + p / (G - 1) + 0.5 * bb
+        c = oracle.freezing_speed([rho] + m + [e], b, G) - abs(v[0])
+        va2, vad2 = bb / rho, b[0] ** 2 / rho
+        # the fast magnetosonic speed is the larger root of
+        # c^4 - (a^2 + v_A^2) c^2 + a^2 v_Ad^2 = 0
+        assert abs(c ** 4 - (a2 + va2) * c ** 2 + a2 * vad2) < 1e-13 * (a2 + va2) ** 2
+        assert c ** 2 >= 0.5 * (a2 + va2) * (1 - 1e-14)
+        assert max(math.sqrt(a2), math.sqrt(vad2)) <= c * (1 + 1e-14) <= math.sqrt(a2 + va2) * (1 + 1e-14)
+        if b[0] == 0.0:
+            assert c == pytest.approx(math.sqrt(a2 + va2), rel=1e-14)
+        if b[1] == b[2] == 0.0:
+            assert c == pytest.approx(max(math.sqrt(a2), math.sqrt(va2)), rel=1e-14)
+        scheme("vanleer", "bound")
+        cb = oracle.freezing_speed([rho] + m + [e], b, G) - abs(v[0])
+        assert cb == pytest.approx(math.sqrt(a2 + va2), rel=1e-14)        # the bound
+        scheme("vanleer", "fast")
+
+
+def test_fast_freezing_equals_bound_without_field(scheme):
+    """With b = 0 the fast speed is the sound speed, which the bound also is:
+    both variants give the same shock tube to rounding."""
+    st = ic.sod((64, 4, 4), axis=0).numpy().copy() if hasattr(ic, "sod") else None
+    if st is None:
+        pytest.skip("no shock tube generator")
+    res = {}
+    for fr in ("bound", "fast"):
+        scheme("vanleer", fr)
+        s = st.copy()
+        for _ in range(10):
+            oracle.step(s, 0.2 / 64, G)
+        res[fr] = s
+    assert np.max(np.abs(res["fast"] - res["bound"])) < 1e-12
+
+
+@pytest.mark.parametrize("lim,fr", [("minmod", "bound"), ("superbee", "bound"), ("vanleer", "fast")])
+def test_variants_conserve_and_keep_div_b(scheme, lim, fr):
+    scheme(lim, fr)
+    st = ic.turbulence((16, 12, 20), seed=3, dtype=torch.float64, kmin=1.0, kmax=3.0).numpy().copy()
+    d0 = oracle.diagnostics(st, G)
+    s = st.copy()
+    for _ in range(3):
+        oracle.step(s, oracle.cfl_dt(s, G, 0.7), G)
+    d1 = oracle.diagnostics(s, G)
+    scale = [np.sum(np.abs(st[q])) for q in range(8)]
+    for q in range(8):
+        assert abs(d1[q] - d0[q]) < 1e-13 * scale[q]
+    assert d1[8] < 1e-12
