@@ -129,6 +129,16 @@ int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
  * where the floor acts). */
 int mhd_set_pressure_floor(mhd_t *m, double p_floor);
 
+/* Scheme variants, ablations of the paper's scheme (limiter 0 and freezing 0,
+ * the default): limiter 1 = minmod, 2 = superbee instead of van Leer, in the
+ * fluid and the magnetic sweeps; freezing 1 = |v_d| + the exact fast
+ * magnetosonic speed along the sweep axis instead of the bound
+ * |v_d| + sqrt((gamma p + |b|^2)/rho) (Section II.B leaves the freezing speed
+ * open).  The CFL timestep keeps the bound.  One ablation at a time:
+ * MHD_E_ARG for limiter and freezing both non-zero or out of range.
+ * Ensembles always use the paper's scheme. */
+int mhd_set_scheme(mhd_t *m, int limiter, int freezing);
+
 /* Pencil segment lengths used by the sweeps along x, y and z.  A sweep splits
  * every pencil of n_d cells into n_d/seg_d pieces, each marched by its own
  * thread (more parallelism for small boxes, 8 cells of warm-up re-read per

@@ -65,6 +65,8 @@ struct mhd_s {
   int xpath = 0;        // x sweeps: 1 direct, 2 through the exchanged layout
   int xpath_req = 0;    // requested by mhd_set_xpath (0 = automatic)
   float p_floor = 0.f;  // optional pressure floor after fluid sweeps (0 = off)
+  int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
+  int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
@@ -197,6 +199,8 @@ int fluid(mhd_s* m, int d, bool rate) {
   a.tau = &m->sc->tau;
   a.rate = rate ? &m->sc->rate[1 - m->rcur] : nullptr;
   a.seg = m->seg[d];
+  a.lim = m->lim;
+  a.fast = m->fast;
   rc = traced(m, MHD_K_FLUID_X + d, [&] {
     CK(mhd::launch_fluid(ka, rate, a, m->stream));
     return MHD_OK;
@@ -217,6 +221,7 @@ int magnetic(mhd_s* m, int d) {
   a.box = *box;
   a.tau = &m->sc->tau;
   a.seg = m->seg[d];
+  a.lim = m->lim;
   rc = traced(m, MHD_K_MAG_X + d, [&] {
     CK(mhd::launch_mag(ka, a, m->stream));
     return MHD_OK;
@@ -562,6 +567,15 @@ int mhd_set_xpath(mhd_t* m, int mode) {
   if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
   m->xpath_req = mode;
   m->xpath = mode ? mode : auto_xpath(m);
+  return MHD_OK;
+}
+
+int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 1 || (limiter && freezing))
+    return fail(MHD_E_ARG, "limiter 0..2, freezing 0..1, one ablation at a time");
+  m->lim = limiter;
+  m->fast = freezing;
   return MHD_OK;
 }
 

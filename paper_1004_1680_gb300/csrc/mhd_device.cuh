@@ -68,11 +68,9 @@ __device__ __forceinline__ float vanleer_half(float a, float b) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 arithmetic on one value (float) or on two independent values at once
-// (float2: Blackwell's packed FP32 instructions).  Every operation is rounded
-// explicitly (no multiply-add contraction left to the compiler), so a pencil
-// marched alone gives bitwise the same result as the same pencil marched
-// beside a neighbour.
+// FP32 arithmetic with every operation rounded explicitly (no multiply-add
+// contraction left to the compiler), so that a pencil gives bitwise the same
+// result in every kernel that marches it (single box, ensemble work list).
 __device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float v_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
@@ -82,34 +80,29 @@ __device__ __forceinline__ float v_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ float v_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ float v_keep(float x, float q) { return keep_if_positive(x, q); }
 
-__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b = fma(b, -1, a): the product is exact, so one rounding as in __fsub_rn
-__device__ __forceinline__ float2 v_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 v_div(float2 a, float2 b) {
-  return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
-}
-__device__ __forceinline__ float2 v_sqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
-__device__ __forceinline__ float2 v_abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
-__device__ __forceinline__ float2 v_keep(float2 x, float2 q) {
-  return make_float2(keep_if_positive(x.x, q.x), keep_if_positive(x.y, q.y));
-}
-
 template <class T>
 __device__ __forceinline__ T v_const(float s);
 template <>
 __device__ __forceinline__ float v_const<float>(float s) { return s; }
-template <>
-__device__ __forceinline__ float2 v_const<float2>(float s) { return make_float2(s, s); }
 
-// Half the van Leer limiter of Section II.B: phi(a,b)/2 = ab/(a+b) when a and
-// b have the same sign, else 0 (a+b cannot vanish when ab > 0; otherwise the
-// quotient is discarded by the select).
-template <class T>
-__device__ __forceinline__ T vanleer_half_t(T a, T b) {
-  const T ab = v_mul(a, b);
-  return v_keep(ab, v_div(ab, v_add(a, b)));
+// Half a slope limiter, phi(a,b)/2, of two neighbouring differences; 0
+// unless they have the same sign.  LIM 0: van Leer, the limiter of Section
+// II.B, phi = 2ab/(a+b) (a+b cannot vanish when ab > 0; otherwise the quotient
+// is discarded by the select).  Ablations: LIM 1 minmod, phi = the difference
+// of smaller magnitude; LIM 2 superbee, phi = sign(a) max(min(2|a|,|b|),
+// min(|a|,2|b|)).
+template <int LIM>
+__device__ __forceinline__ float half_limited(float a, float b) {
+  const float ab = v_mul(a, b);
+  if constexpr (LIM == 1) {
+    return v_keep(ab, v_mul(0.5f, fabsf(a) < fabsf(b) ? a : b));
+  } else if constexpr (LIM == 2) {
+    const float A = fabsf(a), B = fabsf(b);
+    const float m = fmaxf(fminf(v_add(A, A), B), fminf(A, v_add(B, B)));
+    return v_keep(ab, v_mul(0.5f, copysignf(m, a)));
+  } else {
+    return v_keep(ab, v_div(ab, v_add(a, b)));
+  }
 }
 
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame
@@ -117,7 +110,10 @@ __device__ __forceinline__ T vanleer_half_t(T a, T b) {
 // relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
 // bounds the fastest local wave speed (Section II.B, relaxing TVD).
 // Returns the right and left movers FR = (cu + F)/2, FL = FR - F = (cu - F)/2.
-template <class T>
+// FAST = true replaces the bound by |v_d| + the fast magnetosonic speed along
+// d, c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2))/2, s = a^2 + v_A^2 (an ablation:
+// the smallest freezing speed the relaxation allows).
+template <class T, bool FAST = false>
 __device__ __forceinline__ void split_flux_t(const T u[5], const T b[3], float gamma, T FR[5], T FL[5]) {
   const T half = v_const<T>(0.5f);
   const T rinv = v_div(v_const<T>(1.f), u[0]);
@@ -134,7 +130,17 @@ __device__ __forceinline__ void split_flux_t(const T u[5], const T b[3], float g
   F[2] = v_fma(u[2], vd, v_mul(nb0, b[1]));
   F[3] = v_fma(u[3], vd, v_mul(nb0, b[2]));
   F[4] = v_fma(v_add(u[4], pstar), vd, v_mul(nb0, bv));
-  const T c = v_add(v_abs(vd), v_sqrt(v_mul(v_fma(v_const<T>(gamma), p, b2), rinv)));
+  T cs;
+  if constexpr (FAST) {
+    const T a2 = v_mul(v_mul(v_const<T>(gamma), p), rinv), va2 = v_mul(b2, rinv);
+    const T vad2 = v_mul(v_mul(b[0], b[0]), rinv);
+    const T sum = v_add(a2, va2);
+    const T disc = v_fma(v_mul(v_const<T>(-4.f), a2), vad2, v_mul(sum, sum));
+    cs = v_sqrt(v_mul(half, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))));
+  } else {
+    cs = v_sqrt(v_mul(v_fma(v_const<T>(gamma), p, b2), rinv));
+  }
+  const T c = v_add(v_abs(vd), cs);
   const T hc = v_mul(half, c);
 #pragma unroll
   for (int q = 0; q < 5; q++) {
@@ -172,12 +178,10 @@ __device__ __forceinline__ float floored_energy(const float u[5], const float b[
 
 // cell-centred field component: mean of two faces
 __device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_rn(0.5f, __fadd_rn(lo, hi)); }
-__device__ __forceinline__ float2 face_mean(float2 lo, float2 hi) {
-  return __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(lo, hi));
-}
 
 // ---------------------------------------------------------------------------
-// Fluid marching pipeline, for one pencil (T = float) or two (T = float2).
+// Fluid marching pipeline (LIM: limiter, FAST: freezing speed; 0 / false is
+// the paper's scheme).
 //
 // A thread walks its periodic pencil one position t at a time, receiving the
 // raw state U_t and the frozen cell-centred field b_t.  At step t it forms
@@ -188,7 +192,7 @@ __device__ __forceinline__ float2 face_mean(float2 lo, float2 hi) {
 //             Unew(t-3)    = U(t-3) - tau/h (F2(t-5/2) - F2(t-7/2))
 // so Unew at position t-3 is produced at step t (the 7-point stencil of
 // Section II.B).  Every intermediate value is held in registers.
-template <class T>
+template <class T, int LIM = 0, bool FAST = false>
 struct FluidPipeT {
   T U1[5], U2[5], U3[5];  // raw U at t-1, t-2, t-3
   T b1[3];                // frozen b at t-1
@@ -213,7 +217,7 @@ struct FluidPipeT {
   __device__ __forceinline__ void step(const T U[5], const T b[3], float gamma, float c_half, float c_full,
                                        T out[5]) {
     T FR[5], FL[5];
-    split_flux_t(U, b, gamma, FR, FL);
+    split_flux_t<T, FAST>(U, b, gamma, FR, FL);
     const T nch = v_const<T>(-c_half), ncf = v_const<T>(-c_full);
     T Uh[5], f1[5];
 #pragma unroll
@@ -222,11 +226,11 @@ struct FluidPipeT {
       Uh[q] = v_fma(nch, v_sub(f1[q], f1m[q]), U1[q]);
     }
     T Rh[5], Lh[5];
-    split_flux_t(Uh, b1, gamma, Rh, Lh);
+    split_flux_t<T, FAST>(Uh, b1, gamma, Rh, Lh);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      const T right = v_add(Rh3[q], vanleer_half_t(v_sub(Rh3[q], Rh4[q]), v_sub(Rh2[q], Rh3[q])));
-      const T left = v_sub(Lh2[q], vanleer_half_t(v_sub(Lh2[q], Lh3[q]), v_sub(Lh[q], Lh2[q])));
+      const T right = v_add(Rh3[q], half_limited<LIM>(v_sub(Rh3[q], Rh4[q]), v_sub(Rh2[q], Rh3[q])));
+      const T left = v_sub(Lh2[q], half_limited<LIM>(v_sub(Lh2[q], Lh3[q]), v_sub(Lh[q], Lh2[q])));
       const T F2 = v_sub(right, left);
       out[q] = v_fma(ncf, v_sub(F2, F2m[q]), U3[q]);
       F2m[q] = F2;
@@ -247,7 +251,8 @@ struct FluidPipeT {
     b1[2] = b[2];
   }
 };
-using FluidPipe = FluidPipeT<float>;
+template <int LIM, bool FAST>
+using FluidPipe = FluidPipeT<float, LIM, FAST>;
 
 // ---------------------------------------------------------------------------
 // Magnetic advection pipeline for one transverse component q = b_t along the
@@ -259,6 +264,7 @@ using FluidPipe = FluidPipeT<float>;
 //   f(t-5/2)    = ubar(t-5/2) * (qh_up +- phi(dqh-, dqh+)/2)  (van Leer)
 //   qnew(t-3)   = q(t-3) - tau/h (f(t-5/2) - f(t-7/2))
 // f(t-5/2) is the edge flux handed to the constraint on b_d.
+template <int LIM = 0>
 struct MagPipe {
   float q1, q2, q3;   // q at t-1, t-2, t-3
   float u1;           // face velocity at t-1
@@ -283,7 +289,12 @@ struct MagPipe {
     const float base = pos ? h3 : h2;
     const float sa = pos ? d43 : d32;
     const float sb = pos ? d32 : d21;
-    const float lim = vanleer_half(sa, sb);
+    float lim;
+    if constexpr (LIM == 0) {
+      lim = vanleer_half(sa, sb);
+    } else {
+      lim = half_limited<LIM>(sa, sb);
+    }
     const float f = ub2 * (pos ? base + lim : base - lim);
     qnew = q3 - c_full * (f - fm);
     fm = f;

@@ -45,6 +45,8 @@ struct FluidArgs {
   int seg;             // pencil segment length along the sweep axis
   EnsArgs ens;         // ensemble launches only
   int nblocks = 0;     // ensemble launches: number of work items
+  int lim = 0;         // slope limiter: 0 van Leer (the paper's), 1 minmod, 2 superbee
+  int fast = 0;        // freezing speed: 0 the bound, 1 the fast magnetosonic speed
 };
 
 struct MagArgs {
@@ -55,6 +57,7 @@ struct MagArgs {
   int seg;
   EnsArgs ens;
   int nblocks = 0;
+  int lim = 0;         // slope limiter (as FluidArgs::lim)
 };
 
 struct TransposeArgs {
@@ -148,6 +151,23 @@ cudaError_t launch_ens_control(const unsigned* rate_cur, unsigned* rate_next, fl
                                double* time, int nbox, double cfl, cudaStream_t s);
 cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
 cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s);
+// one instantiation per scheme variant, each in its own translation unit
+template <int LIM, bool FAST>
+cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
+template <int LIM>
+cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s);
+template <int LIM>
+cudaError_t prepare_mag_t();
+extern template cudaError_t launch_fluid_t<0, false>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<1, false>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<2, false>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<0, true>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_mag_t<0>(int, const MagArgs&, cudaStream_t);
+extern template cudaError_t launch_mag_t<1>(int, const MagArgs&, cudaStream_t);
+extern template cudaError_t launch_mag_t<2>(int, const MagArgs&, cudaStream_t);
+extern template cudaError_t prepare_mag_t<0>();
+extern template cudaError_t prepare_mag_t<1>();
+extern template cudaError_t prepare_mag_t<2>();
 // one-time per-device kernel attributes (call on the current device before launching)
 cudaError_t prepare_mag_kernels();
 cudaError_t launch_cfl_rate(const float* const f[8], const Box& box, float gamma, unsigned* rate,

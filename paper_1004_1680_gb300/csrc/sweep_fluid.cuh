@@ -1,0 +1,245 @@
+// Relaxing-TVD fluid sweep along one axis (Section II.B, Eq. 6), FP32.
+//
+// One thread owns one pencil segment along the sweep axis D and marches along
+// it with the FluidPipe of mhd_device.cuh: the 7-point stencil is evaluated
+// once per cell, intermediate values live in registers, and each of the 8
+// state fields is read once and each of the 5 conserved fields written once
+// per cell (the two transverse face fields are also read one pencil over,
+// which hits in cache).
+//
+// No transposes: for the y and z sweeps the 32 lanes of a warp are 32
+// neighbouring pencils along x, so every load and store of a plane is a
+// coalesced 128-byte row; for the x sweep a warp stages 8 cells of its 32
+// pencils in shared memory, loading whole 32-byte sectors.
+//
+// The sweep writes out of place (in -> out): neighbouring threads read the
+// transverse faces of this thread's pencil.
+//
+// With RATE = true the kernel also evaluates the CFL signal rate of every
+// cell it writes (Section II.B: the next timestep) and folds the maximum into
+// *rate with one atomicMax per warp, saving a separate pass over the state.
+//
+// LIM selects the slope limiter and FAST the freezing speed (0 / false: the
+// paper's scheme; the others are ablations).  This header holds the kernel
+// template; each scheme variant is instantiated in its own translation unit
+// (sweep_fluid.cu: the paper's scheme; sweep_variant_*.cu: the ablations).
+#pragma once
+#include "mhd_device.cuh"
+#include "mhd_launch.h"
+
+namespace mhd {
+
+template <int D>
+struct Axes {
+  // lane axis A (contiguous pencils across a warp), row axis O, transverse
+  // axes of the local frame T1 = (D+1)%3, T2 = (D+2)%3
+  static constexpr int A = (D == 0) ? 1 : 0;
+  static constexpr int O = (D == 2) ? 1 : 2;
+  static constexpr int T1 = (D + 1) % 3;
+  static constexpr int T2 = (D + 2) % 3;
+};
+
+constexpr int kFluidWarps = 4;
+
+// x sweeps: each warp stages 8 cells x 32 pencils of every source field in
+// shared memory (rows padded to 9 floats: conflict-free column reads), loaded
+// as 32-byte row pieces so each DRAM sector is fetched by exactly one load.
+constexpr int kXChunk = 8;
+constexpr int kXPad = 9;
+constexpr int kXTiles = 10;  // rho, m_d, m_t1, m_t2, e, b_d, b_t1, b_t1(+1), b_t2, b_t2(+1)
+constexpr int kXTile = 32 * kXPad;
+
+// Stage positions p0 .. p0+7 (periodic along x, p0 a multiple of 4) of the
+// pencils whose flat base index lane r holds in `rowbase` into tile[r][0..7].
+template <bool SMALL>
+__device__ __forceinline__ void stage_rows(float* tile, const float* __restrict__ src,
+                                           int rowbase, int p0, int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrap_near<SMALL>(p0 + 4 * h, nx)));
+    float* t = tile + r * kXPad + 4 * h;
+    t[0] = v.x;
+    t[1] = v.y;
+    t[2] = v.z;
+    t[3] = v.w;
+  }
+}
+
+template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, bool FAST>
+__global__ void __launch_bounds__(32 * kFluidWarps, RATE ? 3 : 4)
+fluid_sweep_kernel(FluidArgs a) {
+  using X = Axes<D>;
+  constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
+  __shared__ float xs[(D == 0) ? kFluidWarps * kXTiles * kXTile : 1];
+  const int lane = threadIdx.x;
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, a.rate);
+  const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
+  const int pa = G.bx * 32 + lane;
+  const int pb = G.by * kFluidWarps + threadIdx.y;
+  const bool active = (pa < nA) && (pb < nO);
+  const int ia = min(pa, nA - 1), ib = min(pb, nO - 1);
+  const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
+  const int base = ia * sA + ib * sO;
+  const int baseA1 = wrapi(ia + 1, nA) * sA + ib * sO;  // pencil +1 along A
+  const int baseO1 = ia * sA + wrapi(ib + 1, nO) * sO;  // pencil +1 along O
+  // +1 along the local-frame transverse axes
+  const int baseT1 = (X::T1 == X::A) ? baseA1 : baseO1;
+  const int baseT2 = (X::T2 == X::A) ? baseA1 : baseO1;
+
+  const float* __restrict__ rho = a.in[RHO] + G.off;
+  const float* __restrict__ md = a.in[MX + D] + G.off;
+  const float* __restrict__ m1 = a.in[MX + X::T1] + G.off;
+  const float* __restrict__ m2 = a.in[MX + X::T2] + G.off;
+  const float* __restrict__ en = a.in[EN] + G.off;
+  const float* __restrict__ bd = a.in[BX + D] + G.off;
+  const float* __restrict__ b1 = a.in[BX + X::T1] + G.off;
+  const float* __restrict__ b2 = a.in[BX + X::T2] + G.off;
+  float* __restrict__ o_rho = a.out[RHO] + G.off;
+  float* __restrict__ o_md = a.out[MX + D] + G.off;
+  float* __restrict__ o_m1 = a.out[MX + X::T1] + G.off;
+  float* __restrict__ o_m2 = a.out[MX + X::T2] + G.off;
+  float* __restrict__ o_en = a.out[EN] + G.off;
+  float* xw = xs + (D == 0 ? threadIdx.y * kXTiles * kXTile : 0);  // this warp's tiles
+
+  const float gamma = a.gamma;
+  const float tau = G.tau;
+  const float c_full = tau * (float)nD;  // tau / h_D
+  const float c_half = 0.5f * c_full;    // tau / (2 h_D)
+  const int s0 = G.bz * G.seg;
+  const int s1 = s0 + G.seg;
+  // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
+  // warm-up cell so that x chunks start 16-byte aligned)
+  const int nchunk = (G.seg + 7 + CH - 1) / CH;
+
+  FluidPipe<LIM, FAST> pipe;
+  pipe.init();
+  float bc2[3] = {0.f, 0.f, 0.f}, bc3[3] = {0.f, 0.f, 0.f};  // b_c at t-1, t-2 (RATE only)
+  float rmax = 0.f;
+
+  for (int c = 0; c < nchunk; c++) {
+    const int p0 = s0 - 4 + CH * c;  // first position of this chunk
+    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
+    float U[(D == 0) ? 1 : CH][5], B[(D == 0) ? 1 : CH][3];
+    const float* row = xw + lane * kXPad;
+    float bd_next = 0.f;
+    if constexpr (D == 0) {
+      __syncwarp();
+      stage_rows<SMALL>(xw + 0 * kXTile, rho, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 1 * kXTile, md, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 2 * kXTile, m1, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 3 * kXTile, m2, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 4 * kXTile, en, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 5 * kXTile, bd, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 6 * kXTile, b1, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 7 * kXTile, b1, baseT1, p0, nD, lane);
+      stage_rows<SMALL>(xw + 8 * kXTile, b2, base, p0, nD, lane);
+      stage_rows<SMALL>(xw + 9 * kXTile, b2, baseT2, p0, nD, lane);
+      bd_next = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD));  // high face of the last cell
+      __syncwarp();
+    } else {
+      // one coalesced row per plane
+      float bdn[CH + 1], t1n[CH], t2n[CH];
+#pragma unroll
+      for (int j = 0; j < CH; j++) {
+        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
+        U[j][0] = __ldg(rho + base + off);
+        U[j][1] = __ldg(md + base + off);
+        U[j][2] = __ldg(m1 + base + off);
+        U[j][3] = __ldg(m2 + base + off);
+        U[j][4] = __ldg(en + base + off);
+        bdn[j] = __ldg(bd + base + off);
+        B[j][1] = __ldg(b1 + base + off);
+        B[j][2] = __ldg(b2 + base + off);
+        t1n[j] = __ldg(b1 + baseT1 + off);
+        t2n[j] = __ldg(b2 + baseT2 + off);
+      }
+      bdn[CH] = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD) * sD);
+#pragma unroll
+      for (int j = 0; j < CH; j++) {
+        // cell-centred field: mean of the low and high face of the cell
+        B[j][0] = face_mean(bdn[j], bdn[j + 1]);
+        B[j][1] = face_mean(B[j][1], t1n[j]);
+        B[j][2] = face_mean(B[j][2], t2n[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+      float o[5], Uj[5], Bj[3];
+      if constexpr (D == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) Uj[q] = row[q * kXTile + j];
+        const float hi = (j + 1 < CH) ? row[5 * kXTile + j + 1] : bd_next;
+        // cell-centred field: mean of the low and high face of the cell
+        Bj[0] = face_mean(row[5 * kXTile + j], hi);
+        Bj[1] = face_mean(row[6 * kXTile + j], row[7 * kXTile + j]);
+        Bj[2] = face_mean(row[8 * kXTile + j], row[9 * kXTile + j]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; q++) Uj[q] = U[j][q];
+        Bj[0] = B[j][0];
+        Bj[1] = B[j][1];
+        Bj[2] = B[j][2];
+      }
+      const float bprev0 = pipe.b1[0], bprev1 = pipe.b1[1], bprev2 = pipe.b1[2];  // b_c(t-1)
+      pipe.step(Uj, Bj, gamma, c_half, c_full, o);
+      const int t = p0 + j;
+      const int po = t - 3;  // position of the finished cell
+      if (active && po >= s0 && po < s1) {
+        const int cell = base + po * sD;  // po is inside [s0, s1)
+        if (FLOOR) o[4] = floored_energy(o, bc3, gamma, a.p_floor);  // optional (b_c of this cell is bc3)
+        o_rho[cell] = o[0];
+        o_md[cell] = o[1];
+        o_m1[cell] = o[2];
+        o_m2[cell] = o[3];
+        o_en[cell] = o[4];
+        if (RATE) {
+          float m[3], bg[3];
+          m[D] = o[1]; m[X::T1] = o[2]; m[X::T2] = o[3];
+          bg[D] = bc3[0]; bg[X::T1] = bc3[1]; bg[X::T2] = bc3[2];
+          rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, G.box.n));
+        }
+      }
+      if (RATE || FLOOR) {  // window of b_c: bc2 = b_c(t-1), bc3 = b_c(t-2) for the next step
+        bc3[0] = bc2[0]; bc3[1] = bc2[1]; bc3[2] = bc2[2];
+        bc2[0] = bprev0; bc2[1] = bprev1; bc2[2] = bprev2;
+      }
+    }
+  }
+  if (RATE) {
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (lane == 0) atomicMax(G.rate, __float_as_uint(rmax));
+  }
+}
+
+// Launch of one fluid sweep with scheme (LIM, FAST): kernel axis, fused CFL
+// rate, short axis and pressure floor select the instantiation.
+template <int LIM, bool FAST>
+cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t s) {
+  const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
+  dim3 block(32, kFluidWarps);
+  dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kFluidWarps - 1) / kFluidWarps,
+            a.box.n[axis] / a.seg);
+  // ensemble launches: one block per work item; `small` must hold for every
+  // box of the launch (the host passes the smallest extent in a.box)
+  if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
+  const bool small = a.box.n[axis] < 16;
+  const bool floor = a.p_floor > 0.f;
+#define FLUID_CASE(DD, RR)                                                                            \
+  if (axis == DD && rate == RR) {                                                                     \
+    if (floor) {                                                                                      \
+      if (small) fluid_sweep_kernel<DD, RR, true, true, LIM, FAST><<<grid, block, 0, s>>>(a);         \
+      else fluid_sweep_kernel<DD, RR, false, true, LIM, FAST><<<grid, block, 0, s>>>(a);              \
+    } else {                                                                                          \
+      if (small) fluid_sweep_kernel<DD, RR, true, false, LIM, FAST><<<grid, block, 0, s>>>(a);        \
+      else fluid_sweep_kernel<DD, RR, false, false, LIM, FAST><<<grid, block, 0, s>>>(a);             \
+    }                                                                                                 \
+  }
+  FLUID_CASE(0, false) FLUID_CASE(0, true) FLUID_CASE(1, false) FLUID_CASE(1, true)
+  FLUID_CASE(2, false) FLUID_CASE(2, true)
+#undef FLUID_CASE
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,270 @@
+// Magnetic advection-constraint sweep along one axis D (Section II.B), FP32.
+//
+// For each transverse axis t the face field b_t is advected along D by the
+// upwind + van Leer, 2-stage scheme (MagPipe), and the edge flux f_t it
+// produces is applied to b_D:
+//   b_t(cell)          -= tau/h_D (f_t(i+1/2) - f_t(i-1/2))
+//   b_D(face i+1/2, P) += tau/h_t (f_t(pencil P+e_t) - f_t(pencil P)),
+// which keeps the discrete div b of every cell unchanged (Eq. 5).  The edge
+// flux lives on the edge (D: i+1/2, t: low face of pencil P); the EMF pieces
+// are applied directly and never written to memory.
+//
+// Velocities v_D = m_D/rho are formed once per loaded value.
+//
+// A block owns a tile of 32 (lane axis A) x kMagWarps (row axis O) pencils and
+// marches all of them together along D.  Two extra warps march the halo
+// pencils whose flux the tile needs: row O+kMagWarps (its f along O) and
+// column A+32 (its f along A).  Fluxes are exchanged through shared memory
+// once per chunk of 4 positions.  Writes are out of place.
+//
+// LIM selects the slope limiter (0: van Leer, the paper's; 1 minmod and 2
+// superbee are ablations, instantiated in sweep_variant_*.cu).
+#pragma once
+#include "mhd_device.cuh"
+#include "mhd_launch.h"
+
+namespace mhd {
+
+template <int D>
+struct MagAxes {
+  static constexpr int A = (D == 0) ? 1 : 0;
+  static constexpr int O = (D == 2) ? 1 : 2;
+  static constexpr int T1 = (D + 1) % 3;
+};
+
+// x sweeps stage 8 cells of each warp's 32 pencils in shared memory (rows of
+// 9 floats, 32-byte sector loads): v_x = m_x/rho at the pencil and at its -A
+// and -O neighbours, and the three face fields.
+constexpr int kMXChunk = 8;
+constexpr int kMXPad = 9;
+constexpr int kMXTiles = 6;
+constexpr int kMXTile = 32 * kMXPad;
+constexpr size_t kMagXSmem = sizeof(float) * (kMagWarps + 2) * kMXTiles * kMXTile;
+
+template <bool SMALL>
+__device__ __forceinline__ void stage_rows_m(float* tile, const float* __restrict__ src,
+                                             int rowbase, int p0, int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + rb + wrap_near<SMALL>(p0 + 4 * h, nx)));
+    float* t = tile + r * kMXPad + 4 * h;
+    t[0] = v.x;
+    t[1] = v.y;
+    t[2] = v.z;
+    t[3] = v.w;
+  }
+}
+
+// velocity rows: v = m / rho
+template <bool SMALL>
+__device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__ rho,
+                                          const float* __restrict__ m, int rowbase, int p0,
+                                          int nx, int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int r = 16 * k + (lane >> 1), h = lane & 1;
+    const int rb = __shfl_sync(0xffffffffu, rowbase, r);
+    const int off = wrap_near<SMALL>(p0 + 4 * h, nx);
+    const float4 rr = __ldg(reinterpret_cast<const float4*>(rho + rb + off));
+    const float4 mm = __ldg(reinterpret_cast<const float4*>(m + rb + off));
+    float* t = tile + r * kMXPad + 4 * h;
+    t[0] = __fdividef(mm.x, rr.x);
+    t[1] = __fdividef(mm.y, rr.y);
+    t[2] = __fdividef(mm.z, rr.z);
+    t[3] = __fdividef(mm.w, rr.w);
+  }
+}
+
+template <int D, bool SMALL, int LIM>
+__global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
+mag_sweep_kernel(MagArgs a) {
+  using X = MagAxes<D>;
+  constexpr int CH = (D == 0) ? kMXChunk : 4;
+  __shared__ float fA_s[CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
+  __shared__ float fO_s[CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
+  extern __shared__ float xs_dyn[];               // x sweeps only: staged rows
+
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
+  const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
+  const int a0 = G.bx * 32, b0 = G.by * kMagWarps;
+  const int cntA = min(32, nA - a0), cntO = min(kMagWarps, nO - b0);
+
+  // this thread's pencil and role
+  int pa, pb;
+  bool interior = false;
+  int row, col;  // slot in the exchange arrays
+  if (w < kMagWarps) {
+    pa = a0 + min(lane, cntA - 1);
+    pb = b0 + min(w, cntO - 1);
+    interior = (lane < cntA) && (w < cntO);
+    row = w;
+    col = lane;
+  } else if (w == kMagWarps) {             // halo row: pencils (a0+lane, b0+cntO)
+    pa = a0 + min(lane, cntA - 1);
+    pb = wrapi(b0 + cntO, nO);
+    row = cntO;
+    col = lane;
+  } else {                                 // halo column: pencils (a0+cntA, b0+lane)
+    pa = wrapi(a0 + cntA, nA);
+    pb = b0 + min(lane, cntO - 1);
+    row = min(lane, kMagWarps - 1);
+    col = cntA;
+  }
+  const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
+  const int base = pa * sA + pb * sO;
+  const int baseAm = wrapi(pa - 1, nA) * sA + pb * sO;  // pencil -1 along A
+  const int baseOm = pa * sA + wrapi(pb - 1, nO) * sO;  // pencil -1 along O
+
+  const float* __restrict__ rho = a.in[RHO] + G.off;
+  const float* __restrict__ md = a.in[MX + D] + G.off;
+  const float* __restrict__ bA = a.in[BX + X::A] + G.off;
+  const float* __restrict__ bO = a.in[BX + X::O] + G.off;
+  const float* __restrict__ bD = a.in[BX + D] + G.off;
+  float* __restrict__ o_bA = a.out[X::A] + G.off;
+  float* __restrict__ o_bO = a.out[X::O] + G.off;
+  float* __restrict__ o_bD = a.out[D] + G.off;
+  float* xw = xs_dyn + (D == 0 ? w * kMXTiles * kMXTile : 0);
+
+  const float tau = G.tau;
+  const float c_full = tau * (float)nD;        // tau / h_D
+  const float c_half = 0.5f * c_full;
+  const float kA = tau * (float)nA;             // tau / h_A
+  const float kO = tau * (float)nO;             // tau / h_O
+  const int s0 = G.bz * G.seg;
+  const int s1 = s0 + G.seg;
+  // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
+  // warm-up cell so that x chunks start 16-byte aligned)
+  const int nchunk = (G.seg + 7 + CH - 1) / CH;
+  // slots read by the tile: fO rows 0..cntO (row cntO = halo row), fA columns
+  // 0..cntA (column cntA = halo column); idle lanes of a partial tile must not
+  // overwrite a halo slot
+  const bool write_row = (w < kMagWarps) ? (w < cntO) : (w == kMagWarps);
+  const bool write_col = (w < kMagWarps) ? (w < cntO && lane < cntA)
+                                         : (w == kMagWarps + 1 && lane < cntO);
+
+  MagPipe<LIM> pA, pO;
+  pA.init();
+  pO.init();
+  float bD1 = 0.f, bD2 = 0.f;  // raw b_D at t-1, t-2
+
+  for (int c = 0; c < nchunk; c++) {
+    const int p0 = s0 - 4 + CH * c;
+    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
+    constexpr int R = (D == 0) ? 1 : CH;
+    float qA[R], qO[R], qD[R], rr[R], mm[R], rrA[R], mmA[R], rrO[R], mmO[R];
+    const float* rw = xw + lane * kMXPad;
+    if constexpr (D == 0) {
+      __syncwarp();
+      stage_vel<SMALL>(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
+      stage_vel<SMALL>(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
+      stage_vel<SMALL>(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 3 * kMXTile, bA, base, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 4 * kMXTile, bO, base, p0, nD, lane);
+      stage_rows_m<SMALL>(xw + 5 * kMXTile, bD, base, p0, nD, lane);
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int j = 0; j < CH; j++) {  // all loads of the chunk first; divisions when used
+        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
+        rr[j] = __ldg(rho + base + off);
+        mm[j] = __ldg(md + base + off);
+        rrA[j] = __ldg(rho + baseAm + off);
+        mmA[j] = __ldg(md + baseAm + off);
+        rrO[j] = __ldg(rho + baseOm + off);
+        mmO[j] = __ldg(md + baseOm + off);
+        qA[j] = __ldg(bA + base + off);
+        qO[j] = __ldg(bO + base + off);
+        qD[j] = __ldg(bD + base + off);
+      }
+    }
+    float bDold[CH];  // raw b_D at the face each position's constraint updates
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+      float vj, vAj, vOj, qAj, qOj, qDj;
+      if constexpr (D == 0) {
+        vj = rw[0 * kMXTile + j];
+        vAj = rw[1 * kMXTile + j];
+        vOj = rw[2 * kMXTile + j];
+        qAj = rw[3 * kMXTile + j];
+        qOj = rw[4 * kMXTile + j];
+        qDj = rw[5 * kMXTile + j];
+      } else {
+        vj = __fdividef(mm[j], rr[j]); vAj = __fdividef(mmA[j], rrA[j]); vOj = __fdividef(mmO[j], rrO[j]); qAj = qA[j]; qOj = qO[j]; qDj = qD[j];
+      }
+      const float uA = 0.5f * (vj + vAj);  // v_D on the b_A face
+      const float uO = 0.5f * (vj + vOj);  // v_D on the b_O face
+      // the halo row needs only the flux along O, the halo column only along A
+      float nA_new = 0.f, nO_new = 0.f, fa = 0.f, fo = 0.f;
+      if (w != kMagWarps) fa = pA.step(qAj, uA, c_half, c_full, nA_new);
+      if (w != kMagWarps + 1) fo = pO.step(qOj, uO, c_half, c_full, nO_new);
+      if (write_row) fO_s[j][row][col] = fo;
+      if (write_col) fA_s[j][row][col] = fa;
+      bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
+      bD2 = bD1;
+      bD1 = qDj;
+      const int t = p0 + j;
+      const int po = t - 3;
+      if (interior && po >= s0 && po < s1) {
+        const int cell = base + po * sD;  // po is inside [s0, s1)
+        o_bA[cell] = nA_new;
+        o_bO[cell] = nO_new;
+      }
+    }
+    __syncthreads();
+    if (interior) {
+#pragma unroll
+      for (int j = 0; j < CH; j++) {
+        const int t = p0 + j;
+        const int pf = t - 2;  // b_D face updated by the edge flux f(t-5/2)
+        if (pf >= s0 && pf < s1) {
+          const float fa0 = fA_s[j][row][col], fa1 = fA_s[j][row][col + 1];
+          const float fo0 = fO_s[j][row][col], fo1 = fO_s[j][row + 1][col];
+          float b = bDold[j];
+          if (X::T1 == X::A) {
+            b += kA * (fa1 - fa0);
+            b += kO * (fo1 - fo0);
+          } else {
+            b += kO * (fo1 - fo0);
+            b += kA * (fa1 - fa0);
+          }
+          o_bD[base + pf * sD] = b;  // pf is inside [s0, s1)
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The x sweep stages rows in more than 48 KB of shared memory; the limit is
+// raised once per device before any launch (never during a graph capture).
+template <int LIM>
+cudaError_t prepare_mag_t() {
+  cudaError_t e = cudaFuncSetAttribute(mag_sweep_kernel<0, true, LIM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMagXSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mag_sweep_kernel<0, false, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMagXSmem);
+  return e;
+}
+
+template <int LIM>
+cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
+  const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
+  dim3 block(32, kMagWarps + 2);
+  dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
+  if (a.ens.items) grid = dim3(a.nblocks, 1, 1);  // one block per work item
+  const bool small = a.box.n[axis] < 16;
+#define MAG_CASE(DD, SMEM)                                                       \
+  if (axis == DD) {                                                              \
+    if (small) mag_sweep_kernel<DD, true, LIM><<<grid, block, SMEM, s>>>(a);     \
+    else mag_sweep_kernel<DD, false, LIM><<<grid, block, SMEM, s>>>(a);          \
+  }
+  MAG_CASE(0, kMagXSmem) MAG_CASE(1, 0) MAG_CASE(2, 0)
+#undef MAG_CASE
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,9 @@
+// Ablation of the paper's scheme: the exact fast magnetosonic speed as the
+// freezing speed of the fluid sweeps (its own translation unit).
+#include "sweep_fluid.cuh"
+
+namespace mhd {
+
+template cudaError_t launch_fluid_t<0, true>(int, bool, const FluidArgs&, cudaStream_t);
+
+}  // namespace mhd

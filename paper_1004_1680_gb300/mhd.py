@@ -47,6 +47,7 @@ SIGNATURES = {
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_set_pressure_floor": (_I, [_P, _D]),
+    "mhd_set_scheme": (_I, [_P, _I, _I]),
     "mhd_ens_set_pressure_floor": (_I, [_P, _D]),
     "mhd_diagnostics": (_I, [_P, _DP]),
     "mhd_profile": (_I, [_P, _I]),
@@ -225,6 +226,14 @@ class Box:
     def set_pressure_floor(self, p_floor: float):
         """Optional floor on the gas pressure after fluid sweeps (0 = off)."""
         _check(self.lib.mhd_set_pressure_floor(self.h, float(p_floor)))
+
+    LIMITERS = {"vanleer": 0, "minmod": 1, "superbee": 2}
+    FREEZING = {"bound": 0, "fast": 1}
+
+    def set_scheme(self, limiter: str = "vanleer", freezing: str = "bound"):
+        """Scheme variant (ablation) for the following sweeps; the default is
+        the paper's scheme."""
+        _check(self.lib.mhd_set_scheme(self.h, self.LIMITERS[limiter], self.FREEZING[freezing]))
 
     def set_xpath(self, mode: int):
         """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic."""

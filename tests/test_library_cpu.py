@@ -86,3 +86,7 @@ def test_submit_rejects_null_handle(lib):
     ptrs = (ctypes.c_void_p * 8)()
     assert lib.mhd_submit(None, ptrs, ptrs, 1, 0.7) == M.MHD_E_ARG
     assert lib.mhd_drain(None) == M.MHD_E_ARG
+
+
+def test_set_scheme_rejects_null_handle(lib):
+    assert lib.mhd_set_scheme(None, 0, 0) == M.MHD_E_ARG
