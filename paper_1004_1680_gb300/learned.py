@@ -98,8 +98,11 @@ class Norm:
 class Corrector:
     """Network + normalisation: correction of a coarse state."""
 
-    def __init__(self, net: CorrectionNet, norm: Norm, n):
+    def __init__(self, net: CorrectionNet, norm: Norm, n, alpha: float = 1.0):
+        """alpha scales the applied correction (the projection is linear, so
+        it scales the output scales)."""
         self.net, self.norm, self.n = net, norm, n
+        self.out_scale = [alpha * x for x in norm.out_scale]
         cells = n[0] * n[1] * n[2]
         dev = net.W[0].device
         self.x = torch.empty((cells, 8), dtype=torch.bfloat16, device=dev)
@@ -112,7 +115,7 @@ class Corrector:
         network input is the state before the step, as in the training pairs)."""
         mhd.cnn_normalize(state, self.norm.mu, self.norm.inv_sigma, out=self.x)
         y, _ = self.net.forward(self.x, self.n)
-        return mhd.cnn_project(y, self.n, self.norm.out_scale, out=self.d, sums=self.sums)
+        return mhd.cnn_project(y, self.n, self.out_scale, out=self.d, sums=self.sums)
 
     def apply(self, stepped: torch.Tensor, d: torch.Tensor, nclip=None):
         """Add a predicted correction to the state after the coarse step."""

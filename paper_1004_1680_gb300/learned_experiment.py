@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-seeds", type=int, default=4)
     ap.add_argument("--eval-steps", type=int, default=200)
+    ap.add_argument("--alphas", default="1.0",
+                    help="comma-separated scales of the applied correction to evaluate (1.0: as trained)")
     ap.add_argument("--json", default=None)
     args = ap.parse_args(argv)
     log = lambda s: print(s, file=sys.stderr, flush=True)  # noqa: E731
@@ -49,14 +51,18 @@ def main(argv=None):
     assert mhd.conv_error() == 0
     del inputs, targets
     torch.cuda.empty_cache()
-    corr = learned.Corrector(net, norm, (64, 64, 64))
-
-    res = []
-    for k in range(args.eval_seeds):
-        errs, gpu_ms, T, nclip = learned.evaluate(corr, 10000 + k, nsteps=args.eval_steps)
-        res.append((errs, gpu_ms, T, nclip))
-        log(f"seed {10000 + k}: T={T:.3f} " + " ".join(f"{n}={errs[n].mean():.4f}" for n in errs) +
-            f" clip={nclip}")
+    alphas = [float(a) for a in args.alphas.split(",")]
+    per_alpha = {}
+    for alpha in alphas:
+        corr = learned.Corrector(net, norm, (64, 64, 64), alpha=alpha)
+        res = []
+        for k in range(args.eval_seeds):
+            errs, gpu_ms, T, nclip = learned.evaluate(corr, 10000 + k, nsteps=args.eval_steps)
+            res.append((errs, gpu_ms, T, nclip))
+            log(f"alpha {alpha} seed {10000 + k}: T={T:.3f} " +
+                " ".join(f"{n}={errs[n].mean():.4f}" for n in errs) + f" clip={nclip}")
+        per_alpha[alpha] = res
+    res = per_alpha[alphas[0]]
     runs = ["plain64", "learned64", "plain128"]
     mean_err = {r: float(np.mean([x[0][r].mean() for x in res])) for r in runs}
     final_err = {r: float(np.mean([x[0][r][-1].mean() for x in res])) for r in runs}
@@ -68,6 +74,11 @@ def main(argv=None):
            "mean_nrmse": mean_err, "final_nrmse": final_err, "per_field_nrmse": per_field,
            "nrmse_every_20_steps": curve,
            "gpu_ms_per_run": gpu, "clipped_cells": [x[3] for x in res],
+           "alphas": {str(a): {"mean_nrmse": float(np.mean([x[0]["learned64"].mean() for x in r])),
+                               "final_nrmse": float(np.mean([x[0]["learned64"][-1].mean() for x in r])),
+                               "nrmse_every_20_steps": np.mean([x[0]["learned64"].mean(axis=1) for x in r],
+                                                               axis=0).tolist()}
+                      for a, r in per_alpha.items()},
            "claim_lower_error_than_plain128": mean_err["learned64"] < mean_err["plain128"],
            "claim_less_gpu_time_than_plain128": gpu["learned64"] < gpu["plain128"]}
     print("| run | mean NRMSE (8 fields, every 20 steps) | NRMSE at the last step | GPU ms per run |")
@@ -83,6 +94,11 @@ def main(argv=None):
     print("mean NRMSE after 20, 40, ... coarse steps:")
     for r in runs:
         print(f"  {r}: " + ", ".join(f"{v:.4f}" for v in curve[r]))
+    if len(alphas) > 1:
+        print()
+        print("learned 64^3 with the correction scaled by alpha (mean NRMSE; after 20, 40, ... steps):")
+        for a, r in out["alphas"].items():
+            print(f"  alpha {a}: {r['mean_nrmse']:.4f}; " + ", ".join(f"{v:.3f}" for v in r["nrmse_every_20_steps"]))
     print(f"training: {out['train_pairs']} pairs x {args.epochs} epochs in {train_s:.1f} s; "
           f"loss history {[round(h, 4) for h in hist]}")
     print(f"claim (learned 64^3 error < plain 128^3): {out['claim_lower_error_than_plain128']}; "
