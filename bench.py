@@ -61,6 +61,8 @@ def parse():
                    help="steps of the 256-box ensemble measurement (0: skip)")
     p.add_argument("--limiter", choices=["vanleer", "minmod", "superbee"], default="vanleer",
                    help="slope limiter (van Leer is the paper's; the others are ablations)")
+    p.add_argument("--xpath", type=int, choices=[0, 1, 2, 3], default=0,
+                   help="x sweep path (0 automatic; 3 = every axis through transposes, the paper's data flow)")
     p.add_argument("--freezing", choices=["bound", "fast"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
     p.add_argument("--learned-reps", type=int, default=20,
@@ -372,6 +374,8 @@ def run_ours(args, rank, world, local):
     N = n ** 3
     box = mhd.Box(n, n, n, gamma=5.0 / 3.0)
     box.set_scheme(args.limiter, args.freezing)
+    if args.xpath:
+        box.set_xpath(args.xpath)
     stream = torch.cuda.current_stream()
     st = ic.turbulence((n, n, n), seed=args.seed + rank, device="cuda", dtype=torch.float32)
     host = st.cpu().pin_memory()     # for the end-to-end leg
@@ -489,6 +493,7 @@ def run_ours(args, rank, world, local):
                           "n": n, "seed": args.seed, "cfl": args.cfl,
                           "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
+                          "xpath": args.xpath or "auto",
                           "l2": f"state {32 * N / 1e9:.1f} GB per copy > L2 (no flush needed)",
                           "parallelism": f"replicas x{world}"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -152,8 +152,11 @@ int mhd_set_segments(mhd_t *m, int seg_x, int seg_y, int seg_z);
  * exchanged (all 8 fields transposed once before a group of x sweeps and once
  * after; consecutive steps share one group, so a run of steps costs two
  * transposes per step), 0 = automatic (2 once the state exceeds 64 MiB).
- * Both paths compute the same update; results differ by FP32 rounding of
- * sums taken in another order. */
+ * 3 = the paper's data flow, as an ablation: every sweep runs along the
+ * contiguous axis of a copy transposed so that its axis is fastest (x<->y
+ * around the y sweeps, x<->z around the z sweeps; six transposes per step);
+ * needs every extent a multiple of 4.  All paths compute the same update;
+ * results differ by FP32 rounding of sums taken in another order. */
 int mhd_set_xpath(mhd_t *m, int mode);
 
 /* FP64 diagnostics of the current state, computed on the device with

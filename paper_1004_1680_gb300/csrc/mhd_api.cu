@@ -58,11 +58,13 @@ struct mhd_s {
   long long N;
   mhd::Box box;
   mhd::Box tbox;       // the same box with x and y exchanged
+  mhd::Box zbox;       // the same box with x and z exchanged (x path 3)
   float* arena = nullptr;
   float* cur[8];        // current copy of each field (in the current layout)
   float* spare[8];      // the other copy, written by the next kernel
-  int layout = 0;       // 0: x fastest; 1: x and y exchanged (for x sweeps)
-  int xpath = 0;        // x sweeps: 1 direct, 2 through the exchanged layout
+  int layout = 0;       // 0: x fastest; 1: x and y exchanged (for x sweeps); 2: x and z exchanged
+  int xpath = 0;        // x sweeps: 1 direct, 2 through the exchanged layout; 3: every
+                        // axis swept along the contiguous one (the paper's data flow)
   int xpath_req = 0;    // requested by mhd_set_xpath (0 = automatic)
   float p_floor = 0.f;  // optional pressure floor after fluid sweeps (0 = off)
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
@@ -166,20 +168,69 @@ int exchange_xy(mhd_s* m) {
   return MHD_OK;
 }
 
-int ensure_layout(mhd_s* m, int layout) { return m->layout == layout ? MHD_OK : exchange_xy(m); }
+// Exchange x and z of all fields (out of place), between layouts 0 and 2;
+// slots 1 / 5 and 3 / 7 are relabelled as for exchange_xy.
+int exchange_xz(mhd_s* m) {
+  mhd::TransposeArgs a;
+  const mhd::Box& b = m->layout == 0 ? m->box : m->zbox;
+  for (int q = 0; q < 8; q++) {
+    a.in[q] = m->cur[q];
+    a.out[q] = m->spare[q];
+  }
+  a.n[0] = b.n[0];
+  a.n[1] = b.n[1];
+  a.n[2] = b.n[2];
+  int rc = traced(m, MHD_K_TRANSPOSE, [&] {
+    CK(mhd::launch_transpose02(a, m->stream));
+    return MHD_OK;
+  });
+  if (rc) return rc;
+  static const int relabel[8] = {0, 3, 2, 1, 4, 7, 6, 5};
+  float* nc[8];
+  float* ns[8];
+  for (int q = 0; q < 8; q++) {
+    nc[relabel[q]] = m->spare[q];
+    ns[relabel[q]] = m->cur[q];
+  }
+  for (int q = 0; q < 8; q++) {
+    m->cur[q] = nc[q];
+    m->spare[q] = ns[q];
+  }
+  m->layout = m->layout == 0 ? 2 : 0;
+  return MHD_OK;
+}
+
+int ensure_layout(mhd_s* m, int layout) {
+  if (m->layout == layout) return MHD_OK;
+  int rc = MHD_OK;
+  if (m->layout == 1) rc = exchange_xy(m);
+  if (!rc && m->layout == 2) rc = exchange_xz(m);
+  if (!rc && layout == 1) rc = exchange_xy(m);
+  if (!rc && layout == 2) rc = exchange_xz(m);
+  return rc;
+}
 
 // Frame of a sweep along physical axis d: the layout it runs in, the box as
 // the kernels see it and the kernel axis.  y sweeps need x fastest; x sweeps
 // run in the exchanged layout when xpath == 2 (as kernel axis 1); z sweeps
-// run in whichever layout is current.
+// run in whichever layout is current.  With xpath == 3 every sweep runs along
+// the contiguous axis (kernel axis 0) of the layout that makes d the fastest.
 int sweep_frame(mhd_s* m, int d, const mhd::Box** box, int* kaxis) {
   int want = m->layout;
-  if (d == 0) want = (m->xpath == 2) ? 1 : 0;
-  if (d == 1) want = 0;
+  if (m->xpath == 3) {
+    want = d;  // layout 0: x fastest, 1: y fastest, 2: z fastest
+  } else {
+    if (d == 0) want = (m->xpath == 2) ? 1 : 0;
+    if (d == 1) want = 0;
+    if (d == 2 && want == 2) want = 0;
+  }
   int rc = ensure_layout(m, want);
   if (rc) return rc;
-  *box = m->layout ? &m->tbox : &m->box;
-  *kaxis = (m->layout && d < 2) ? 1 - d : d;
+  *box = m->layout == 2 ? &m->zbox : (m->layout ? &m->tbox : &m->box);
+  if (m->layout == 2)
+    *kaxis = (d == 2) ? 0 : (d == 0 ? 2 : 1);
+  else
+    *kaxis = (m->layout && d < 2) ? 1 - d : d;
   return MHD_OK;
 }
 
@@ -369,6 +420,12 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   m->tbox.stride[0] = 1;
   m->tbox.stride[1] = ny;
   m->tbox.stride[2] = (long long)nx * ny;
+  m->zbox.n[0] = nz;
+  m->zbox.n[1] = ny;
+  m->zbox.n[2] = nx;
+  m->zbox.stride[0] = 1;
+  m->zbox.stride[1] = nz;
+  m->zbox.stride[2] = (long long)nz * ny;
   m->xpath = auto_xpath(m);
   const int nblk = mhd::diag_blocks(m->box);
   if ((e = cudaMalloc(&m->sc, sizeof(Scalars))) != cudaSuccess ||
@@ -409,10 +466,11 @@ int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
   if (int rc = join_pipeline(m)) return rc;
   const size_t bytes = sizeof(float) * (size_t)m->N;
   if (m->layout) {  // back to the plain layout (the old state is overwritten)
-    std::swap(m->cur[1], m->cur[2]);
-    std::swap(m->spare[1], m->spare[2]);
-    std::swap(m->cur[5], m->cur[6]);
-    std::swap(m->spare[5], m->spare[6]);
+    const int a = m->layout == 1 ? 2 : 3;  // the slot exchanged with x
+    std::swap(m->cur[1], m->cur[a]);
+    std::swap(m->spare[1], m->spare[a]);
+    std::swap(m->cur[5], m->cur[4 + a]);
+    std::swap(m->spare[5], m->spare[4 + a]);
     m->layout = 0;
   }
   for (int q = 0; q < 8; q++)
@@ -563,7 +621,9 @@ int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {
 
 int mhd_set_xpath(mhd_t* m, int mode) {
   if (!check_box(m)) return MHD_E_ARG;
-  if (mode < 0 || mode > 2) return fail(MHD_E_ARG, "x path mode must be 0, 1 or 2");
+  if (mode < 0 || mode > 3) return fail(MHD_E_ARG, "x path mode must be 0, 1, 2 or 3");
+  if (mode == 3 && (m->n[0] % 4 || m->n[1] % 4 || m->n[2] % 4 || m->n[1] > 65535))
+    return fail(MHD_E_ARG, "x path 3 needs every extent a multiple of 4 (and ny <= 65535)");
   if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
   m->xpath_req = mode;
   m->xpath = mode ? mode : auto_xpath(m);

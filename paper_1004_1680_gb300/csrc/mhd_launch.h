@@ -145,6 +145,7 @@ cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, c
 
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);
+cudaError_t launch_transpose02(const TransposeArgs& a, cudaStream_t s);  // single box only
 // ensemble step control: for every box b < nbox, tau[b] = cfl / rate_cur[b]
 // (0 for an invalid state), time[b] += 2 tau[b], rate_next[b] = 0
 cudaError_t launch_ens_control(const unsigned* rate_cur, unsigned* rate_next, float* tau,

@@ -51,6 +51,44 @@ transpose01_kernel(TransposeArgs a) {
   }
 }
 
+// Exchange of the fastest and the slowest axis (x and z) of all 8 fields of
+// one box, for the ablation that sweeps every axis along the contiguous one
+// (the paper's data flow): out[q][k + n2*(j + n1*i)] = in[q][i + n0*(j + n1*k)].
+// A block moves one 32x32 tile of the (i, k) plane at fixed j.
+__global__ void __launch_bounds__(kTile * kTRows)
+transpose02_kernel(TransposeArgs a) {
+  __shared__ float tile[8][kTile][kTile + 1];
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const int i0 = blockIdx.x * kTile, k0 = blockIdx.y * kTile, j = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long in_row = (long long)n0 * j, in_plane = (long long)n0 * n1;
+  const long long out_row = (long long)n2 * j, out_plane = (long long)n2 * n1;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+#pragma unroll
+    for (int r = 0; r < kTile / kTRows; r++) {
+      const int i = i0 + tx, k = k0 + ty + kTRows * r;
+      if (i < n0 && k < n2) tile[q][ty + kTRows * r][tx] = __ldg(a.in[q] + i + in_row + in_plane * k);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+#pragma unroll
+    for (int r = 0; r < kTile / kTRows; r++) {
+      const int k = k0 + tx, i = i0 + ty + kTRows * r;
+      if (i < n0 && k < n2) a.out[q][k + out_row + out_plane * i] = tile[q][tx][ty + kTRows * r];
+    }
+  }
+}
+
+cudaError_t launch_transpose02(const TransposeArgs& a, cudaStream_t s) {
+  dim3 block(kTile, kTRows);
+  dim3 grid((a.n[0] + kTile - 1) / kTile, (a.n[2] + kTile - 1) / kTile, a.n[1]);
+  transpose02_kernel<<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s) {
   dim3 block(kTile, kTRows);
   dim3 grid((a.n[0] + kTile - 1) / kTile, (a.n[1] + kTile - 1) / kTile, a.n[2]);

@@ -236,7 +236,9 @@ class Box:
         _check(self.lib.mhd_set_scheme(self.h, self.LIMITERS[limiter], self.FREEZING[freezing]))
 
     def set_xpath(self, mode: int):
-        """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic."""
+        """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic;
+        3: every sweep along the contiguous axis of a transposed copy (the
+        paper's data flow, an ablation)."""
         _check(self.lib.mhd_set_xpath(self.h, int(mode)))
 
     def profile(self, capacity: int):

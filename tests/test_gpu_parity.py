@@ -83,7 +83,7 @@ def test_x_sweep_both_paths(mhd, xpath, kind):
         assert np.all(err < 1e-5), (dims, err)
 
 
-@pytest.mark.parametrize("xpath", [1, 2])
+@pytest.mark.parametrize("xpath", [1, 2, 3])
 def test_full_steps_both_x_paths(mhd, xpath):
     st = ic.turbulence((40, 24, 20), seed=24, dtype=torch.float64, kmin=1.0, kmax=3.0)
     s = oracle_input(st)
@@ -95,6 +95,26 @@ def test_full_steps_both_x_paths(mhd, xpath):
     assert box.time() == pytest.approx(t_orc, rel=1e-5)
     err = rel_err(from_gpu(box.get_state()), s, S)
     assert np.all(err < 1e-4), err
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_paper_data_flow_single_sweeps(mhd, axis, kind):
+    """x path 3 (every sweep along the contiguous axis of a transposed copy)
+    against the oracle, one sweep of each axis and kind on a box whose three
+    extents differ."""
+    st = ic.turbulence((48, 40, 36), seed=25, dtype=torch.float64, kmin=1.0, kmax=3.0)
+    s = oracle_input(st)
+    tau = 0.35 / oracle.cfl_rate(s, G)
+    box = make_box(mhd, st)
+    box.set_xpath(3)
+    box.sweep(axis, kind, tau)
+    g = from_gpu(box.get_state())
+    if kind == 0:
+        oracle.fluid_sweep(s, axis, tau, G)
+    else:
+        oracle.mag_sweep(s, axis, tau)
+    assert np.all(rel_err(g, s, field_scales(s)) < 1e-5)
 
 
 @pytest.mark.parametrize("segs", [(16, 8, 12), (8, 20, 4), (48, 40, 36)])
