@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local):
 
     box.run(args.warmup, args.cfl)
     box.cfl_dt(args.cfl)               # raises if the state went invalid
-    launches_per_step = 13
+    launches_per_step = 19             # 12 sweeps, step control, up to 6 transposes (x path 3)
     box.profile(args.steps * launches_per_step + 16)
 
     uuid = None
