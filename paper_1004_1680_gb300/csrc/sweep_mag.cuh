@@ -82,8 +82,10 @@ __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_kernel(MagArgs a) {
   using X = MagAxes<D>;
   constexpr int CH = (D == 0) ? kMXChunk : 4;
-  __shared__ float fA_s[CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
-  __shared__ float fO_s[CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
+  // double-buffered by chunk parity: a chunk's fluxes are written while the
+  // previous chunk's may still be read, so one barrier per chunk suffices
+  __shared__ float fA_s[2][CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
+  __shared__ float fO_s[2][CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
   extern __shared__ float xs_dyn[];               // x sweeps only: staged rows
 
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -200,8 +202,8 @@ mag_sweep_kernel(MagArgs a) {
       float nA_new = 0.f, nO_new = 0.f, fa = 0.f, fo = 0.f;
       if (w != kMagWarps) fa = pA.step(qAj, uA, c_half, c_full, nA_new);
       if (w != kMagWarps + 1) fo = pO.step(qOj, uO, c_half, c_full, nO_new);
-      if (write_row) fO_s[j][row][col] = fo;
-      if (write_col) fA_s[j][row][col] = fa;
+      if (write_row) fO_s[c & 1][j][row][col] = fo;
+      if (write_col) fA_s[c & 1][j][row][col] = fa;
       bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
       bD2 = bD1;
       bD1 = qDj;
@@ -220,8 +222,8 @@ mag_sweep_kernel(MagArgs a) {
         const int t = p0 + j;
         const int pf = t - 2;  // b_D face updated by the edge flux f(t-5/2)
         if (pf >= s0 && pf < s1) {
-          const float fa0 = fA_s[j][row][col], fa1 = fA_s[j][row][col + 1];
-          const float fo0 = fO_s[j][row][col], fo1 = fO_s[j][row + 1][col];
+          const float fa0 = fA_s[c & 1][j][row][col], fa1 = fA_s[c & 1][j][row][col + 1];
+          const float fo0 = fO_s[c & 1][j][row][col], fo1 = fO_s[c & 1][j][row + 1][col];
           float b = bDold[j];
           if (X::T1 == X::A) {
             b += kA * (fa1 - fa0);
@@ -234,7 +236,6 @@ mag_sweep_kernel(MagArgs a) {
         }
       }
     }
-    __syncthreads();
   }
 }
 
