@@ -123,7 +123,7 @@ __device__ __forceinline__ void split_flux_t(const T u[5], const T b[3], float g
   const T p = v_mul(v_const<T>(gamma - 1.f), v_fma(v_const<T>(-0.5f), b2, v_sub(u[4], kin)));
   const T pstar = v_fma(half, b2, p);
   const T bv = v_fma(b[0], vd, v_fma(b[1], v1, v_mul(b[2], v2)));
-  const T nb0 = v_mul(b[0], v_const<T>(-1.f));
+  const T nb0 = -b[0];  // exact; folds into the multiply-adds
   T F[5];
   F[0] = u[1];
   F[1] = v_fma(u[1], vd, v_fma(nb0, b[0], pstar));
@@ -198,8 +198,10 @@ struct FluidPipeT {
   T b1[3];                // frozen b at t-1
   T FR1[5];               // stage-1 right mover at t-1
   T f1m[5];               // stage-1 interface flux at t-3/2
-  T Rh2[5], Rh3[5], Rh4[5];  // stage-2 right movers at t-2, t-3, t-4
-  T Lh2[5], Lh3[5];          // stage-2 left movers at t-2, t-3
+  T Rh2[5], Rh3[5];       // stage-2 right movers at t-2, t-3
+  T dR3[5];                // Rh(t-3) - Rh(t-4), carried from the previous step
+  T Lh2[5];                // stage-2 left mover at t-2
+  T dL2[5];                // Lh(t-2) - Lh(t-3), carried from the previous step
   T F2m[5];               // stage-2 interface flux at t-7/2
 
   __device__ __forceinline__ void init() {
@@ -207,7 +209,7 @@ struct FluidPipeT {
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = z;
-      Rh2[q] = Rh3[q] = Rh4[q] = Lh2[q] = Lh3[q] = F2m[q] = z;
+      Rh2[q] = Rh3[q] = dR3[q] = Lh2[q] = dL2[q] = F2m[q] = z;
     }
     b1[0] = b1[1] = b1[2] = z;
   }
@@ -229,8 +231,10 @@ struct FluidPipeT {
     split_flux_t<T, FAST>(Uh, b1, gamma, Rh, Lh);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      const T right = v_add(Rh3[q], half_limited<LIM>(v_sub(Rh3[q], Rh4[q]), v_sub(Rh2[q], Rh3[q])));
-      const T left = v_sub(Lh2[q], half_limited<LIM>(v_sub(Lh2[q], Lh3[q]), v_sub(Lh[q], Lh2[q])));
+      // the left-hand differences were the right-hand ones one step earlier
+      const T dR2 = v_sub(Rh2[q], Rh3[q]), dL1 = v_sub(Lh[q], Lh2[q]);
+      const T right = v_add(Rh3[q], half_limited<LIM>(dR3[q], dR2));
+      const T left = v_sub(Lh2[q], half_limited<LIM>(dL2[q], dL1));
       const T F2 = v_sub(right, left);
       out[q] = v_fma(ncf, v_sub(F2, F2m[q]), U3[q]);
       F2m[q] = F2;
@@ -240,10 +244,10 @@ struct FluidPipeT {
       U1[q] = U[q];
       FR1[q] = FR[q];
       f1m[q] = f1[q];
-      Rh4[q] = Rh3[q];
+      dR3[q] = dR2;
       Rh3[q] = Rh2[q];
       Rh2[q] = Rh[q];
-      Lh3[q] = Lh2[q];
+      dL2[q] = dL1;
       Lh2[q] = Lh[q];
     }
     b1[0] = b[0];
