@@ -41,6 +41,7 @@ UNIT = "cell-updates/s"
 #   fluid sweep: reads rho, m (3), e, b (3) = 32 B, writes rho, m, e = 20 B
 #   magnetic sweep: reads rho, m_d, b (3) = 20 B, writes b (3) = 12 B
 ALGO_BYTES = {"fluid": 52, "mag": 32}
+TRANSPOSE_BYTES = 64   # x<->y exchange: read and write 8 fields
 STEP_BYTES = 384  # 6 sweeps x (read + write of 8 FP32 fields): the full-step model
 P_FLOOR_ENSEMBLE = 1e-3
 
@@ -425,8 +426,9 @@ def run_ours(args, rank, world, local):
     achieved = ALGO_BYTES[dom] * N / avg_s / 1e9
     peak, peak_kind = peaks()
     traffic = measured_traffic(dom, n)
+    fam_bytes = {"fluid": ALGO_BYTES["fluid"], "mag": ALGO_BYTES["mag"], "transpose": TRANSPOSE_BYTES}
     per_kernel = {k: {"launches": c, "avg_ms": (ms / c if c else None),
-                      "GB/s": ((ALGO_BYTES["fluid" if k.startswith("fluid") else "mag"] * N / (ms / c / 1e3) / 1e9)
+                      "GB/s": ((fam_bytes[k.split("_")[0]] * N / (ms / c / 1e3) / 1e9)
                                if c and k != "control" else None)}
                   for k, (c, ms) in prof.items()}
     launches = sum(c for c, _ in prof.values())
