@@ -80,10 +80,6 @@ __device__ __forceinline__ float v_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ float v_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ float v_keep(float x, float q) { return keep_if_positive(x, q); }
 
-template <class T>
-__device__ __forceinline__ T v_const(float s);
-template <>
-__device__ __forceinline__ float v_const<float>(float s) { return s; }
 
 // Half a slope limiter, phi(a,b)/2, of two neighbouring differences; 0
 // unless they have the same sign.  LIM 0: van Leer, the limiter of Section
@@ -105,48 +101,84 @@ __device__ __forceinline__ float half_limited(float a, float b) {
   }
 }
 
+// The five conserved components of a cell as two pairs and a scalar,
+// (rho, m_d), (m_t1, m_t2), e, so that the component-wise parts of the
+// pipeline run on packed FP32 (two components per instruction, Blackwell's
+// FFMA2 / FADD2 / FMUL2).  Every element is rounded exactly as the scalar
+// operation would round it.
+struct V5 {
+  float2 p0, p1;
+  float e;
+};
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+// a - b = fma(b, -1, a): the product is exact, so one rounding as in __fsub_rn
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+__device__ __forceinline__ V5 v5_sub(const V5& a, const V5& b) {
+  return {sub2(a.p0, b.p0), sub2(a.p1, b.p1), __fsub_rn(a.e, b.e)};
+}
+__device__ __forceinline__ V5 v5_add(const V5& a, const V5& b) {
+  return {__fadd2_rn(a.p0, b.p0), __fadd2_rn(a.p1, b.p1), __fadd_rn(a.e, b.e)};
+}
+// s x + y
+__device__ __forceinline__ V5 v5_fma(float s, const V5& x, const V5& y) {
+  return {__ffma2_rn(f2(s), x.p0, y.p0), __ffma2_rn(f2(s), x.p1, y.p1), __fmaf_rn(s, x.e, y.e)};
+}
+__device__ __forceinline__ V5 v5_zero() { return {f2(0.f), f2(0.f), 0.f}; }
+
+template <int LIM>
+__device__ __forceinline__ float2 half_limited2(float2 a, float2 b) {
+  if constexpr (LIM == 0) {
+    const float2 ab = __fmul2_rn(a, b), s = __fadd2_rn(a, b);
+    return make_float2(v_keep(ab.x, v_div(ab.x, s.x)), v_keep(ab.y, v_div(ab.y, s.y)));
+  } else {
+    return make_float2(half_limited<LIM>(a.x, b.x), half_limited<LIM>(a.y, b.y));
+  }
+}
+template <int LIM>
+__device__ __forceinline__ V5 half_limited5(const V5& a, const V5& b) {
+  return {half_limited2<LIM>(a.p0, b.p0), half_limited2<LIM>(a.p1, b.p1), half_limited<LIM>(a.e, b.e)};
+}
+
 // Flux of Eq. 2-3 projected on the sweep axis d, in the sweep's local frame
-// (u = (rho, m_d, m_t1, m_t2, e), b = cell-centred (b_d, b_t1, b_t2)), and the
-// relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
+// (u = (rho, m_d, m_t1, m_t2, e), b = cell-centred (b_d, (b_t1, b_t2))), and
+// the relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
 // bounds the fastest local wave speed (Section II.B, relaxing TVD).
 // Returns the right and left movers FR = (cu + F)/2, FL = FR - F = (cu - F)/2.
 // FAST = true replaces the bound by |v_d| + the fast magnetosonic speed along
 // d, c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2))/2, s = a^2 + v_A^2 (an ablation:
 // the smallest freezing speed the relaxation allows).
-template <class T, bool FAST = false>
-__device__ __forceinline__ void split_flux_t(const T u[5], const T b[3], float gamma, T FR[5], T FL[5]) {
-  const T half = v_const<T>(0.5f);
-  const T rinv = v_div(v_const<T>(1.f), u[0]);
-  const T vd = v_mul(u[1], rinv), v1 = v_mul(u[2], rinv), v2 = v_mul(u[3], rinv);
-  const T b2 = v_fma(b[0], b[0], v_fma(b[1], b[1], v_mul(b[2], b[2])));
-  const T kin = v_mul(half, v_fma(u[1], vd, v_fma(u[2], v1, v_mul(u[3], v2))));
-  const T p = v_mul(v_const<T>(gamma - 1.f), v_fma(v_const<T>(-0.5f), b2, v_sub(u[4], kin)));
-  const T pstar = v_fma(half, b2, p);
-  const T bv = v_fma(b[0], vd, v_fma(b[1], v1, v_mul(b[2], v2)));
-  const T nb0 = -b[0];  // exact; folds into the multiply-adds
-  T F[5];
-  F[0] = u[1];
-  F[1] = v_fma(u[1], vd, v_fma(nb0, b[0], pstar));
-  F[2] = v_fma(u[2], vd, v_mul(nb0, b[1]));
-  F[3] = v_fma(u[3], vd, v_mul(nb0, b[2]));
-  F[4] = v_fma(v_add(u[4], pstar), vd, v_mul(nb0, bv));
-  T cs;
+template <bool FAST = false>
+__device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, float gamma, V5& FR, V5& FL) {
+  const float md = u.p0.y;
+  const float rinv = v_div(1.f, u.p0.x);
+  const float vd = v_mul(md, rinv);
+  const float2 vt = __fmul2_rn(u.p1, f2(rinv));
+  const float b2 = v_fma(bd, bd, v_fma(bt.x, bt.x, v_mul(bt.y, bt.y)));
+  const float kin = v_mul(0.5f, v_fma(md, vd, v_fma(u.p1.x, vt.x, v_mul(u.p1.y, vt.y))));
+  const float p = v_mul(gamma - 1.f, v_fma(-0.5f, b2, v_sub(u.e, kin)));
+  const float pstar = v_fma(0.5f, b2, p);
+  const float bv = v_fma(bd, vd, v_fma(bt.x, vt.x, v_mul(bt.y, vt.y)));
+  const float nb0 = -bd;  // exact; folds into the multiply-adds
+  const float2 F01 = make_float2(md, v_fma(md, vd, v_fma(nb0, bd, pstar)));
+  const float2 F23 = __ffma2_rn(u.p1, f2(vd), __fmul2_rn(f2(nb0), bt));
+  const float F4 = v_fma(v_add(u.e, pstar), vd, v_mul(nb0, bv));
+  float cs;
   if constexpr (FAST) {
-    const T a2 = v_mul(v_mul(v_const<T>(gamma), p), rinv), va2 = v_mul(b2, rinv);
-    const T vad2 = v_mul(v_mul(b[0], b[0]), rinv);
-    const T sum = v_add(a2, va2);
-    const T disc = v_fma(v_mul(v_const<T>(-4.f), a2), vad2, v_mul(sum, sum));
-    cs = v_sqrt(v_mul(half, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))));
+    const float a2 = v_mul(v_mul(gamma, p), rinv), va2 = v_mul(b2, rinv);
+    const float vad2 = v_mul(v_mul(bd, bd), rinv);
+    const float sum = v_add(a2, va2);
+    const float disc = v_fma(v_mul(-4.f, a2), vad2, v_mul(sum, sum));
+    cs = v_sqrt(v_mul(0.5f, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))));
   } else {
-    cs = v_sqrt(v_mul(v_fma(v_const<T>(gamma), p, b2), rinv));
+    cs = v_sqrt(v_mul(v_fma(gamma, p, b2), rinv));
   }
-  const T c = v_add(v_abs(vd), cs);
-  const T hc = v_mul(half, c);
-#pragma unroll
-  for (int q = 0; q < 5; q++) {
-    FR[q] = v_fma(hc, u[q], v_mul(half, F[q]));
-    FL[q] = v_sub(FR[q], F[q]);
-  }
+  const float hc = v_mul(0.5f, v_add(v_abs(vd), cs));
+  FR.p0 = __ffma2_rn(f2(hc), u.p0, __fmul2_rn(f2(0.5f), F01));
+  FR.p1 = __ffma2_rn(f2(hc), u.p1, __fmul2_rn(f2(0.5f), F23));
+  FR.e = v_fma(hc, u.e, v_mul(0.5f, F4));
+  FL.p0 = sub2(FR.p0, F01);
+  FL.p1 = sub2(FR.p1, F23);
+  FL.e = v_sub(FR.e, F4);
 }
 
 // Largest signal rate of one cell, max_d (|v_d| + c_f*) * n_d, in the global
@@ -192,71 +224,62 @@ __device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_r
 //             Unew(t-3)    = U(t-3) - tau/h (F2(t-5/2) - F2(t-7/2))
 // so Unew at position t-3 is produced at step t (the 7-point stencil of
 // Section II.B).  Every intermediate value is held in registers.
-template <class T, int LIM = 0, bool FAST = false>
-struct FluidPipeT {
-  T U1[5], U2[5], U3[5];  // raw U at t-1, t-2, t-3
-  T b1[3];                // frozen b at t-1
-  T FR1[5];               // stage-1 right mover at t-1
-  T f1m[5];               // stage-1 interface flux at t-3/2
-  T Rh2[5], Rh3[5];       // stage-2 right movers at t-2, t-3
-  T dR3[5];                // Rh(t-3) - Rh(t-4), carried from the previous step
-  T Lh2[5];                // stage-2 left mover at t-2
-  T dL2[5];                // Lh(t-2) - Lh(t-3), carried from the previous step
-  T F2m[5];               // stage-2 interface flux at t-7/2
+template <int LIM = 0, bool FAST = false>
+struct FluidPipe {
+  V5 U1, U2, U3;   // raw U at t-1, t-2, t-3
+  float b1[3];     // frozen b at t-1
+  V5 FR1;          // stage-1 right mover at t-1
+  V5 f1m;          // stage-1 interface flux at t-3/2
+  V5 Rh2, Rh3;     // stage-2 right movers at t-2, t-3
+  V5 dR3;          // Rh(t-3) - Rh(t-4), carried from the previous step
+  V5 Lh2;          // stage-2 left mover at t-2
+  V5 dL2;          // Lh(t-2) - Lh(t-3), carried from the previous step
+  V5 F2m;          // stage-2 interface flux at t-7/2
 
   __device__ __forceinline__ void init() {
-    const T z = v_const<T>(0.f);
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-      U1[q] = U2[q] = U3[q] = FR1[q] = f1m[q] = z;
-      Rh2[q] = Rh3[q] = dR3[q] = Lh2[q] = dL2[q] = F2m[q] = z;
-    }
-    b1[0] = b1[1] = b1[2] = z;
+    U1 = U2 = U3 = FR1 = f1m = Rh2 = Rh3 = dR3 = Lh2 = dL2 = F2m = v5_zero();
+    b1[0] = b1[1] = b1[2] = 0.f;
   }
 
   // Consume position t; write Unew(t-3) into out.  c_half = tau/(2h),
   // c_full = tau/h.
-  __device__ __forceinline__ void step(const T U[5], const T b[3], float gamma, float c_half, float c_full,
-                                       T out[5]) {
-    T FR[5], FL[5];
-    split_flux_t<T, FAST>(U, b, gamma, FR, FL);
-    const T nch = v_const<T>(-c_half), ncf = v_const<T>(-c_full);
-    T Uh[5], f1[5];
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-      f1[q] = v_sub(FR1[q], FL[q]);
-      Uh[q] = v_fma(nch, v_sub(f1[q], f1m[q]), U1[q]);
-    }
-    T Rh[5], Lh[5];
-    split_flux_t<T, FAST>(Uh, b1, gamma, Rh, Lh);
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-      // the left-hand differences were the right-hand ones one step earlier
-      const T dR2 = v_sub(Rh2[q], Rh3[q]), dL1 = v_sub(Lh[q], Lh2[q]);
-      const T right = v_add(Rh3[q], half_limited<LIM>(dR3[q], dR2));
-      const T left = v_sub(Lh2[q], half_limited<LIM>(dL2[q], dL1));
-      const T F2 = v_sub(right, left);
-      out[q] = v_fma(ncf, v_sub(F2, F2m[q]), U3[q]);
-      F2m[q] = F2;
-      // shift the windows
-      U3[q] = U2[q];
-      U2[q] = U1[q];
-      U1[q] = U[q];
-      FR1[q] = FR[q];
-      f1m[q] = f1[q];
-      dR3[q] = dR2;
-      Rh3[q] = Rh2[q];
-      Rh2[q] = Rh[q];
-      dL2[q] = dL1;
-      Lh2[q] = Lh[q];
-    }
+  __device__ __forceinline__ void step(const float U[5], const float b[3], float gamma, float c_half,
+                                       float c_full, float out[5]) {
+    const V5 u = {make_float2(U[0], U[1]), make_float2(U[2], U[3]), U[4]};
+    V5 FR, FL;
+    split_flux<FAST>(u, b[0], make_float2(b[1], b[2]), gamma, FR, FL);
+    const V5 f1 = v5_sub(FR1, FL);
+    const V5 Uh = v5_fma(-c_half, v5_sub(f1, f1m), U1);
+    V5 Rh, Lh;
+    split_flux<FAST>(Uh, b1[0], make_float2(b1[1], b1[2]), gamma, Rh, Lh);
+    // the left-hand differences were the right-hand ones one step earlier
+    const V5 dR2 = v5_sub(Rh2, Rh3), dL1 = v5_sub(Lh, Lh2);
+    const V5 right = v5_add(Rh3, half_limited5<LIM>(dR3, dR2));
+    const V5 left = v5_sub(Lh2, half_limited5<LIM>(dL2, dL1));
+    const V5 F2 = v5_sub(right, left);
+    const V5 o = v5_fma(-c_full, v5_sub(F2, F2m), U3);
+    out[0] = o.p0.x;
+    out[1] = o.p0.y;
+    out[2] = o.p1.x;
+    out[3] = o.p1.y;
+    out[4] = o.e;
+    // shift the windows
+    F2m = F2;
+    U3 = U2;
+    U2 = U1;
+    U1 = u;
+    FR1 = FR;
+    f1m = f1;
+    dR3 = dR2;
+    Rh3 = Rh2;
+    Rh2 = Rh;
+    dL2 = dL1;
+    Lh2 = Lh;
     b1[0] = b[0];
     b1[1] = b[1];
     b1[2] = b[2];
   }
 };
-template <int LIM, bool FAST>
-using FluidPipe = FluidPipeT<float, LIM, FAST>;
 
 // ---------------------------------------------------------------------------
 // Magnetic advection pipeline for one transverse component q = b_t along the
