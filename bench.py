@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--size", type=int, default=512)
     p.add_argument("--cfl", type=float, default=0.7)
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-sample", type=int, default=128, help="edge of the oracle's sample box")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100,
