@@ -64,6 +64,8 @@ def parse():
                    help="slope limiter (van Leer is the paper's; the others are ablations)")
     p.add_argument("--xpath", type=int, choices=[0, 1, 2, 3], default=0,
                    help="x sweep path (0 automatic; 3 = every axis through transposes, the paper's data flow)")
+    p.add_argument("--seg", type=int, default=0,
+                   help="pencil segment length for every axis (0: the library's choice)")
     p.add_argument("--freezing", choices=["bound", "fast"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
     p.add_argument("--learned-reps", type=int, default=20,
@@ -377,6 +379,8 @@ def run_ours(args, rank, world, local):
     box.set_scheme(args.limiter, args.freezing)
     if args.xpath:
         box.set_xpath(args.xpath)
+    if args.seg:
+        box.set_segments(args.seg, args.seg, args.seg)
     stream = torch.cuda.current_stream()
     st = ic.turbulence((n, n, n), seed=args.seed + rank, device="cuda", dtype=torch.float32)
     host = st.cpu().pin_memory()     # for the end-to-end leg

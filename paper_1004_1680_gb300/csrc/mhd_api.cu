@@ -74,6 +74,7 @@ struct mhd_s {
   int rcur = 0;
   cudaStream_t stream = nullptr;
   int seg[3];
+  int sms = 0;          // multiprocessors of the device (segment choice)
   // tracing: event pairs around launches (see mhd_profile)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
@@ -97,17 +98,48 @@ namespace {
 // only L2 can absorb).
 int auto_xpath(const mhd_s* m) { return m->N * 32LL > (64LL << 20) ? 2 : 1; }
 
-// Segment length along each axis: whole pencils when they already give the
-// GPU enough threads, otherwise split pencils (each split re-reads 8 cells of
-// warm-up) down to 32 cells.
+// Segment length along each axis.  Splitting pencils into segments adds 7
+// cells of warm-up per segment but gives the GPU more threads.  First split
+// until the pencil segments give about one full wave of threads (152 x 1024:
+// enough warps to hide latency); then, since a sweep runs ceil(n_A/32) x
+// ceil(n_O/W) blocks per segment of every pencil (W = 4 rows for the fluid
+// sweep, 8 for the magnetic one), take among that and further splits (at
+// least 32 cells, multiples of 8) the one that minimises (warm-up work) /
+// sqrt(last-wave efficiency) summed over the two sweeps, with the resident
+// blocks per SM of each kernel (fluid 4, magnetic 2).
 int choose_seg(const mhd_s* m, int d) {
   const int nd = m->n[d];
   const long long pencils = m->N / nd;
-  const long long want = 152LL * 1024;  // threads for about one full wave of the GPU
-  int seg = nd;
-  while (pencils * (nd / seg) < want && seg % 8 == 0 && seg / 2 >= 32 && nd % (seg / 2) == 0)
+  const long long want = 152LL * 1024;
+  int first = nd;
+  while (pencils * (nd / first) < want && first % 8 == 0 && first / 2 >= 32 && nd % (first / 2) == 0)
+    first /= 2;
+  const int nA = m->n[d == 0 ? 1 : 0], nO = m->n[d == 2 ? 1 : 2];
+  const double sms = m->sms > 0 ? m->sms : 152;
+  auto cost = [&](int seg) {
+    double c = 0.0;
+    const int rows[2] = {4, mhd::kMagWarps}, resident[2] = {4, 2};
+    for (int k = 0; k < 2; k++) {
+      const double blocks = (double)((nA + 31) / 32) * ((nO + rows[k] - 1) / rows[k]) * (nd / seg);
+      const double waves = blocks / (sms * resident[k]);
+      // a partial last wave costs less than its idle fraction (the SMs that
+      // run it go faster alone): its weight enters as a square root, which
+      // matches measured sweeps at 256^3, 512^3 and 1024^3
+      c += (double)(seg + 7) / seg * std::sqrt(std::ceil(waves) / waves);
+    }
+    return c;
+  };
+  int best = first;
+  double best_cost = cost(first);
+  for (int seg = first; seg % 8 == 0 && seg / 2 >= 32 && nd % (seg / 2) == 0;) {
     seg /= 2;
-  return seg;
+    const double c = cost(seg);
+    if (c < best_cost * 0.999) {
+      best = seg;
+      best_cost = c;
+    }
+  }
+  return best;
 }
 
 // Bracket the launches issued by `body` with an event pair when tracing.
@@ -427,6 +459,11 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   m->zbox.stride[1] = nz;
   m->zbox.stride[2] = (long long)nz * ny;
   m->xpath = auto_xpath(m);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   const int nblk = mhd::diag_blocks(m->box);
   if ((e = cudaMalloc(&m->sc, sizeof(Scalars))) != cudaSuccess ||
       (e = cudaMalloc(&m->diag_partial, sizeof(double) * mhd::kDiagSlots * nblk)) != cudaSuccess ||
