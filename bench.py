@@ -299,6 +299,12 @@ def learned_leg(args):
         h = yf if last else yb
     work = st.clone()
     correction_ms = graph_ms(lambda: corr.apply(work, corr.predict(st)))
+    # weight gradient of a 32 -> 32 layer (CUDA cores; FP32 atomics accumulate)
+    acts_in = mhd.conv3d(corr.x, net.img[0], n, 8, 32, bias=net.b[0], relu=True)[0]
+    gy = (torch.randn(cells, 32, device="cuda") * 0.1).to(torch.bfloat16)
+    gw = torch.zeros(32 * 32 * 27, device="cuda")
+    gb = torch.zeros(32, device="cuda")
+    wgrad_ms = graph_ms(lambda: mhd.conv3d_wgrad(acts_in, gy, n, 32, 32, gw, gb))
     if mhd.conv_error():
         raise RuntimeError("a tensor-core wait gave up")
     peak, peak_kind = bf16_peak()
@@ -311,6 +317,8 @@ def learned_leg(args):
                         "frac": tf / peak, "kernel": "conv3d (tcgen05 implicit GEMM)",
                         "peak_kind": peak_kind},
            "correction_ms": correction_ms,
+           "wgrad_32x32_ms": wgrad_ms,
+           "wgrad_32x32_tflops": 2.0 * 27 * 32 * 32 * cells / (wgrad_ms / 1e3) / 1e12,
            "timing": "CUDA graph of the repeated calls (device time only)",
            "reps": args.learned_reps}
     return out
