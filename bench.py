@@ -508,6 +508,7 @@ def run_ours(args, rank, world, local):
                           "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
                           "xpath": args.xpath or "auto",
+                          "segments": args.seg or "auto",
                           "l2": f"state {32 * N / 1e9:.1f} GB per copy > L2 (no flush needed)",
                           "parallelism": f"replicas x{world}"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
