@@ -293,7 +293,11 @@ int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void *x, const v
                float *y_f32, void *stream);
 
 /* Weight gradient: gw[co][ci][tap] += sum_cell gy[cell][co] x[cell + offset][ci],
- * gb[co] += sum_cell gy[cell][co] (FP32 atomics: the caller zeroes them). */
+ * gb[co] += sum_cell gy[cell][co] (FP32 atomics: the caller zeroes them; gb
+ * may be NULL).  With nx % 8 == 0, ny % 16 == 0 and x, gy 16-byte aligned the
+ * sum over cells runs on the tensor cores (tcgen05, FP32 accumulation; a
+ * bounded wait that gives up sets the flag mhd_conv_error reads); otherwise
+ * on the CUDA cores. */
 int mhd_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *gy,
                      float *gw, float *gb, void *stream);
 

@@ -57,9 +57,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor, K-major canonical layout without swizzle:
-// core matrices of 8 rows x 16 bytes; `lbo` = byte distance between core
-// matrices adjacent along K, `sbo` = between 8-row groups along M/N.
+// Shared-memory matrix descriptor, canonical layout without swizzle: core
+// matrices of 8 x 16 bytes (K-major: 8 rows of M/N, 16 bytes of K; MN-major:
+// 8 rows of K, 16 bytes of M/N); `lbo` = byte distance between core matrices
+// adjacent along K, `sbo` = between core matrices adjacent along M/N.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -339,6 +340,169 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int cin, int cout,
   }
 }
 
+// Weight gradient on the tensor cores.  gw[o][c][tap] += sum over cells of
+// gy[cell][o] x[cell + offset(tap)][c] is a GEMM whose reduction runs over
+// the cells: D[o, c] (M = 128 rows, output channels, 32 or 8 of them real and
+// the rest zero planes; N = 32 input channels; FP32 in TMEM, 32 columns per
+// tap) += A[o, cell] B[c, cell].  Both operands are MN-major (8 channels
+// contiguous, 16 bytes, per cell): A is the tile's output gradient, one plane
+// per 8 output channels; B is the tile's halo exactly as in the forward
+// kernel, and the tap is again a shift of B's start address.  One block per
+// SM loops over tiles and accumulates up to 16 taps in TMEM (the 27 taps take
+// two launches); at the end warp 0 reads the accumulators and adds them to gw.
+struct WgradArgs {
+  const __nv_bfloat16* x;
+  const __nv_bfloat16* gy;
+  int n[3];
+  int cin, cout;
+  int tap0, ntaps;
+  float* gw;
+  int* err;
+};
+
+// Operands plus barrier; at least 116 KB so that one block holds an SM (it
+// allocates all 512 TMEM columns).
+template <int TY>
+constexpr size_t wgrad_smem_bytes() {
+  constexpr size_t need = (size_t)16 * (8 * TY * 16) + 4 * (size_t)Halo<TY>::plane_bytes + 64;
+  return need > 116 * 1024 ? need : 116 * 1024;
+}
+
+template <int TY>
+__global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
+  using H = Halo<TY>;
+  constexpr int NT = 8 * TY;           // threads = cells of a tile
+  constexpr int APL = NT * 16;         // one A plane: 8 output channels of every tile cell
+  constexpr uint32_t kCols = 512;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* sA = smem;                  // 16 planes (output channels 0..127)
+  uint8_t* sB = smem + 16 * APL;       // 4 halo planes (input channels 0..31)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + 4 * H::plane_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int G = a.cin / 8, GO = a.cout / 8;
+
+  // every plane starts at zero: the planes beyond the real channels stay zero
+  for (int i = tid; i < (16 * APL + 4 * H::plane_bytes) / 16; i += NT)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tiles_x = nx / kTX, tiles_y = ny / TY;
+  const int ntiles = tiles_x * tiles_y * nz;
+  // M = 128, N = 32, BF16 in, FP32 accumulate, both operands MN-major
+  const uint32_t idesc = make_idesc(kM, 32) | (1u << 15) | (1u << 16);
+  bool ok = true;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * TY, z0 = tile / (tiles_x * tiles_y);
+    if (G == 4)
+      load_halo<4, TY>(sB, a.x, x0, y0, z0, nx, ny, nz, warp, lane);
+    else
+      load_halo<1, TY>(sB, a.x, x0, y0, z0, nx, ny, nz, warp, lane);
+    // the tile's output gradient: cell m = tx + 8 ty of the tile, plane g
+    for (int p = tid; p < NT * GO; p += NT) {
+      const int m = p / GO, g = p - m * GO;
+      const int cell = (x0 + (m & 7)) + nx * ((y0 + (m >> 3)) + ny * z0);
+      cp_async16(smem_addr(sA + g * APL + m * 16), a.gy + (size_t)cell * a.cout + g * 8);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // K = 16 cells per MMA: tile rows ty = 2 ks and 2 ks + 1.  MN-major
+      // core matrices are 8 cells (K, 16 B apart) x 8 channels (MN, the 16
+      // contiguous bytes).  A: the next 8 cells 128 B on (lbo), the next 8
+      // output channels one plane on (sbo).  B: the next 8 cells one halo row
+      // on (lbo), the next 8 input channels one halo plane on (sbo).
+      const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+      for (int t = 0; t < a.ntaps; t++) {
+        const int off = tap_offset<TY>(a.tap0 + t);
+        for (int ks = 0; ks < TY / 2; ks++) {
+          const uint64_t adesc = make_desc(a_addr + ks * 256, 128, APL);
+          const uint64_t bdesc = make_desc(b_addr + (off + 2 * ks * kHX) * 16, kHX * 16, H::plane_bytes);
+          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + t * 32),
+              "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(bar))
+                   : "memory");
+    }
+    if (ok) ok = mbar_wait(smem_addr(bar), it & 1);
+    if (!ok) {
+      if (tid == 0) atomicExch(a.err, 1);
+      mbar_wait(smem_addr(bar), it & 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok);  // the operands are rewritten only after the MMAs read them
+    if (!ok) break;
+  }
+  // warp 0 holds TMEM lanes 0..31 = output channels; columns t*32 + c
+  if (warp == 0 && ok && it > 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int t = 0; t < a.ntaps; t++) {
+      uint32_t r[32];
+#pragma unroll
+      for (int half = 0; half < 2; half++) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16 * half + 0]), "=r"(r[16 * half + 1]), "=r"(r[16 * half + 2]), "=r"(r[16 * half + 3]),
+              "=r"(r[16 * half + 4]), "=r"(r[16 * half + 5]), "=r"(r[16 * half + 6]), "=r"(r[16 * half + 7]),
+              "=r"(r[16 * half + 8]), "=r"(r[16 * half + 9]), "=r"(r[16 * half + 10]), "=r"(r[16 * half + 11]),
+              "=r"(r[16 * half + 12]), "=r"(r[16 * half + 13]), "=r"(r[16 * half + 14]), "=r"(r[16 * half + 15])
+            : "r"(tmem + t * 32 + half * 16));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (lane < a.cout) {
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+          if (c < a.cin) atomicAdd(a.gw + ((size_t)lane * a.cin + c) * 27 + a.tap0 + t, __uint_as_float(r[c]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// gb[o] += sum over cells of gy[cell][o]: a block sums a chunk of cells.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16* __restrict__ gy, long long cells,
+                                                        int cout, float* __restrict__ gb) {
+  __shared__ float part[256];
+  const int tid = threadIdx.x, o = tid % cout, rows = 256 / cout;
+  float acc = 0.f;
+  for (long long c = (long long)blockIdx.x * rows + tid / cout; c < cells; c += (long long)gridDim.x * rows)
+    acc += __bfloat162float(gy[c * cout + o]);
+  part[tid] = acc;
+  __syncthreads();
+  if (tid < cout) {
+    float s = 0.f;
+    for (int r = 0; r < rows; r++) s += part[r * cout + tid];
+    atomicAdd(gb + tid, s);
+  }
+}
+
 // Weight gradient on the CUDA cores: gw[co][ci][tap] += sum over a chunk of
 // cells of gy[cell][co] * x[cell + offset(tap)][ci] (FP32 accumulation,
 // atomically added across chunks), and gb[co] += sum gy[cell][co].
@@ -391,8 +555,54 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const __nv_bfloat16* __
   if (tap == 13 && tid < cout && gb) atomicAdd(&gb[tid], bacc);
 }
 
+namespace {
+template <int TY>
+cudaError_t launch_wgrad_tc(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
+                            float* gw, int* err, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)(n[0] / kTX) * (n[1] / TY) * n[2];
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  WgradArgs a;
+  a.x = x;
+  a.gy = gy;
+  a.n[0] = n[0];
+  a.n[1] = n[1];
+  a.n[2] = n[2];
+  a.cin = cin;
+  a.cout = cout;
+  a.gw = gw;
+  a.err = err;
+  for (int tap0 = 0; tap0 < 27; tap0 += 16) {  // TMEM holds 16 taps of 32 columns
+    a.tap0 = tap0;
+    a.ntaps = 27 - tap0 < 16 ? 27 - tap0 : 16;
+    conv_wgrad_tc_kernel<TY><<<grid, 8 * TY, wgrad_smem_bytes<TY>(), s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+// Weight and bias gradient: on the tensor cores when err is given (the
+// caller has checked that the box tiles into 8 x 16 x 1 cells and that x and
+// gy are 16-byte aligned), else on the CUDA cores.
 cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
-                              float* gw, float* gb, cudaStream_t s) {
+                              float* gw, float* gb, int* err, cudaStream_t s) {
+  if (err) {
+    cudaError_t e = n[1] % 32 == 0 ? launch_wgrad_tc<32>(x, gy, n, cin, cout, gw, err, s)
+                                   : launch_wgrad_tc<16>(x, gy, n, cin, cout, gw, err, s);
+    if (e != cudaSuccess || !gb) return e;
+    const long long cells = (long long)n[0] * n[1] * n[2];
+    bias_grad_kernel<<<256, 256, 0, s>>>(gy, cells, cout, gb);
+    return cudaGetLastError();
+  }
+  return launch_conv_wgrad_cuda_cores(x, gy, n, cin, cout, gw, gb, s);
+}
+
+cudaError_t launch_conv_wgrad_cuda_cores(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin,
+                                         int cout, float* gw, float* gb, cudaStream_t s) {
   const long long cells = (long long)n[0] * n[1] * n[2];
   int nchunk = 64;
   while (nchunk > 1 && (cells % ((long long)nchunk * kWgTile))) nchunk >>= 1;
@@ -470,7 +680,12 @@ cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t prepare_conv_kernels() {
-  cudaError_t e = prepare_one<4, 32>();
+  cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)wgrad_smem_bytes<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)wgrad_smem_bytes<16>());
+  if (e == cudaSuccess) e = prepare_one<4, 32>();
   if (e == cudaSuccess) e = prepare_one<4, 16>();
   if (e == cudaSuccess) e = prepare_one<1, 32>();
   if (e == cudaSuccess) e = prepare_one<1, 16>();

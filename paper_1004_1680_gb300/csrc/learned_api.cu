@@ -105,8 +105,14 @@ int mhd_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void* x, c
       !valid_channels(cout) || !x || !gy || !gw)
     return mhd::set_error(MHD_E_ARG, "mhd_conv3d_wgrad", "bad arguments");
   const int n[3] = {nx, ny, nz};
+  int* err = nullptr;
+  int rc = device_setup(&err);
+  if (rc) return rc;
+  // the tensor-core path copies 16-byte pieces of whole 8 x 16 x 1 tiles
+  const bool tiles = nx % 8 == 0 && ny % 16 == 0 && !(((uintptr_t)x | (uintptr_t)gy) & 15);
   cudaError_t e = mhd::launch_conv_wgrad(static_cast<const __nv_bfloat16*>(x), static_cast<const __nv_bfloat16*>(gy),
-                                         n, cin, cout, gw, gb, static_cast<cudaStream_t>(stream));
+                                         n, cin, cout, gw, gb, tiles ? err : nullptr,
+                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return mhd::set_error(MHD_E_CUDA, "mhd_conv3d_wgrad", cudaGetErrorString(e));
   return MHD_OK;
 }

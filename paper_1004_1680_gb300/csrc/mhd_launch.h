@@ -141,7 +141,9 @@ cudaError_t prepare_conv_kernels();
 cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s);
 cudaError_t launch_conv3d(const ConvArgs& a, cudaStream_t s);
 cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
-                              float* gw, float* gb, cudaStream_t s);
+                              float* gw, float* gb, int* err, cudaStream_t s);
+cudaError_t launch_conv_wgrad_cuda_cores(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin,
+                                         int cout, float* gw, float* gb, cudaStream_t s);
 
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);

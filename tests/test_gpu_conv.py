@@ -65,6 +65,31 @@ def test_conv_forward_dgrad_wgrad(cin, cout):
     assert float((gb.cpu().double() - b64.grad).abs().max()) < 1e-4 * float(b64.grad.abs().max())
 
 
+@pytest.mark.parametrize("n", [(12, 8, 4), (8, 16, 2)])
+def test_wgrad_paths(n):
+    """Weight and bias gradient of a box that does not tile into 8 x 16 x 1
+    cells (CUDA-core path) and of a single-tile-row box (tensor-core path,
+    every tap's halo wraps), against FP64 autograd."""
+    from paper_1004_1680_gb300 import mhd
+    torch.manual_seed(7)
+    cin, cout = 32, 8
+    cells = n[0] * n[1] * n[2]
+    xb = (torch.randn(cells, cin) * 0.5).to(torch.bfloat16)
+    gyb = torch.randn(cells, cout).to(torch.bfloat16)
+    x64 = to_ncdhw(xb.double(), n)
+    w64 = torch.zeros(cout, cin, 3, 3, 3, dtype=torch.float64, requires_grad=True)
+    b64 = torch.zeros(cout, dtype=torch.float64, requires_grad=True)
+    F.conv3d(F.pad(x64, (1, 1, 1, 1, 1, 1), mode="circular"), w64, b64).backward(to_ncdhw(gyb.double(), n))
+    gw = torch.zeros(cout * cin * 27, device="cuda")
+    gb = torch.zeros(cout, device="cuda")
+    mhd.conv3d_wgrad(xb.cuda(), gyb.cuda(), n, cin, cout, gw, gb)
+    torch.cuda.synchronize()
+    assert mhd.conv_error() == 0
+    gwr = w64.grad.reshape(-1)
+    assert float((gw.cpu().double() - gwr).abs().max()) < 1e-4 * float(gwr.abs().max())
+    assert float((gb.cpu().double() - b64.grad).abs().max()) < 1e-4 * float(b64.grad.abs().max())
+
+
 def sampled_conv(x, w, n, cells, flip=False):
     """FP64 output of the circular cross-correlation at the given cells only:
     y[c, o] = sum_{ci, taps} w[o, ci, tap] x[c + s * offset(tap), ci]."""
