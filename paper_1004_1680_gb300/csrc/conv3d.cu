@@ -341,50 +341,130 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int cin, int cout,
 }
 
 // Weight gradient on the tensor cores.  gw[o][c][tap] += sum over cells of
-// gy[cell][o] x[cell + offset(tap)][c] is a GEMM whose reduction runs over
-// the cells: D[o, c] (M = 128 rows, output channels, 32 or 8 of them real and
-// the rest zero planes; N = 32 input channels; FP32 in TMEM, 32 columns per
-// tap) += A[o, cell] B[c, cell].  Both operands are MN-major (8 channels
-// contiguous, 16 bytes, per cell): A is the tile's output gradient, one plane
-// per 8 output channels; B is the tile's halo exactly as in the forward
-// kernel, and the tap is again a shift of B's start address.  One block per
-// SM loops over tiles and accumulates up to 16 taps in TMEM (the 27 taps take
-// two launches); at the end warp 0 reads the accumulators and adds them to gw.
+// gy[cell][o] x[cell + d(tap)][c] is a GEMM whose reduction runs over the
+// cells, computed tile by tile (8 x TY x 1 cells, K = 16 cells per MMA):
+// D[row, col] += A[row, cell] B[col, cell], FP32 in TMEM, M = 128.  Both
+// operands are MN-major: a cell's 8 channels are the 16 contiguous bytes of
+// a core-matrix row, 8 cells along x make a core matrix.
+//
+// One MMA covers 9 (or 3) taps:
+//  * A rows are three copies of the tile's output gradient taken from the
+//    planes z0 + 1, z0, z0 - 1 (copy kz = 0, 1, 2; 4 planes of 8 output
+//    channels per copy for 32 output channels, one for 8);
+//  * B is the tile's x halo in its own z plane, stored row by row as
+//    [halo row][channel plane][10 cells], so core matrices adjacent along N
+//    are 160 bytes apart both from plane to plane and from the last plane of
+//    a row to the first of the next: N = 96 columns = 3 halo rows (ky) x 32
+//    input channels (for 8 input channels, 3 rows of 8 plus 8 ignored
+//    columns: N = 32);
+//  * the start of B, shifted by kx cells, selects the x tap: 3 accumulators.
+// Row (kz, o) x column (ky, c) of accumulator kx then sums
+// gy[cell'] x[cell' + (kx-1, ky-1, kz-1)] over the tile moved by (0, 0, 1-kz);
+// the moved tiles still cover the grid once, so it is one tap of the full
+// sum.  Rows and columns beyond the real channels read unused shared memory
+// and are never stored.
+//
+// One block per SM loops over tiles through three operand stages: lane 0 of
+// warp 0 issues the MMAs while the other warps copy the next tiles' operands
+// (mbarriers mark a stage full and, by tcgen05.commit, empty again).  At the
+// end warps 0..2 read the accumulators (TMEM lane = A row) into shared
+// memory, and the block adds its partial gw with coalesced reductions.
 struct WgradArgs {
   const __nv_bfloat16* x;
   const __nv_bfloat16* gy;
   int n[3];
   int cin, cout;
-  int tap0, ntaps;
   float* gw;
   int* err;
 };
 
-// Operands plus barrier; at least 116 KB so that one block holds an SM (it
-// allocates all 512 TMEM columns).
+template <int TY>
+struct WgradTile {
+  static constexpr int NT = 8 * TY;                      // threads; cells of a tile
+  static constexpr int NL = NT - 32;                     // copying threads (warps 1..)
+  static constexpr int APL = NT * 16;                    // one A plane: 8 channels of every tile cell
+  static constexpr int A_BYTES = 12 * APL;               // 3 copies x 4 planes; rows 96..127 read B
+  static constexpr int HY = TY + 2;                      // halo rows (one z plane)
+  static constexpr int SEG = kHX * 16;                   // one halo row of one channel plane
+  static constexpr int B_BYTES = (HY + 1) * 4 * SEG;     // 32 input channels, one spare row
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int NSTAGE = 3;
+  static constexpr int BASE = 1024;                      // barriers and TMEM address first
+  // barriers plus operands of three stages (afterwards: the block's partial
+  // gw, 32 x 32 x 27 floats and a pad word per output channel); at least
+  // 116 KB so that one block holds an SM (it allocates all 512 TMEM columns)
+  static constexpr size_t need = BASE + NSTAGE * (size_t)STAGE;
+  static constexpr size_t smem = need > 116 * 1024 ? need : 116 * 1024;
+  static_assert(16 * APL <= STAGE, "A rows 96..127 stay inside the stage");
+};
+
 template <int TY>
 constexpr size_t wgrad_smem_bytes() {
-  constexpr size_t need = (size_t)16 * (8 * TY * 16) + 4 * (size_t)Halo<TY>::plane_bytes + 64;
-  return need > 116 * 1024 ? need : 116 * 1024;
+  return WgradTile<TY>::smem;
 }
 
-template <int TY>
+// Copies of one tile's operands into a stage by the copying threads (lt =
+// 0..NL-1), one cp.async group per thread.  WIDE: 32 output channels, else 8;
+// G4: 32 input channels, else 8.
+template <int TY, bool WIDE, bool G4>
+__device__ __forceinline__ void wgrad_load(uint8_t* stage, const WgradArgs& a, int x0, int y0, int z0, int lt) {
+  using W = WgradTile<TY>;
+  constexpr int G = G4 ? 4 : 1, NT = W::NT, NL = W::NL;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const uint32_t sa = smem_addr(stage), sb = sa + W::A_BYTES;
+  // A: copy kz (the plane z0 + 1 - kz), tile cell m, plane g; consecutive
+  // threads take consecutive 16-byte pieces of a cell's channels
+  constexpr int PA = WIDE ? 3 * 4 * NT : 3 * NT;
+#pragma unroll
+  for (int i = 0; i < (PA + NL - 1) / NL; i++) {
+    const int p = lt + NL * i;
+    if (p < PA) {
+      if (WIDE) {
+        const int kz = p / (4 * NT), r = p % (4 * NT), g = r & 3, m = r >> 2;
+        const int cell = (x0 + (m & 7)) + nx * (y0 + (m >> 3) + ny * wrap1(z0 + 1 - kz, nz));
+        cp_async16(sa + (4 * kz + g) * W::APL + m * 16, a.gy + (size_t)cell * 32 + g * 8);
+      } else {
+        const int kz = p / NT, m = p % NT;
+        const int cell = (x0 + (m & 7)) + nx * (y0 + (m >> 3) + ny * wrap1(z0 + 1 - kz, nz));
+        cp_async16(sa + kz * W::APL + m * 16, a.gy + (size_t)cell * 8);
+      }
+    }
+  }
+  // B: halo cell (hx, hy) of plane g = x at (x0 - 1 + hx, y0 - 1 + hy, z0)
+  constexpr int P = kHX * G, PB = W::HY * P;
+#pragma unroll
+  for (int i = 0; i < (PB + NL - 1) / NL; i++) {
+    const int p = lt + NL * i;
+    if (p < PB) {
+      const int hy = p / P, l = p - hy * P, hx = l / G, g = l - hx * G;
+      const int cell = wrap1(x0 - 1 + hx, nx) + nx * (wrap1(y0 - 1 + hy, ny) + ny * z0);
+      cp_async16(sb + (hy * G + g) * W::SEG + hx * 16, a.x + (size_t)cell * (8 * G) + g * 8);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int TY, bool WIDE, bool G4>
 __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
-  using H = Halo<TY>;
-  constexpr int NT = 8 * TY;           // threads = cells of a tile
-  constexpr int APL = NT * 16;         // one A plane: 8 output channels of every tile cell
+  using W = WgradTile<TY>;
   constexpr uint32_t kCols = 512;
+  constexpr int G = G4 ? 4 : 1;
+  constexpr int NCOL = G4 ? 96 : 32;  // columns per accumulator
+  constexpr int RB = G * W::SEG;      // one halo row of every plane
+  constexpr int NS = W::NSTAGE;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* sA = smem;                  // 16 planes (output channels 0..127)
-  uint8_t* sB = smem + 16 * APL;       // 4 halo planes (input channels 0..31)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + 4 * H::plane_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int G = a.cin / 8, GO = a.cout / 8;
+  // full[s]: the copying threads' pieces of stage s have landed; empty[s]:
+  // the MMAs that read stage s are done
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + NS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + NS);
+  uint8_t* stages = smem + W::BASE;
 
-  // every plane starts at zero: the planes beyond the real channels stay zero
-  for (int i = tid; i < (16 * APL + 4 * H::plane_bytes) / 16; i += NT)
-    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"(kCols)
@@ -392,7 +472,10 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    for (int st = 0; st < NS; st++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + st)), "r"(W::NL) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(empty + st)) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -400,84 +483,135 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int nx = a.n[0], ny = a.n[1];
   const int tiles_x = nx / kTX, tiles_y = ny / TY;
-  const int ntiles = tiles_x * tiles_y * nz;
-  // M = 128, N = 32, BF16 in, FP32 accumulate, both operands MN-major
-  const uint32_t idesc = make_idesc(kM, 32) | (1u << 15) | (1u << 16);
+  const int ntiles = tiles_x * tiles_y * a.n[2];
+  const int K = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   bool ok = true;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
-    const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * TY, z0 = tile / (tiles_x * tiles_y);
-    if (G == 4)
-      load_halo<4, TY>(sB, a.x, x0, y0, z0, nx, ny, nz, warp, lane);
-    else
-      load_halo<1, TY>(sB, a.x, x0, y0, z0, nx, ny, nz, warp, lane);
-    // the tile's output gradient: cell m = tx + 8 ty of the tile, plane g
-    for (int p = tid; p < NT * GO; p += NT) {
-      const int m = p / GO, g = p - m * GO;
-      const int cell = (x0 + (m & 7)) + nx * ((y0 + (m >> 3)) + ny * z0);
-      cp_async16(smem_addr(sA + g * APL + m * 16), a.gy + (size_t)cell * a.cout + g * 8);
+  if (warp == 0) {
+    // lane 0 issues every MMA: per tile and x tap kx, TY / 2 K steps
+    // (tile rows 2 ks, 2 ks + 1).  A: the next 8 cells 128 B on (lbo), the
+    // next 8 rows one plane on (sbo).  B: the next 8 cells one halo row on
+    // (lbo), the next 8 columns 160 B on (sbo).  Address fields count 16-byte
+    // units, so shifts add to the descriptor.
+    if (lane == 0) {
+      // M = 128, N = NCOL, BF16 in, FP32 accumulate, both operands MN-major
+      constexpr uint32_t idesc = make_idesc(kM, NCOL) | (1u << 15) | (1u << 16);
+      int issued = 0;
+      for (int k = 0; k < K; k++) {
+        const int st = k % NS;
+        ok = mbar_wait(smem_addr(full + st), (k / NS) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_addr = smem_addr(stages + st * W::STAGE);
+        const uint64_t ad = make_desc(a_addr, 128, W::APL);
+        const uint64_t bd = make_desc(a_addr + W::A_BYTES, RB, W::SEG);
+#pragma unroll
+        for (int kx = 0; kx < 3; kx++) {
+#pragma unroll
+          for (int ks = 0; ks < TY / 2; ks++) {
+            const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + kx * NCOL),
+                "l"(ad + (uint64_t)(16 * ks)), "l"(bd + (uint64_t)(kx + 2 * ks * (RB / 16))), "r"(idesc),
+                "r"(acc)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(empty + st))
+                     : "memory");
+        issued = k + 1;
+      }
+      // the last issued tile's MMAs, also when a wait gave up, so that
+      // nothing is in flight when TMEM is freed
+      if (issued > 0) {
+        const bool done = mbar_wait(smem_addr(empty + (issued - 1) % NS), ((issued - 1) / NS) & 1);
+        ok = ok && done;
+      }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  } else {
+    const int lt = tid - 32;
+    for (int k = 0; k < K; k++) {
+      const int st = k % NS;
+      // stage st was last read by the MMAs of tile k - NS
+      if (k >= NS) ok = mbar_wait(smem_addr(empty + st), (k / NS - 1) & 1);
+      if (!ok) break;
+      const int tile = blockIdx.x + k * gridDim.x;
+      wgrad_load<TY, WIDE, G4>(stages + st * W::STAGE, a, (tile % tiles_x) * kTX, ((tile / tiles_x) % tiles_y) * TY,
+                               tile / (tiles_x * tiles_y), lt);
+      if (k >= 1) {  // the previous tile's pieces
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_addr(full + (k - 1) % NS));
+      }
+    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // K = 16 cells per MMA: tile rows ty = 2 ks and 2 ks + 1.  MN-major
-      // core matrices are 8 cells (K, 16 B apart) x 8 channels (MN, the 16
-      // contiguous bytes).  A: the next 8 cells 128 B on (lbo), the next 8
-      // output channels one plane on (sbo).  B: the next 8 cells one halo row
-      // on (lbo), the next 8 input channels one halo plane on (sbo).
-      const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
-      for (int t = 0; t < a.ntaps; t++) {
-        const int off = tap_offset<TY>(a.tap0 + t);
-        for (int ks = 0; ks < TY / 2; ks++) {
-          const uint64_t adesc = make_desc(a_addr + ks * 256, 128, APL);
-          const uint64_t bdesc = make_desc(b_addr + (off + 2 * ks * kHX) * 16, kHX * 16, H::plane_bytes);
-          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+    if (ok && K > 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_addr(full + (K - 1) % NS));
+    }
+  }
+  if (!ok) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // The block's partial gw goes through shared memory (the stages are free
+  // now) so that the additions to gw are contiguous: gw index
+  // i = (o cin + c) 27 + tap sits at word i + o (the pad word per output
+  // channel spreads the stores of a warp's lanes over the banks).
+  constexpr int CIN = G4 ? 32 : 8, ROW = CIN * 27, TOTAL = (WIDE ? 32 : 8) * ROW;
+  float* part = reinterpret_cast<float*>(stages);
+  // warps 0..2 hold TMEM lanes 0..95: A row L = 8 q + r of plane q
+  if (warp < (WIDE ? 3 : 1) && ok && K > 0) {
+    const int L = 32 * warp + lane, q = L >> 3, r = L & 7;
+    const int kz = WIDE ? q >> 2 : q, o = WIDE ? 8 * (q & 3) + r : r;
+    const bool live = WIDE ? q < 12 : q < 3;
+#pragma unroll 1
+    for (int kx = 0; kx < 3; kx++) {
+#pragma unroll 1
+      for (int ch = 0; ch < NCOL / 32; ch++) {  // 32 columns at a time
+        uint32_t v[32];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
           asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + t * 32),
-              "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-              : "memory");
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(v[16 * h + 0]), "=r"(v[16 * h + 1]), "=r"(v[16 * h + 2]), "=r"(v[16 * h + 3]),
+                "=r"(v[16 * h + 4]), "=r"(v[16 * h + 5]), "=r"(v[16 * h + 6]), "=r"(v[16 * h + 7]),
+                "=r"(v[16 * h + 8]), "=r"(v[16 * h + 9]), "=r"(v[16 * h + 10]), "=r"(v[16 * h + 11]),
+                "=r"(v[16 * h + 12]), "=r"(v[16 * h + 13]), "=r"(v[16 * h + 14]), "=r"(v[16 * h + 15])
+              : "r"(tmem + ((uint32_t)(32 * warp) << 16) + kx * NCOL + ch * 32 + h * 16));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (live) {
+          float* dst = part + o * (ROW + 1) + 9 * kz + kx;
+          if (G4) {  // columns: ky = ch, c = 0..31
+#pragma unroll
+            for (int c = 0; c < 32; c++) dst[c * 27 + 3 * ch] = __uint_as_float(v[c]);
+          } else {   // columns 8 ky + c, ky < 3
+#pragma unroll
+            for (int k = 0; k < 24; k++) dst[(k & 7) * 27 + 3 * (k >> 3)] = __uint_as_float(v[k]);
+          }
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(bar))
-                   : "memory");
     }
-    if (ok) ok = mbar_wait(smem_addr(bar), it & 1);
-    if (!ok) {
-      if (tid == 0) atomicExch(a.err, 1);
-      mbar_wait(smem_addr(bar), it & 1);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok);  // the operands are rewritten only after the MMAs read them
-    if (!ok) break;
   }
-  // warp 0 holds TMEM lanes 0..31 = output channels; columns t*32 + c
-  if (warp == 0 && ok && it > 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    for (int t = 0; t < a.ntaps; t++) {
-      uint32_t r[32];
-#pragma unroll
-      for (int half = 0; half < 2; half++) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[16 * half + 0]), "=r"(r[16 * half + 1]), "=r"(r[16 * half + 2]), "=r"(r[16 * half + 3]),
-              "=r"(r[16 * half + 4]), "=r"(r[16 * half + 5]), "=r"(r[16 * half + 6]), "=r"(r[16 * half + 7]),
-              "=r"(r[16 * half + 8]), "=r"(r[16 * half + 9]), "=r"(r[16 * half + 10]), "=r"(r[16 * half + 11]),
-              "=r"(r[16 * half + 12]), "=r"(r[16 * half + 13]), "=r"(r[16 * half + 14]), "=r"(r[16 * half + 15])
-            : "r"(tmem + t * 32 + half * 16));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (lane < a.cout) {
-#pragma unroll
-        for (int c = 0; c < 32; c++)
-          if (c < a.cin) atomicAdd(a.gw + ((size_t)lane * a.cin + c) * 27 + a.tap0 + t, __uint_as_float(r[c]));
-      }
+  __syncthreads();
+  if (ok && K > 0) {
+    // ROW is a multiple of 4, so 4 consecutive indices share o
+    const bool vec = ((uintptr_t)a.gw & 15) == 0;
+    for (int i = 4 * tid; i < TOTAL; i += 4 * W::NT) {
+      const float* src = part + i + i / ROW;
+      float* dst = a.gw + i;
+      if (vec)
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(src[0]), "f"(src[1]),
+                     "f"(src[2]), "f"(src[3])
+                     : "memory");
+      else
+        for (int k = 0; k < 4; k++) atomicAdd(dst + k, src[k]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -575,13 +709,14 @@ cudaError_t launch_wgrad_tc(const __nv_bfloat16* x, const __nv_bfloat16* gy, con
   a.cout = cout;
   a.gw = gw;
   a.err = err;
-  for (int tap0 = 0; tap0 < 27; tap0 += 16) {  // TMEM holds 16 taps of 32 columns
-    a.tap0 = tap0;
-    a.ntaps = 27 - tap0 < 16 ? 27 - tap0 : 16;
-    conv_wgrad_tc_kernel<TY><<<grid, 8 * TY, wgrad_smem_bytes<TY>(), s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const size_t smem = wgrad_smem_bytes<TY>();
+  if (cout == 32)
+    cin == 32 ? conv_wgrad_tc_kernel<TY, true, true><<<grid, 8 * TY, smem, s>>>(a)
+              : conv_wgrad_tc_kernel<TY, true, false><<<grid, 8 * TY, smem, s>>>(a);
+  else
+    cin == 32 ? conv_wgrad_tc_kernel<TY, false, true><<<grid, 8 * TY, smem, s>>>(a)
+              : conv_wgrad_tc_kernel<TY, false, false><<<grid, 8 * TY, smem, s>>>(a);
+  return cudaGetLastError();
 }
 }  // namespace
 
@@ -621,6 +756,21 @@ size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty) {
 }
 
 namespace {
+template <int TY>
+cudaError_t prepare_wgrad() {
+  const int smem = (int)wgrad_smem_bytes<TY>();
+  cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<TY, true, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<TY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<TY, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<TY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  return e;
+}
+
 template <int G, int TY>
 cudaError_t prepare_one() {
   cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<G, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -680,11 +830,8 @@ cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t prepare_conv_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)wgrad_smem_bytes<32>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)wgrad_smem_bytes<16>());
+  cudaError_t e = prepare_wgrad<32>();
+  if (e == cudaSuccess) e = prepare_wgrad<16>();
   if (e == cudaSuccess) e = prepare_one<4, 32>();
   if (e == cudaSuccess) e = prepare_one<4, 16>();
   if (e == cudaSuccess) e = prepare_one<1, 32>();
