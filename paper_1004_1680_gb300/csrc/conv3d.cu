@@ -365,23 +365,27 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int cin, int cout,
 // and are never stored.
 //
 // One block per SM loops over tiles through three operand stages: lane 0 of
-// warp 0 issues the MMAs while the other warps copy the next tiles' operands
-// (mbarriers mark a stage full and, by tcgen05.commit, empty again).  At the
-// end warps 0..2 read the accumulators (TMEM lane = A row) into shared
-// memory, and the block adds its partial gw with coalesced reductions.
+// warp 0 issues the MMAs while the copying warps fetch the next tiles'
+// operands and a last warp sums copy kz = 1 (the tile's own output gradient)
+// for the bias gradient (mbarriers mark a stage full, and empty again once
+// tcgen05.commit and the bias warp have both arrived).  At the end warps
+// 0..2 read the accumulators (TMEM lane = A row) into shared memory, and the
+// block adds its partial gw with coalesced reductions.
 struct WgradArgs {
   const __nv_bfloat16* x;
   const __nv_bfloat16* gy;
   int n[3];
   int cin, cout;
   float* gw;
+  float* gb;  // may be null
   int* err;
 };
 
 template <int TY>
 struct WgradTile {
-  static constexpr int NT = 8 * TY;                      // threads; cells of a tile
-  static constexpr int NL = NT - 32;                     // copying threads (warps 1..)
+  static constexpr int NT = 8 * TY;                      // cells of a tile
+  static constexpr int NTHR = NT + 32;                   // threads: MMA warp, copying warps, bias warp
+  static constexpr int NL = NT - 32;                     // copying threads (warps 1 .. NT / 32 - 1)
   static constexpr int APL = NT * 16;                    // one A plane: 8 channels of every tile cell
   static constexpr int A_BYTES = 12 * APL;               // 3 copies x 4 planes; rows 96..127 read B
   static constexpr int HY = TY + 2;                      // halo rows (one z plane)
@@ -449,7 +453,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 template <int TY, bool WIDE, bool G4>
-__global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
+__global__ void __launch_bounds__(8 * TY + 32, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   using W = WgradTile<TY>;
   constexpr uint32_t kCols = 512;
   constexpr int G = G4 ? 4 : 1;
@@ -459,7 +463,8 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // full[s]: the copying threads' pieces of stage s have landed; empty[s]:
-  // the MMAs that read stage s are done
+  // the MMAs that read stage s are done (tcgen05.commit) and the bias warp
+  // has summed it
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + NS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + NS);
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   if (tid == 0) {
     for (int st = 0; st < NS; st++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + st)), "r"(W::NL) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(empty + st)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_addr(empty + st)) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -532,6 +537,39 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
       }
     }
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  } else if (warp == W::NT / 32) {
+    // bias warp: gb[o] sums the output gradient over the cells, i.e. copy
+    // kz = 1 (the tile's own plane) of every tile; lane l keeps channel group
+    // l % 4 (one group for 8 output channels)
+    constexpr int GO = WIDE ? 4 : 1;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < K; k++) {
+      const int st = k % NS;
+      ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(full + st), (k / NS) & 1));  // the warp stays converged
+      if (!ok) break;
+      if (a.gb) {
+        const uint8_t* own = stages + st * W::STAGE + GO * W::APL;
+        for (int p = lane; p < GO * W::NT; p += 32) {
+          const int g = p % GO, m = p / GO;
+          const uint4 v = *reinterpret_cast<const uint4*>(own + g * W::APL + m * 16);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            acc[2 * q] += __uint_as_float(w[q] << 16);
+            acc[2 * q + 1] += __uint_as_float(w[q] & 0xFFFF0000u);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(empty + st));
+    }
+    if (a.gb && ok && K > 0) {
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        for (int d = GO; d < 32; d *= 2) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], d);
+        if (lane < GO) atomicAdd(a.gb + 8 * lane + q, acc[q]);
+      }
+    }
   } else {
     const int lt = tid - 32;
     for (int k = 0; k < K; k++) {
@@ -603,7 +641,7 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   if (ok && K > 0) {
     // ROW is a multiple of 4, so 4 consecutive indices share o
     const bool vec = ((uintptr_t)a.gw & 15) == 0;
-    for (int i = 4 * tid; i < TOTAL; i += 4 * W::NT) {
+    for (int i = 4 * tid; i < TOTAL; i += 4 * W::NTHR) {
       const float* src = part + i + i / ROW;
       float* dst = a.gw + i;
       if (vec)
@@ -618,23 +656,6 @@ __global__ void __launch_bounds__(8 * TY, 1) conv_wgrad_tc_kernel(WgradArgs a) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
-}
-
-// gb[o] += sum over cells of gy[cell][o]: a block sums a chunk of cells.
-__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16* __restrict__ gy, long long cells,
-                                                        int cout, float* __restrict__ gb) {
-  __shared__ float part[256];
-  const int tid = threadIdx.x, o = tid % cout, rows = 256 / cout;
-  float acc = 0.f;
-  for (long long c = (long long)blockIdx.x * rows + tid / cout; c < cells; c += (long long)gridDim.x * rows)
-    acc += __bfloat162float(gy[c * cout + o]);
-  part[tid] = acc;
-  __syncthreads();
-  if (tid < cout) {
-    float s = 0.f;
-    for (int r = 0; r < rows; r++) s += part[r * cout + tid];
-    atomicAdd(gb + tid, s);
-  }
 }
 
 // Weight gradient on the CUDA cores: gw[co][ci][tap] += sum over a chunk of
@@ -692,7 +713,7 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const __nv_bfloat16* __
 namespace {
 template <int TY>
 cudaError_t launch_wgrad_tc(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
-                            float* gw, int* err, cudaStream_t s) {
+                            float* gw, float* gb, int* err, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -708,14 +729,16 @@ cudaError_t launch_wgrad_tc(const __nv_bfloat16* x, const __nv_bfloat16* gy, con
   a.cin = cin;
   a.cout = cout;
   a.gw = gw;
+  a.gb = gb;
   a.err = err;
   const size_t smem = wgrad_smem_bytes<TY>();
+  constexpr int threads = WgradTile<TY>::NTHR;
   if (cout == 32)
-    cin == 32 ? conv_wgrad_tc_kernel<TY, true, true><<<grid, 8 * TY, smem, s>>>(a)
-              : conv_wgrad_tc_kernel<TY, true, false><<<grid, 8 * TY, smem, s>>>(a);
+    cin == 32 ? conv_wgrad_tc_kernel<TY, true, true><<<grid, threads, smem, s>>>(a)
+              : conv_wgrad_tc_kernel<TY, true, false><<<grid, threads, smem, s>>>(a);
   else
-    cin == 32 ? conv_wgrad_tc_kernel<TY, false, true><<<grid, 8 * TY, smem, s>>>(a)
-              : conv_wgrad_tc_kernel<TY, false, false><<<grid, 8 * TY, smem, s>>>(a);
+    cin == 32 ? conv_wgrad_tc_kernel<TY, false, true><<<grid, threads, smem, s>>>(a)
+              : conv_wgrad_tc_kernel<TY, false, false><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 }  // namespace
@@ -725,14 +748,9 @@ cudaError_t launch_wgrad_tc(const __nv_bfloat16* x, const __nv_bfloat16* gy, con
 // gy are 16-byte aligned), else on the CUDA cores.
 cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin, int cout,
                               float* gw, float* gb, int* err, cudaStream_t s) {
-  if (err) {
-    cudaError_t e = n[1] % 32 == 0 ? launch_wgrad_tc<32>(x, gy, n, cin, cout, gw, err, s)
-                                   : launch_wgrad_tc<16>(x, gy, n, cin, cout, gw, err, s);
-    if (e != cudaSuccess || !gb) return e;
-    const long long cells = (long long)n[0] * n[1] * n[2];
-    bias_grad_kernel<<<256, 256, 0, s>>>(gy, cells, cout, gb);
-    return cudaGetLastError();
-  }
+  if (err)
+    return n[1] % 32 == 0 ? launch_wgrad_tc<32>(x, gy, n, cin, cout, gw, gb, err, s)
+                          : launch_wgrad_tc<16>(x, gy, n, cin, cout, gw, gb, err, s);
   return launch_conv_wgrad_cuda_cores(x, gy, n, cin, cout, gw, gb, s);
 }
 
