@@ -20,7 +20,8 @@
 // and writes BF16 and/or FP32 with 16-byte stores.
 //
 // The input gradient is the same kernel with mirrored taps and the weights
-// packed transposed.
+// packed transposed.  The weight gradient (a reduction over the cells) is a
+// second tcgen05 kernel with both operands MN-major, described above it.
 //
 // Every mbarrier wait is bounded: on timeout the block records an error in
 // *err, waits (bounded) once more, frees its tensor memory and returns.
@@ -540,7 +541,8 @@ __global__ void __launch_bounds__(8 * TY + 32, 1) conv_wgrad_tc_kernel(WgradArgs
   } else if (warp == W::NT / 32) {
     // bias warp: gb[o] sums the output gradient over the cells, i.e. copy
     // kz = 1 (the tile's own plane) of every tile; lane l keeps channel group
-    // l % 4 (one group for 8 output channels)
+    // l / 8 (one group for 8 output channels), so that the 8 lanes of a
+    // quarter warp read 128 contiguous bytes of one plane
     constexpr int GO = WIDE ? 4 : 1;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < K; k++) {
@@ -549,8 +551,9 @@ __global__ void __launch_bounds__(8 * TY + 32, 1) conv_wgrad_tc_kernel(WgradArgs
       if (!ok) break;
       if (a.gb) {
         const uint8_t* own = stages + st * W::STAGE + GO * W::APL;
-        for (int p = lane; p < GO * W::NT; p += 32) {
-          const int g = p % GO, m = p / GO;
+        const int g = WIDE ? lane >> 3 : 0, m0 = WIDE ? lane & 7 : lane;
+#pragma unroll 4
+        for (int m = m0; m < W::NT; m += 32 / GO) {
           const uint4 v = *reinterpret_cast<const uint4*>(own + g * W::APL + m * 16);
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -566,8 +569,8 @@ __global__ void __launch_bounds__(8 * TY + 32, 1) conv_wgrad_tc_kernel(WgradArgs
     if (a.gb && ok && K > 0) {
 #pragma unroll
       for (int q = 0; q < 8; q++) {
-        for (int d = GO; d < 32; d *= 2) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], d);
-        if (lane < GO) atomicAdd(a.gb + 8 * lane + q, acc[q]);
+        for (int d = 1; d < 32 / GO; d *= 2) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], d);
+        if ((lane & (32 / GO - 1)) == 0) atomicAdd(a.gb + 8 * (lane / (32 / GO)) + q, acc[q]);
       }
     }
   } else {
