@@ -15,7 +15,11 @@
 // marches all of them together along D.  Two extra warps march the halo
 // pencils whose flux the tile needs: row O+kMagWarps (its f along O) and
 // column A+32 (its f along A).  Fluxes are exchanged through shared memory
-// once per chunk of 4 positions.  Writes are out of place.
+// once per chunk of positions.  Writes are out of place.
+//
+// mag_sweep_kernel sweeps along x itself (the staged x path: rows of 8 cells
+// staged in shared memory); mag_sweep_pipe_kernel sweeps along y and z, and
+// along x on the x <-> y exchanged copy.
 //
 // LIM selects the slope limiter (0: van Leer, the paper's; 1 minmod and 2
 // superbee are ablations, instantiated in sweep_variant_*.cu).
@@ -80,13 +84,14 @@ __device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__
 template <int D, bool SMALL, int LIM>
 __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_kernel(MagArgs a) {
+  static_assert(D == 0, "y and z sweeps use mag_sweep_pipe_kernel");
   using X = MagAxes<D>;
-  constexpr int CH = (D == 0) ? kMXChunk : 4;
+  constexpr int CH = kMXChunk;
   // double-buffered by chunk parity: a chunk's fluxes are written while the
   // previous chunk's may still be read, so one barrier per chunk suffices
   __shared__ float fA_s[2][CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
   __shared__ float fO_s[2][CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
-  extern __shared__ float xs_dyn[];               // x sweeps only: staged rows
+  extern __shared__ float xs_dyn[];               // staged rows
 
   const int lane = threadIdx.x, w = threadIdx.y;
   const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
@@ -128,7 +133,7 @@ mag_sweep_kernel(MagArgs a) {
   float* __restrict__ o_bA = a.out[X::A] + G.off;
   float* __restrict__ o_bO = a.out[X::O] + G.off;
   float* __restrict__ o_bD = a.out[D] + G.off;
-  float* xw = xs_dyn + (D == 0 ? w * kMXTiles * kMXTile : 0);
+  float* xw = xs_dyn + w * kMXTiles * kMXTile;
 
   const float tau = G.tau;
   const float c_full = tau * (float)nD;        // tau / h_D
@@ -154,48 +159,25 @@ mag_sweep_kernel(MagArgs a) {
 
   for (int c = 0; c < nchunk; c++) {
     const int p0 = s0 - 4 + CH * c;
-    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
-    constexpr int R = (D == 0) ? 1 : CH;
-    float qA[R], qO[R], qD[R], rr[R], mm[R], rrA[R], mmA[R], rrO[R], mmO[R];
+    // the chunk's rows staged in shared memory
     const float* rw = xw + lane * kMXPad;
-    if constexpr (D == 0) {
-      __syncwarp();
-      stage_vel<SMALL>(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
-      stage_vel<SMALL>(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
-      stage_vel<SMALL>(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
-      stage_rows_m<SMALL>(xw + 3 * kMXTile, bA, base, p0, nD, lane);
-      stage_rows_m<SMALL>(xw + 4 * kMXTile, bO, base, p0, nD, lane);
-      stage_rows_m<SMALL>(xw + 5 * kMXTile, bD, base, p0, nD, lane);
-      __syncwarp();
-    } else {
-#pragma unroll
-      for (int j = 0; j < CH; j++) {  // all loads of the chunk first; divisions when used
-        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
-        rr[j] = __ldg(rho + base + off);
-        mm[j] = __ldg(md + base + off);
-        rrA[j] = __ldg(rho + baseAm + off);
-        mmA[j] = __ldg(md + baseAm + off);
-        rrO[j] = __ldg(rho + baseOm + off);
-        mmO[j] = __ldg(md + baseOm + off);
-        qA[j] = __ldg(bA + base + off);
-        qO[j] = __ldg(bO + base + off);
-        qD[j] = __ldg(bD + base + off);
-      }
-    }
+    __syncwarp();
+    stage_vel<SMALL>(xw + 0 * kMXTile, rho, md, base, p0, nD, lane);
+    stage_vel<SMALL>(xw + 1 * kMXTile, rho, md, baseAm, p0, nD, lane);
+    stage_vel<SMALL>(xw + 2 * kMXTile, rho, md, baseOm, p0, nD, lane);
+    stage_rows_m<SMALL>(xw + 3 * kMXTile, bA, base, p0, nD, lane);
+    stage_rows_m<SMALL>(xw + 4 * kMXTile, bO, base, p0, nD, lane);
+    stage_rows_m<SMALL>(xw + 5 * kMXTile, bD, base, p0, nD, lane);
+    __syncwarp();
     float bDold[CH];  // raw b_D at the face each position's constraint updates
 #pragma unroll
     for (int j = 0; j < CH; j++) {
-      float vj, vAj, vOj, qAj, qOj, qDj;
-      if constexpr (D == 0) {
-        vj = rw[0 * kMXTile + j];
-        vAj = rw[1 * kMXTile + j];
-        vOj = rw[2 * kMXTile + j];
-        qAj = rw[3 * kMXTile + j];
-        qOj = rw[4 * kMXTile + j];
-        qDj = rw[5 * kMXTile + j];
-      } else {
-        vj = __fdividef(mm[j], rr[j]); vAj = __fdividef(mmA[j], rrA[j]); vOj = __fdividef(mmO[j], rrO[j]); qAj = qA[j]; qOj = qO[j]; qDj = qD[j];
-      }
+      const float vj = rw[0 * kMXTile + j];
+      const float vAj = rw[1 * kMXTile + j];
+      const float vOj = rw[2 * kMXTile + j];
+      const float qAj = rw[3 * kMXTile + j];
+      const float qOj = rw[4 * kMXTile + j];
+      const float qDj = rw[5 * kMXTile + j];
       const float uA = 0.5f * (vj + vAj);  // v_D on the b_A face
       const float uO = 0.5f * (vj + vOj);  // v_D on the b_O face
       // the halo row needs only the flux along O, the halo column only along A
@@ -239,11 +221,9 @@ mag_sweep_kernel(MagArgs a) {
   }
 }
 
-// Sweeps along y (D = 1; the x sweeps also run here, on the x <-> y
-// exchanged copy): the same arithmetic as mag_sweep_kernel, reorganised for
-// memory-level parallelism.  (Along z, whose positions are a whole plane
-// apart, mag_sweep_kernel measured faster: 1.41 against 1.65 ms at 512^3,
-// against 1.39 -> 1.15 ms here along y.)
+// Sweeps along y and z (D = 1, 2; the x sweeps also run along y, on the
+// x <-> y exchanged copy): the same arithmetic as mag_sweep_kernel,
+// reorganised for memory-level parallelism.
 //  * Every thread loads 5 values per position.  An interior pencil loads
 //    rho, m_D, b_A, b_O, b_D.  The halo row loads rho, m_D, b_O and rho, m_D
 //    of the pencil row below the tile (-O).  The halo column loads rho, m_D,
@@ -252,13 +232,18 @@ mag_sweep_kernel(MagArgs a) {
 //    loads per position.
 //  * v_D = m_D / rho of the -A and -O neighbours comes from shared memory,
 //    v_s[row + 1][col + 1] (row 0: the -O pencils, column 0: the -A ones).
-//  * The loads of chunk c + 1 are issued before chunk c is computed, and
-//    their v_D is written to the other half of v_s before the chunk's
-//    barrier, which therefore covers both exchanges.
+//  * The v_D of chunk c + 1 is written to the other half of v_s before
+//    chunk c's barrier, which therefore covers both exchanges.  Along y the
+//    loads of chunk c + 1 are issued before chunk c is computed; along z,
+//    whose positions are a whole plane apart, they are issued after it.
+//    Issuing them early measured 1.39 -> 1.15 ms per launch along y at
+//    512^3 (from mag_sweep_kernel), but 1.65 ms along z, where issuing them
+//    late gives 1.33 (mag_sweep_kernel: 1.41).
 template <int D, bool SMALL, int LIM>
 __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_pipe_kernel(MagArgs a) {
-  static_assert(D == 1, "x sweeps use the staged kernel, z sweeps mag_sweep_kernel");
+  static_assert(D != 0, "x sweeps use the staged kernel");
+  constexpr bool kEarly = D == 1;  // next chunk's loads before the current chunk's arithmetic
   using X = MagAxes<D>;
   constexpr int CH = 4;
   __shared__ float fA_s[2][CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
@@ -402,7 +387,7 @@ mag_sweep_pipe_kernel(MagArgs a) {
     const int p0 = s0 - 4 + CH * c;
     const bool more = c + 1 < nchunk;
     float n0[CH], n1[CH], n2[CH], n3[CH], n4[CH];
-    if (more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
+    if (kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
     float bDold[CH];  // raw b_D at the face each position's constraint updates
 #pragma unroll
     for (int j = 0; j < CH; j++) {
@@ -429,6 +414,7 @@ mag_sweep_pipe_kernel(MagArgs a) {
         o_bO[cell] = nO_new;
       }
     }
+    if (!kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
     if (more) publish((c + 1) & 1, n0, n1, n2, n3, n4);
     __syncthreads();
     if (interior) {
@@ -478,11 +464,15 @@ cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
     if (small) mag_sweep_kernel<DD, true, LIM><<<grid, block, SMEM, s>>>(a);     \
     else mag_sweep_kernel<DD, false, LIM><<<grid, block, SMEM, s>>>(a);          \
   }
-  MAG_CASE(0, kMagXSmem) MAG_CASE(2, 0)
+  MAG_CASE(0, kMagXSmem)
 #undef MAG_CASE
   if (axis == 1) {
     if (small) mag_sweep_pipe_kernel<1, true, LIM><<<grid, block, 0, s>>>(a);
     else mag_sweep_pipe_kernel<1, false, LIM><<<grid, block, 0, s>>>(a);
+  }
+  if (axis == 2) {
+    if (small) mag_sweep_pipe_kernel<2, true, LIM><<<grid, block, 0, s>>>(a);
+    else mag_sweep_pipe_kernel<2, false, LIM><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
