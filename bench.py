@@ -182,6 +182,22 @@ def measured_traffic(kernel: str, n: int):
     return r["bytes_per_cell"] * n ** 3
 
 
+def measured_issue(kernel: str):
+    """Warp instructions per cell of a kernel family from the committed ncu
+    capture (smsp__inst_executed.sum over cells), if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    r = rec.get(kernel)
+    if not r or r.get("source_hash") != kernel_source_hash():
+        return None
+    return r.get("warp_instructions_per_cell")
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -498,6 +514,22 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, args.seed, args.cfl)
 
+    # the same kernel against the instruction issue rate: warp instructions
+    # per cell (ncu, committed capture) x cells / launch time, against one
+    # warp instruction per cycle on each of the 4 schedulers of every SM at
+    # the median SM clock sampled during the timed region
+    issue = None
+    ipc = measured_issue(dom)
+    if ipc:
+        mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+        if mhz:
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            ach = ipc * N / avg_s
+            pk = sms * 4 * mhz * 1e6
+            issue = {"unit": "warp instructions/s", "achieved": ach, "peak": pk, "frac": ach / pk,
+                     "warp_instructions_per_cell": ipc,
+                     "peak_basis": f"{sms} SMs x 4 schedulers x 1 warp instruction/cycle x {mhz:.0f} MHz"}
+
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -514,7 +546,7 @@ def run_ours(args, rank, world, local):
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom} sweep",
                             "algorithmic_bytes_per_cell": ALGO_BYTES[dom],
-                            "peak_kind": peak_kind},
+                            "peak_kind": peak_kind, "issue": issue},
                "step_roofline": {"model_bytes_per_cell": STEP_BYTES,
                                  "achieved_GBps": STEP_BYTES * N * args.steps / secs / 1e9,
                                  "frac": STEP_BYTES * N * args.steps / secs / 1e9 / peak},

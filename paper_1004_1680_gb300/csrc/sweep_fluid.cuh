@@ -67,8 +67,12 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
   }
 }
 
+// 4 blocks of 128 threads per SM, so at most 128 registers per thread: the
+// RATE variant spills a few words at that limit (it needs about 160), which
+// measured faster than 3 blocks per SM without spills (1.77 against 1.85 ms
+// at 512^3).
 template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, bool FAST>
-__global__ void __launch_bounds__(32 * kFluidWarps, RATE ? 3 : 4)
+__global__ void __launch_bounds__(32 * kFluidWarps, 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
   constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
