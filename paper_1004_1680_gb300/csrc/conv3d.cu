@@ -3,28 +3,30 @@
 //
 // GEMM view: D[cell, o] = sum_k A[cell, k] W[o, k], k = (tap, channel) over
 // the 27 taps and the cin input channels (channels-last BF16 activations).
-// A is never materialised.  A block owns a tile of 8 x TY x 1 cells (TY = 32:
-// two 128-row accumulators; 16: one) and copies the tile's halo, (8+2) x
-// (TY+2) x 3 cells, once into shared memory with cp.async, stored as one plane
-// per 8-channel group (16 bytes per cell).  In that layout the canonical
-// K-major core matrix of 8 GEMM rows x 8 channels is 8 consecutive halo cells
-// along x, so the operand of tap t is the same halo addressed from a shifted
-// start: every tap is one descriptor offset, with no per-tap gather.  The
-// weights (packed once by conv_pack) stay in shared memory for the block's
-// lifetime; blocks are persistent and prefetch the next tile's halo into a
-// second buffer while the tensor core works.  Per tile, one thread per
-// accumulator issues its 27 x (cin / 16) tcgen05.mma (M = 128, N = 32 or 16,
-// K = 16; BF16 in, FP32 in TMEM) and a tcgen05.commit onto a shared
-// mbarrier.  The epilogue reads TMEM with tcgen05.ld, adds the bias, applies
-// ReLU (forward) or the ReLU mask of the saved activation (input gradient),
-// and writes BF16 and/or FP32 with 16-byte stores.
+// A is never materialised.  A block owns a run of tiles of 8 x TY x 1 cells
+// (TY = 32: two 128-row accumulators; 16: one), consecutive along z.  A tile
+// needs the halo planes z-1, z, z+1, each (8+2) x (TY+2) cells stored as one
+// plane per 8-channel group (16 bytes per cell) in a ring of shared-memory
+// slots; consecutive tiles share two of them, so a tile copies one new plane
+// (cp.async).  In that layout the canonical K-major core matrix of 8 GEMM
+// rows x 8 channels is 8 consecutive halo cells along x, so the operand of
+// tap t is its plane's slot addressed from a shifted start: every tap is one
+// descriptor offset, with no per-tap gather.  The weights (packed once by
+// conv_pack) stay in shared memory for the block's lifetime.  Warps
+// specialise: one thread per accumulator issues its 27 x (cin / 16)
+// tcgen05.mma (M = 128, N = 32 or 16, K = 16; BF16 in, FP32 in TMEM) into
+// one of two TMEM buffers, two warps copy planes, four warps run the
+// epilogue of the previous tile (tcgen05.ld, bias, ReLU or the ReLU mask of
+// the saved activation, BF16 and/or FP32 16-byte stores); mbarriers pass
+// slots and buffers between them.
 //
 // The input gradient is the same kernel with mirrored taps and the weights
 // packed transposed.  The weight gradient (a reduction over the cells) is a
 // second tcgen05 kernel with both operands MN-major, described above it.
 //
 // Every mbarrier wait is bounded: on timeout the block records an error in
-// *err, waits (bounded) once more, frees its tensor memory and returns.
+// *err, and every role leaves its loop; the MMA threads wait (bounded) for
+// their last commit before the tensor memory is freed.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -38,20 +40,8 @@ namespace {
 
 constexpr int kM = 128;       // GEMM rows per MMA (tile cells per accumulator)
 constexpr int kKC = 32;       // k per 32-wide chunk of the packed weight image
-constexpr int kTX = 8, kHX = kTX + 2, kHZ = 3;     // tile: 8 x TY x 1 cells, TY = 16 or 32
+constexpr int kTX = 8, kHX = kTX + 2;     // tile: 8 x TY x 1 cells (TY = 16 or 32), halo rows of kHX cells
 
-// Halo of an 8 x TY x 1 tile: kHX x (TY + 2) x kHZ cells, one 16-byte channel
-// group per cell and plane, padded by 4 zeroed cells (read, times zero
-// weights, by the cin = 8 MMAs).
-template <int TY>
-struct Halo {
-  static constexpr int HY = TY + 2;
-  static constexpr int cells = kHX * HY * kHZ;      // 540 or 1020
-  static constexpr int plane_cells = cells + 4;
-  static constexpr int plane_bytes = plane_cells * 16;
-  static constexpr int rows = HY * kHZ;             // halo rows along x
-};
-constexpr uint32_t kTmemCols = 64;                 // two 32-column accumulators
 constexpr long long kSpinLimit = 1LL << 22;  // about 0.5 s of polling
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -112,211 +102,281 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
-// Halo of a tile (the 8 x TY x 1 cells at (x0, y0, z0) and one cell around
-// them, periodic) into shared memory by asynchronous 16-byte copies: plane g
-// (channels 8g..8g+7), halo cell c at buf + g * plane_bytes + c * 16.  Warps
-// take whole halo rows (the y, z wrap is computed once per row); lanes take
-// the 16-byte pieces of a row.  One commit group.
+// Shared-memory ring of halo planes for the forward / input-gradient kernel:
+// slot = one z plane of a tile's halo, kHX x (TY + 2) cells per channel group
+// (plus 4 zero cells read, times zero weights, by the cin = 8 MMAs), one plane
+// per 8-channel group.
 template <int G, int TY>
-__device__ __forceinline__ void load_halo(uint8_t* buf, const __nv_bfloat16* __restrict__ x, int x0, int y0, int z0,
-                                          int nx, int ny, int nz, int warp, int lane) {
-  using H = Halo<TY>;
-  constexpr int P = kHX * G;        // 16-byte pieces per halo row
-  constexpr int NW = TY / 4;        // warps per block (8 TY threads)
-  const uint32_t base = smem_addr(buf);
-  // this lane's pieces: (hx, g) and the wrapped x, fixed for the tile
-  const int l0 = lane, l1 = lane + 32;
-  const int xs0 = wrap1(x0 - 1 + l0 / G, nx), xs1 = wrap1(x0 - 1 + l1 / G, nx);
-  for (int r = warp; r < H::rows; r += NW) {
-    const int hy = r % H::HY, hz = r / H::HY;
-    const int row = nx * (wrap1(y0 - 1 + hy, ny) + ny * wrap1(z0 - 1 + hz, nz));
-    const int c = r * kHX;
-    if (l0 < P)
-      cp_async16(base + (l0 % G) * H::plane_bytes + (c + l0 / G) * 16,
-                 x + (size_t)(row + xs0) * (8 * G) + (l0 % G) * 8);
-    if (P > 32 && l1 < P)
-      cp_async16(base + (l1 % G) * H::plane_bytes + (c + l1 / G) * 16,
-                 x + (size_t)(row + xs1) * (8 * G) + (l1 % G) * 8);
+struct ConvRing {
+  static constexpr int HY = TY + 2;
+  static constexpr int PLANE = (kHX * HY + 4) * 16;   // one channel group of one z plane
+  static constexpr int SLOT = G * PLANE;              // one z plane of the halo
+  static constexpr int NSLOT = 6;
+  static constexpr int NACC = TY / 16;                // 128-row accumulators per tile
+  static constexpr int TMEM_COLS = 2 * NACC * 32;     // two buffers of NACC x 32 columns
+};
+
+// The block's contiguous run of tiles, z fastest: tile t is column t / nz
+// (an 8 x TY patch of the x-y plane) at z = t % nz.  Consecutive tiles of a
+// column share two of their three halo planes, so the ring receives one new
+// plane per tile, three at the start of a column.
+struct TileRun {
+  int t0, count, nz, tiles_x;
+  __device__ int col(int i) const { return (t0 + i) / nz; }
+  __device__ int z(int i) const { return (t0 + i) % nz; }
+  __device__ bool fresh(int i) const { return i == 0 || col(i) != col(i - 1); }
+};
+
+// Halo plane z (wrapped) of column c into ring slot `slot` by the copying
+// threads lt = 0..nl-1; one cp.async group per thread.
+template <int G, int TY>
+__device__ __forceinline__ void load_plane(uint8_t* slot, const __nv_bfloat16* __restrict__ x, int c, int z,
+                                           const TileRun& run, int nx, int ny, int lt, int nl) {
+  using R = ConvRing<G, TY>;
+  constexpr int P = kHX * G;  // 16-byte pieces per halo row
+  const int x0 = (c % run.tiles_x) * kTX, y0 = (c / run.tiles_x) * TY;
+  const uint32_t base = smem_addr(slot);
+  for (int p = lt; p < R::HY * P; p += nl) {
+    const int hy = p / P, l = p - hy * P, hx = l / G, g = l - hx * G;
+    const int cell = wrap1(x0 - 1 + hx, nx) + nx * (wrap1(y0 - 1 + hy, ny) + ny * z);
+    cp_async16(base + g * R::PLANE + (hy * kHX + hx) * 16, x + (size_t)cell * (8 * G) + g * 8);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// halo cell of output cell (0, 0) shifted by tap t = (kz * 3 + ky) * 3 + kx
-template <int TY>
-__host__ __device__ constexpr int tap_offset(int t) {
-  return ((t / 9) * Halo<TY>::HY + (t / 3) % 3) * kHX + t % 3;
-}
-
 // G = cin / 8 channel groups, tiles of 8 x TY x 1 cells (TY / 16 accumulators
-// of 128 rows).  Persistent: each block copies the weights once and loops
-// over tiles; the next tile's halo is copied (cp.async) into the second
-// buffer while the tensor core works on the current one.
+// of 128 rows).  Persistent, 256 threads, warp-specialised:
+//  * warps 0 .. NACC-1: lane 0 issues accumulator q = warp's MMAs (27 taps x
+//    cin / 16 K steps) into one of two TMEM buffers;
+//  * warps 2, 3: copy halo planes into the ring (cp.async);
+//  * warps 4..7: epilogue (TMEM lanes 32 (warp - 4) ..): bias, ReLU or the
+//    ReLU mask, BF16 / FP32 stores.
+// mbarriers: slot full (copying threads) / empty (tcgen05.commit once no
+// later tile reads the plane); accumulator buffer full (commit) / empty
+// (epilogue warps).  The weights (packed once by conv_pack) are copied into
+// shared memory once per block.
 template <int G, int TY>
-__global__ void __launch_bounds__(8 * TY, 1) conv3d_tc_kernel(ConvArgs a) {
-  using H = Halo<TY>;
-  constexpr int NT = 8 * TY, NACC = TY / 16;
-  constexpr int kBuf = G * H::plane_bytes;  // one halo buffer
+__global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
+  using R = ConvRing<G, TY>;
+  constexpr int NS = R::NSLOT, NACC = R::NACC;
+  constexpr int NL = 64;  // copying threads
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Kp = a.kchunks * kKC;
   const int bBytes = a.npad * Kp * 2;
   uint8_t* sB = smem;
-  uint8_t* sH = smem + ((bBytes + 1023) & ~1023);  // two halo buffers
-  float* sBias = reinterpret_cast<float*>(sH + 2 * kBuf);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sBias + 32);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint8_t* ring = smem + ((bBytes + 1023) & ~1023);
+  float* sBias = reinterpret_cast<float*>(ring + NS * R::SLOT);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sBias + 32);
+  uint64_t* empty = full + NS;
+  uint64_t* afull = empty + NS;
+  uint64_t* aempty = afull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(aempty + 2);
 
   const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
   const int tiles_x = nx / kTX, tiles_y = ny / TY;
   const int ntiles = tiles_x * tiles_y * nz;
-  int tile = blockIdx.x;
-  if (tile < ntiles)
-    load_halo<G, TY>(sH, a.x, (tile % tiles_x) * kTX, ((tile / tiles_x) % tiles_y) * TY, tile / (tiles_x * tiles_y),
-                     nx, ny, nz, warp, lane);
+  TileRun run;
+  run.t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+  run.count = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x) - run.t0;
+  run.nz = nz;
+  run.tiles_x = tiles_x;
 
-  // weights: a straight copy of the packed image, once per block
-  for (int i = tid; i < bBytes / 16; i += NT)
+  // weights: a straight copy of the packed image, once per block; zero pad cells
+  for (int i = tid; i < bBytes / 16; i += 256)
     reinterpret_cast<uint4*>(sB)[i] = __ldg(reinterpret_cast<const uint4*>(a.wpack) + i);
-  constexpr int kPad = H::plane_cells - H::cells;
-  for (int i = tid; i < 2 * G * kPad; i += NT)
-    *reinterpret_cast<uint4*>(sH + (i / kPad) * H::plane_bytes + (H::cells + i % kPad) * 16) =
-        make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < NS * G * 4; i += 256)
+    *reinterpret_cast<uint4*>(ring + (i / 4) * R::PLANE + (kHX * R::HY + i % 4) * 16) = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 32) sBias[tid] = (a.bias && tid < a.cout) ? __ldg(a.bias + tid) : 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(R::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {  // one arrival per accumulator's issuing thread
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(NACC) : "memory");
+  if (tid == 0) {
+    for (int i = 0; i < NS; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + i)), "r"(NL) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(empty + i)), "r"(NACC) : "memory");
+    }
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(afull + i)), "r"(NACC) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(aempty + i)) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights and pads, for the tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const uint32_t idesc = make_idesc(kM, a.npad);
-  const uint32_t sbo_b = (Kp / 8) * 128;
-  const int co_n = a.cout;
   bool ok = true;
-
-  for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
-    uint8_t* cur = sH + (it & 1) * kBuf;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    // lane 0 of warp 4 q issues accumulator q's MMAs and commits them
-    if ((tid & 127) == 0 && ok) {
-      const int q = tid >> 7;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // GEMM row m of accumulator q = tile cell (m % 8, 16 q + m / 8): the rows
-      // of a core matrix are 8 consecutive halo cells along x (16 bytes
-      // apart), 8-row groups are one halo row apart (SBO = kHX * 16); tap t
-      // reads the halo shifted by its offset (the mirrored tap for the input
-      // gradient).  Descriptor address fields are in 16-byte units, so shifts
-      // add to the descriptor.
-      const uint64_t a0 = make_desc(smem_addr(cur), G == 4 ? H::plane_bytes : 16, kHX * 16);
+  if (warp < NACC) {
+    // ---- MMA issue: accumulator q -------------------------------------
+    if (lane == 0) {
+      const int q = warp;
+      const uint32_t idesc = make_idesc(kM, a.npad);
+      const uint32_t sbo_b = (Kp / 8) * 128;
       const uint32_t b_addr = smem_addr(sB);
+      int e = -1;       // ring index of the newest plane of the current tile
+      int seen = -1;    // ring entries up to this one are known to have landed
+      int freed = 0;    // ring indices below this have been released
+      int issued = 0;
+      for (int i = 0; i < run.count && ok; i++) {
+        e += run.fresh(i) ? 3 : 1;
+        // the tile's planes z-1, z, z+1 are ring entries e-2, e-1, e; the
+        // entries shared with the previous tile need no second wait
+        for (int k = seen + 1; k <= e && ok; k++) ok = mbar_wait(smem_addr(full + k % NS), (k / NS) & 1);
+        seen = e;
+        const int b = i & 1;
+        if (ok && i >= 2) ok = mbar_wait(smem_addr(aempty + b), (i / 2 - 1) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // GEMM row m of accumulator q = tile cell (m % 8, 16 q + m / 8): the
+        // rows of a core matrix are 8 consecutive halo cells along x (16
+        // bytes apart), 8-row groups one halo row apart (SBO = kHX * 16); tap
+        // t reads plane kz's slot from the cell shifted by (kx, ky) (the
+        // mirrored tap for the input gradient).  Address fields count
+        // 16-byte units, so shifts add to the descriptor.
+        uint64_t a0[3];
 #pragma unroll
-      for (int t = 0; t < 27; t++) {
-        const int off = a.flip ? tap_offset<TY>(26 - t) : tap_offset<TY>(t);
+        for (int kz = 0; kz < 3; kz++)
+          a0[kz] = make_desc(smem_addr(ring + ((e - 2 + kz) % NS) * R::SLOT), G == 4 ? R::PLANE : 16, kHX * 16) +
+                   (uint64_t)(q * 16 * kHX);
+        const uint32_t d = tmem + (uint32_t)((b * NACC + q) * 32);
 #pragma unroll
-        for (int h = 0; h < (G == 4 ? 2 : 1); h++) {
-          const uint64_t bdesc = (G == 4) ? make_desc(b_addr + (t * 4 + 2 * h) * 128, 128, sbo_b)
-                                          : make_desc(b_addr + t * 128, (27 - t) * 128, sbo_b);
-          const uint32_t acc = (t > 0 || h > 0) ? 1u : 0u;
-          // G = 4: k = 16 channels 16h..16h+15 (planes 2h, 2h+1); G = 1: the
-          // 8 channels of tap t, then 8 whose weights are the zero k-group 27
-          const uint64_t adesc =
-              a0 + (uint64_t)(off + q * (16 * kHX) + (G == 4 ? h * (2 * H::plane_bytes / 16) : 0));
+        for (int t = 0; t < 27; t++) {
+          const int tt = a.flip ? 26 - t : t;
+          const int kz = tt / 9, off = ((tt / 3) % 3) * kHX + tt % 3;
+#pragma unroll
+          for (int h = 0; h < (G == 4 ? 2 : 1); h++) {
+            const uint64_t bdesc = (G == 4) ? make_desc(b_addr + (t * 4 + 2 * h) * 128, 128, sbo_b)
+                                            : make_desc(b_addr + t * 128, (27 - t) * 128, sbo_b);
+            const uint32_t acc = (t > 0 || h > 0) ? 1u : 0u;
+            // G = 4: k = 16 channels 16h..16h+15 (planes 2h, 2h+1); G = 1: the
+            // 8 channels of tap t, then 8 whose weights are the zero k-group 27
+            const uint64_t adesc =
+                (kz == 0 ? a0[0] : kz == 1 ? a0[1] : a0[2]) + (uint64_t)(off + (G == 4 ? h * (2 * R::PLANE / 16) : 0));
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(afull + b))
+                     : "memory");
+        issued = i + 1;
+        // release the planes that no later tile reads
+        const int keep = (i + 1 < run.count) ? (run.fresh(i + 1) ? e + 1 : e - 1) : e + 1;
+        for (; freed < keep; freed++)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_addr(empty + freed % NS))
+                       : "memory");
+      }
+      // nothing of this thread in flight when TMEM is freed
+      if (issued > 0) {
+        const bool done = mbar_wait(smem_addr(afull + (issued - 1) % 2), ((issued - 1) / 2) & 1);
+        ok = ok && done;
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  } else if (warp == 2 || warp == 3) {
+    // ---- copies: ring entry k goes to slot k % NS ------------------------
+    const int lt = tid - 64;
+    int k = 0;
+    for (int i = 0; i < run.count && ok; i++) {
+      const int c = run.col(i), z = run.z(i);
+      const int first = run.fresh(i) ? -1 : 1;
+      for (int dz = first; dz <= 1 && ok; dz++, k++) {
+        if (k >= NS) ok = mbar_wait(smem_addr(empty + k % NS), (k / NS - 1) & 1);
+        if (!ok) break;
+        load_plane<G, TY>(ring + (k % NS) * R::SLOT, a.x, c, wrap1(z + dz, nz), run, nx, ny, lt, NL);
+        if (k >= 1) {  // the previous entry's pieces have landed
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + (k - 1) % NS)) : "memory");
+        }
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok && k > 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + (k - 1) % NS)) : "memory");
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM lanes 32 (warp - 4) + lane = GEMM row -------------
+    const int ew = warp - 4, row = 32 * ew + lane;
+    const int co_n = a.cout;
+    for (int i = 0; i < run.count; i++) {
+      const int b = i & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(afull + b), (i / 2) & 1));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int c = run.col(i), z0 = run.z(i);
+      const int x0 = (c % tiles_x) * kTX, y0 = (c / tiles_x) * TY;
+#pragma unroll
+      for (int q = 0; q < NACC; q++) {
+        const int cell = (x0 + (row & 7)) + nx * ((y0 + 16 * q + (row >> 3)) + ny * z0);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)((b * NACC + q) * 32);
+        float acc[32];
+        uint32_t r[16];
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+          if (half >= a.npad / 16) break;
           asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + q * 32),
-              "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-              : "memory");
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr + half * 16));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; j++) acc[half * 16 + j] = __uint_as_float(r[j]);
+        }
+        // 8 channels (16 bytes of BF16) at a time; cout is 8 or 32
+#pragma unroll
+        for (int c8 = 0; c8 < 4; c8++) {
+          if (c8 >= co_n / 8) break;
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            v[j] = acc[c8 * 8 + j] + sBias[c8 * 8 + j];
+            if (a.relu) v[j] = fmaxf(v[j], 0.f);
+          }
+          if (a.mask) {
+            const uint4 mk = load16(a.mask + (size_t)cell * co_n + c8 * 8);
+            const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const float m = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mw[j / 2] >> (16 * (j & 1)))));
+              v[j] = m > 0.f ? v[j] : 0.f;
+            }
+          }
+          if (a.y)
+            *reinterpret_cast<uint4*>(a.y + (size_t)cell * co_n + c8 * 8) =
+                make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                           pack_bf16x2(v[6], v[7]));
+          if (a.y32) {
+            float4* o = reinterpret_cast<float4*>(a.y32 + (size_t)cell * co_n + c8 * 8);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+          }
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(bar))
-                   : "memory");
+      // the buffer's TMEM has been read: the tile after next may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(aempty + b)) : "memory");
     }
-    // the other buffer was last read by the previous tile's MMAs, which completed
-    const int next = tile + gridDim.x;
-    if (next < ntiles)
-      load_halo<G, TY>(sH + ((it + 1) & 1) * kBuf, a.x, (next % tiles_x) * kTX, ((next / tiles_x) % tiles_y) * TY,
-                       next / (tiles_x * tiles_y), nx, ny, nz, warp, lane);
-
-    if (ok) ok = mbar_wait(smem_addr(bar), it & 1);
-    if (!ok) {
-      if ((tid & 127) == 0) atomicExch(a.err, 1);
-      // give in-flight tensor-core work a bounded chance to finish before freeing
-      mbar_wait(smem_addr(bar), it & 1);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok);  // the epilogue's tcgen05.ld is warp-collective
-    if (!ok) break;
-
-    // epilogue: warp w reads accumulator w / 4, TMEM lanes 32 (w % 4) ..; its
-    // lane holds GEMM row 32 (w % 4) + lane, columns = output channels
-    const int q = warp >> 2, row = 32 * (warp & 3) + lane;
-    const int x0 = (tile % tiles_x) * kTX, y0 = ((tile / tiles_x) % tiles_y) * TY, z0 = tile / (tiles_x * tiles_y);
-    const int cell = (x0 + (row & 7)) + nx * ((y0 + 16 * q + (row >> 3)) + ny * z0);
-    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + q * 32;
-    float acc[32];
-    uint32_t r[16];
-#pragma unroll
-    for (int half = 0; half < 2; half++) {
-      if (half >= a.npad / 16) break;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr + half * 16));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int i = 0; i < 16; i++) acc[half * 16 + i] = __uint_as_float(r[i]);
-    }
-    // 8 channels (16 bytes of BF16) at a time; cout is 8 or 32
-#pragma unroll
-    for (int c8 = 0; c8 < 4; c8++) {
-      if (c8 >= co_n / 8) break;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; i++) {
-        v[i] = acc[c8 * 8 + i] + sBias[c8 * 8 + i];
-        if (a.relu) v[i] = fmaxf(v[i], 0.f);
-      }
-      if (a.mask) {
-        const uint4 mk = load16(a.mask + (size_t)cell * co_n + c8 * 8);
-        const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const float m = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mw[i / 2] >> (16 * (i & 1)))));
-          v[i] = m > 0.f ? v[i] : 0.f;
-        }
-      }
-      if (a.y)
-        *reinterpret_cast<uint4*>(a.y + (size_t)cell * co_n + c8 * 8) =
-            make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                       pack_bf16x2(v[6], v[7]));
-      if (a.y32) {
-        float4* o = reinterpret_cast<float4*>(a.y32 + (size_t)cell * co_n + c8 * 8);
-        o[0] = make_float4(v[0], v[1], v[2], v[3]);
-        o[1] = make_float4(v[4], v[5], v[6], v[7]);
-      }
-    }
-    // TMEM read before the next tile's MMAs overwrite it
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
+  if (!ok) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(R::TMEM_COLS) : "memory");
 }
 
 // Pack conv weights w[cout][cin][27] (FP32, PyTorch order, tap = (kz*3+ky)*3+kx)
@@ -772,8 +832,10 @@ int conv_npad(int n) { return n <= 16 ? 16 : 32; }
 int conv_kchunks(int c) { return (27 * c + kKC - 1) / kKC; }
 size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty) {
   const size_t b = (size_t)npad * kchunks * kKC * 2;
-  const size_t plane = ty == 32 ? Halo<32>::plane_bytes : Halo<16>::plane_bytes;
-  return ((b + 1023) & ~(size_t)1023) + 2 * (size_t)(cin / 8) * plane + 32 * sizeof(float) + 64;
+  const size_t slot = ty == 32 ? (cin == 32 ? ConvRing<4, 32>::SLOT : ConvRing<1, 32>::SLOT)
+                               : (cin == 32 ? ConvRing<4, 16>::SLOT : ConvRing<1, 16>::SLOT);
+  // weights, ring, bias, 16 mbarriers, TMEM address
+  return ((b + 1023) & ~(size_t)1023) + ConvRing<4, 32>::NSLOT * slot + 32 * sizeof(float) + 16 * 8 + 16;
 }
 
 namespace {
@@ -832,8 +894,11 @@ cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
       int sms = 0, per_sm = 0;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3d_tc_kernel<G, TY>, 8 * TY, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3d_tc_kernel<G, TY>, 256, smem);
       if (e != cudaSuccess) return e;
+      // resident blocks of an SM share its 512 TMEM columns
+      const int tmem_cap = 512 / ConvRing<G, TY>::TMEM_COLS;
+      per_sm = per_sm < tmem_cap ? per_sm : tmem_cap;
       cap = sms * (per_sm > 0 ? per_sm : 1);
       if (c.used < kCacheSizes) {
         c.fn[c.used] = fn;
@@ -845,7 +910,7 @@ cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
   }
   const long long tiles = (long long)(a.n[0] / kTX) * (a.n[1] / TY) * a.n[2];
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  conv3d_tc_kernel<G, TY><<<grid, 8 * TY, smem, s>>>(a);
+  conv3d_tc_kernel<G, TY><<<grid, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 }  // namespace
