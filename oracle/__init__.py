@@ -5,7 +5,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 package imports nothing from it.
 
 The arithmetic lives in ``mhd_oracle.c`` (plain loops, FP64, periodic
-indexing); this module compiles it with gcc, loads it with ctypes and adds the
+indexing, optional outflow or reflecting ghost layers); this module compiles it with gcc, loads it with ctypes and adds the
 FP64 diagnostics (exactly rounded sums with ``math.fsum``) and the coarse-grid
 restriction, both written from their plain definitions.  ``cnn.py`` is the
 FP64 oracle of the learned coarse-grid correction (network, projection, loss,
@@ -74,6 +74,12 @@ def _load():
             lib.orc_limiter.restype = ctypes.c_double
             lib.orc_freezing_speed.argtypes = [dp, dp, ctypes.c_double]
             lib.orc_freezing_speed.restype = ctypes.c_double
+            lib.orc_set_boundary.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.orc_set_boundary.restype = ctypes.c_int
+            lib.orc_boundary.argtypes = [ctypes.c_int]
+            lib.orc_boundary.restype = ctypes.c_int
+            lib.orc_fill_ghosts.argtypes = [i3, ctypes.c_void_p]
+            lib.orc_fill_ghosts.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -119,6 +125,55 @@ def set_scheme(limiter: str = "vanleer", freezing: str = "bound") -> None:
         raise ValueError("bad scheme")
 
 
+BOUNDARIES = {"periodic": 0, "outflow": 1, "reflecting": 2}
+GHOST = 4  # ghost cells at each end of a non-periodic axis, inside the box
+
+
+def set_boundary(axis: int, mode: str) -> None:
+    """Boundary of axis (0=x, 1=y, 2=z) for the following sweeps: periodic
+    (the paper's), outflow or reflecting (extensions; the axis then keeps
+    GHOST ghost cells at each end, refilled before every sweep)."""
+    if _load().orc_set_boundary(int(axis), BOUNDARIES[mode]):
+        raise ValueError("bad boundary")
+
+
+def boundary(axis: int) -> str:
+    code = _load().orc_boundary(int(axis))
+    return {v: k for k, v in BOUNDARIES.items()}[code]
+
+
+class boundaries:
+    """Context manager: boundaries(x="outflow", z="reflecting") sets the given
+    axes and restores periodic boundaries on every axis at exit."""
+
+    def __init__(self, **modes):
+        self.modes = modes
+
+    def __enter__(self):
+        for name, mode in self.modes.items():
+            set_boundary("xyz".index(name), mode)
+        return self
+
+    def __exit__(self, *exc):
+        for a in range(3):
+            set_boundary(a, "periodic")
+        return False
+
+
+def _check_boundary_dims(state: np.ndarray) -> None:
+    nz, ny, nx = state.shape[1:]
+    for a, n in enumerate((nx, ny, nz)):
+        if _load().orc_boundary(a) and n < 3 * GHOST:
+            raise ValueError(f"a non-periodic axis needs at least {3 * GHOST} cells")
+
+
+def fill_ghosts(state: np.ndarray) -> None:
+    """In place: refill the ghost layers of the non-periodic axes (the sweeps
+    and the CFL rate do this themselves before they read the state)."""
+    _check_boundary_dims(state)
+    _load().orc_fill_ghosts(_dims(state), _ptrs(state))
+
+
 def limiter(a: float, b: float) -> float:
     """phi(a, b) of the current limiter."""
     return _load().orc_limiter(float(a), float(b))
@@ -133,16 +188,19 @@ def freezing_speed(u, b, gamma: float) -> float:
 
 def fluid_sweep(state: np.ndarray, d: int, tau: float, gamma: float) -> None:
     """In place: relaxing-TVD fluid sweep along axis d (0=x, 1=y, 2=z), step tau."""
+    _check_boundary_dims(state)
     _load().orc_fluid_sweep(_dims(state), gamma, _ptrs(state), int(d), float(tau))
 
 
 def mag_sweep(state: np.ndarray, d: int, tau: float) -> None:
     """In place: magnetic advection-constraint sweep along axis d, step tau."""
+    _check_boundary_dims(state)
     _load().orc_mag_sweep(_dims(state), _ptrs(state), int(d), float(tau))
 
 
 def cfl_rate(state: np.ndarray, gamma: float) -> float:
     """max over cells and axes of (|v_d| + c_f*) / h_d."""
+    _check_boundary_dims(state)
     return _load().orc_cfl_rate(_dims(state), gamma, _ptrs(state))
 
 
@@ -153,11 +211,13 @@ def cfl_dt(state: np.ndarray, gamma: float, cfl: float) -> float:
 
 def step(state: np.ndarray, dt: float, gamma: float) -> None:
     """In place: one full step (x, y, z then z, y, x; each sweep tau = dt/2)."""
+    _check_boundary_dims(state)
     _load().orc_step(_dims(state), gamma, _ptrs(state), float(dt))
 
 
 def run(state: np.ndarray, nsteps: int, cfl: float, gamma: float):
     """In place: nsteps full steps with per-step CFL dt. Returns (t, dts)."""
+    _check_boundary_dims(state)
     dts = np.zeros(max(nsteps, 1), dtype=np.float64)
     t = _load().orc_run(_dims(state), gamma, _ptrs(state), int(nsteps), float(cfl),
                         dts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))

@@ -37,7 +37,8 @@
  *   - schedule: forward half [fluid_d, magnetic_d] for d = x, y, z, reverse
  *     half [magnetic_d, fluid_d] for d = z, y, x, every sweep with tau = dt/2;
  *   - CFL: dt = 2 * cfl / max_cells max_d (|v_d| + c_f*) / h_d;
- *   - domain is the periodic unit cube, h_d = 1 / n_d.
+ *   - domain is the periodic unit cube, h_d = 1 / n_d (non-periodic axes: see
+ *     the boundaries below).
  *
  * Layout: 8 arrays (rho, m_x, m_y, m_z, e, b_x, b_y, b_z), each nx*ny*nz
  * doubles, flat index i + nx*(j + ny*k).
@@ -56,6 +57,79 @@ enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
  * which the total-energy scheme drives p negative. */
 static double g_pfloor = 0.0;
 void orc_set_pressure_floor(double p_floor) { g_pfloor = p_floor > 0.0 ? p_floor : 0.0; }
+
+/* Boundaries (an extension: the paper's runs are periodic).  An axis is
+ * periodic (0, the default), outflow (1) or reflecting (2).  A non-periodic
+ * axis of n cells keeps GHOST = 4 ghost cells at each end inside the box:
+ * interior cells GHOST .. n-GHOST-1, wall faces GHOST (low) and n-GHOST (the
+ * low face of the first high ghost cell).  Before every sweep and before the
+ * CFL rate the ghost layers are refilled from the interior, axis by axis in
+ * the order x, y, z over the whole extent of the other two axes:
+ *   outflow:    a ghost cell copies the nearest interior cell; ghost faces of
+ *               the normal field copy the wall face (zero gradient);
+ *   reflecting: a ghost cell copies its mirror image in the wall with the
+ *               normal momentum negated; ghost faces of the normal field copy
+ *               their mirror faces, negated.
+ * The tangential face fields are cell-like along the axis and follow the
+ * cell rule.  The sweeps are then the periodic ones: a cell reads at most 3
+ * cells along the sweep and 1 pencil across, all inside the ghost layers,
+ * and whatever the sweep writes into the ghost layers is replaced by the next
+ * fill.  A non-periodic axis needs n >= 3 GHOST (the sweeps of a shorter
+ * one leave its ghost layers as they are; the Python wrappers refuse it). */
+enum { GHOST = 4 };
+static int g_bc[3] = {0, 0, 0};
+int orc_set_boundary(int axis, int mode) {
+    if (axis < 0 || axis > 2 || mode < 0 || mode > 2) return 1;
+    g_bc[axis] = mode;
+    return 0;
+}
+int orc_boundary(int axis) { return (axis < 0 || axis > 2) ? -1 : g_bc[axis]; }
+static int any_boundary(void) { return g_bc[0] || g_bc[1] || g_bc[2]; }
+
+/* Returns 1 (and writes nothing) if a non-periodic axis is shorter than
+ * 3 GHOST cells. */
+int orc_fill_ghosts(const int n[3], double *f[8]) {
+    int d;
+    for (d = 0; d < 3; d++)
+        if (g_bc[d] && n[d] < 3 * GHOST) return 1;
+    for (d = 0; d < 3; d++) {
+        const int mode = g_bc[d], t1 = (d + 1) % 3, t2 = (d + 2) % 3, nd = n[d];
+        const int wlo = GHOST, whi = nd - GHOST;  /* wall faces */
+        long sd, st1, st2;
+        int a1, a2;
+        if (!mode) continue;
+        sd = d == 0 ? 1 : (d == 1 ? n[0] : (long)n[0] * n[1]);
+        st1 = t1 == 0 ? 1 : (t1 == 1 ? n[0] : (long)n[0] * n[1]);
+        st2 = t2 == 0 ? 1 : (t2 == 1 ? n[0] : (long)n[0] * n[1]);
+        for (a2 = 0; a2 < n[t2]; a2++) {
+            for (a1 = 0; a1 < n[t1]; a1++) {
+                const long base = a1 * st1 + a2 * st2;
+                int k, q;
+                for (k = 0; k < GHOST; k++) {
+                    /* cells: low ghost k, high ghost nd-1-k */
+                    const int lo = k, hi = nd - 1 - k;
+                    const int slo = mode == 1 ? wlo : 2 * wlo - 1 - lo;
+                    const int shi = mode == 1 ? whi - 1 : 2 * whi - 1 - hi;
+                    for (q = 0; q < 8; q++) {
+                        double sign = 1.0;
+                        if (q == BX + d) continue;
+                        if (mode == 2 && q == MX + d) sign = -1.0;
+                        f[q][base + lo * sd] = sign * f[q][base + slo * sd];
+                        f[q][base + hi * sd] = sign * f[q][base + shi * sd];
+                    }
+                    /* normal face field: low ghost faces 0..GHOST-1, high
+                     * ghost faces whi+1 .. nd-1 (the wall faces stay) */
+                    f[BX + d][base + lo * sd] =
+                        mode == 1 ? f[BX + d][base + wlo * sd] : -f[BX + d][base + (2 * wlo - lo) * sd];
+                    if (hi > whi)
+                        f[BX + d][base + hi * sd] =
+                            mode == 1 ? f[BX + d][base + whi * sd] : -f[BX + d][base + (2 * whi - hi) * sd];
+                }
+            }
+        }
+    }
+    return 0;
+}
 
 /* periodic wrap of an index */
 static int wrap(int i, int n) {
@@ -241,6 +315,7 @@ static int t2_of(int d) { return (d + 2) % 3; }
  * (the magnetic field is frozen; it only enters through b_c).
  */
 void orc_fluid_sweep(const int n[3], double gamma, double *f[8], int d, double tau) {
+    if (any_boundary()) orc_fill_ghosts(n, f);
     int t1 = t1_of(d), t2 = t2_of(d);
     int nd = n[d];
     double h = 1.0 / nd;
@@ -299,6 +374,7 @@ void orc_fluid_sweep(const int n[3], double gamma, double *f[8], int d, double t
  * energy e is not touched (it is the conserved variable of Eq. 3).
  */
 void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
+    if (any_boundary()) orc_fill_ghosts(n, f);
     int nd = n[d];
     double hd = 1.0 / nd;
     long N = (long)n[0] * n[1] * n[2];
@@ -375,6 +451,7 @@ void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
  * bound sqrt((gamma p + |b_c|^2)/rho); the CFL timestep is 2*cfl/rate. */
 double orc_cfl_rate(const int n[3], double gamma, double *const f[8]) {
     long N = (long)n[0] * n[1] * n[2];
+    if (any_boundary()) orc_fill_ghosts(n, (double **)f);
     double rmax = 0.0;
     long id;
 #pragma omp parallel for reduction(max : rmax) schedule(static)
