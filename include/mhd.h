@@ -139,6 +139,33 @@ int mhd_set_pressure_floor(mhd_t *m, double p_floor);
  * Ensembles always use the paper's scheme. */
 int mhd_set_scheme(mhd_t *m, int limiter, int freezing);
 
+/* Boundaries (an extension: the paper's runs are periodic).  mode 0 =
+ * periodic (the default), 1 = outflow, 2 = reflecting, for physical axis
+ * `axis` (0 = x, 1 = y, 2 = z).  A non-periodic axis keeps 4 ghost cells at
+ * each end inside the box (the caller includes them in n_axis, which must be
+ * at least 12): interior cells 4 .. n-5, wall faces 4 (low) and n-4 (the low
+ * face of the first high ghost cell).  Before every sweep and before every
+ * CFL rate the library refills the ghost layers from the interior, axis by
+ * axis in the order x, y, z:
+ *   outflow:    a ghost cell copies the nearest interior cell; ghost faces of
+ *               the normal field copy the wall face (zero gradient);
+ *   reflecting: a ghost cell copies its mirror image in the wall with the
+ *               normal momentum negated; ghost faces of the normal field copy
+ *               their mirror faces, negated.
+ * Tangential face fields follow the cell rule.  The sweeps themselves are the
+ * periodic ones (a cell reads at most 3 cells along a sweep and 1 pencil
+ * across, all inside the ghost layers); what they write into the ghost
+ * layers is replaced by the next fill, so after a step the ghost layers hold
+ * such values until mhd_fill_ghosts.  The CFL rate is taken over the whole
+ * box after a fill (not fused into the last sweep).  Diagnostics sum the
+ * whole box, ghost layers included.  Ensembles are always periodic.
+ * MHD_E_ARG for a bad axis or mode or too short an axis. */
+int mhd_set_boundary(mhd_t *m, int axis, int mode);
+
+/* Refill the ghost layers of the non-periodic axes now (no-op without any):
+ * after it the whole box, ghosts included, follows the boundary rules. */
+int mhd_fill_ghosts(mhd_t *m);
+
 /* Pencil segment lengths used by the sweeps along x, y and z.  A sweep splits
  * every pencil of n_d cells into n_d/seg_d pieces, each marched by its own
  * thread (more parallelism for small boxes, 8 cells of warm-up re-read per

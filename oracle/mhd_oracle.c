@@ -74,7 +74,8 @@ void orc_set_pressure_floor(double p_floor) { g_pfloor = p_floor > 0.0 ? p_floor
  * cell rule.  The sweeps are then the periodic ones: a cell reads at most 3
  * cells along the sweep and 1 pencil across, all inside the ghost layers,
  * and whatever the sweep writes into the ghost layers is replaced by the next
- * fill.  A non-periodic axis needs n >= 3 GHOST (the sweeps of a shorter
+ * fill.  The CFL rate takes the interior cells only.  A non-periodic axis
+ * needs n >= 3 GHOST (the sweeps of a shorter
  * one leave its ghost layers as they are; the Python wrappers refuse it). */
 enum { GHOST = 4 };
 static int g_bc[3] = {0, 0, 0};
@@ -448,7 +449,9 @@ void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
 }
 
 /* Largest signal rate max_cells max_d (|v_d| + c_f*) / h_d, c_f* the fast-speed
- * bound sqrt((gamma p + |b_c|^2)/rho); the CFL timestep is 2*cfl/rate. */
+ * bound sqrt((gamma p + |b_c|^2)/rho); the CFL timestep is 2*cfl/rate.  With
+ * non-periodic axes: over the interior cells, after refilling the ghosts (a
+ * ghost cell next to the periodic wrap pairs faces from both ends). */
 double orc_cfl_rate(const int n[3], double gamma, double *const f[8]) {
     long N = (long)n[0] * n[1] * n[2];
     if (any_boundary()) orc_fill_ghosts(n, (double **)f);
@@ -461,6 +464,9 @@ double orc_cfl_rate(const int n[3], double gamma, double *const f[8]) {
         c[0] = (int)(id % n[0]);
         c[1] = (int)((id / n[0]) % n[1]);
         c[2] = (int)(id / ((long)n[0] * n[1]));
+        for (a = 0; a < 3; a++)  /* interior cells only along non-periodic axes */
+            if (g_bc[a] && (c[a] < GHOST || c[a] >= n[a] - GHOST)) break;
+        if (a < 3) continue;
         for (a = 0; a < 3; a++) {
             memcpy(cn, c, sizeof cn);
             cn[a] += 1;

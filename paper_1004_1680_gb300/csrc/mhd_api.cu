@@ -69,6 +69,7 @@ struct mhd_s {
   float p_floor = 0.f;  // optional pressure floor after fluid sweeps (0 = off)
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
+  int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
@@ -266,11 +267,58 @@ int sweep_frame(mhd_s* m, int d, const mhd::Box** box, int* kaxis) {
   return MHD_OK;
 }
 
+bool any_bc(const mhd_s* m) { return m->bc[0] || m->bc[1] || m->bc[2]; }
+
+// Refill the ghost layers of the non-periodic axes in the current layout:
+// physical axis a is kernel axis k there, with its normal momentum and face
+// field in slots 1 + k and 5 + k (the exchanges relabel the slots).  Axes in
+// physical order x, y, z.
+int fill_ghosts(mhd_s* m) {
+  if (!any_bc(m)) return MHD_OK;
+  const mhd::Box& b = m->layout == 2 ? m->zbox : (m->layout ? m->tbox : m->box);
+  for (int a = 0; a < 3; a++) {
+    if (!m->bc[a]) continue;
+    int k = a;
+    if (m->layout == 1 && a < 2) k = 1 - a;
+    if (m->layout == 2 && a != 1) k = 2 - a;
+    if (int rc = traced(m, MHD_K_CONTROL, [&] {
+          CK(mhd::launch_ghost_fill(m->cur, b, k, m->bc[a], m->stream));
+          return MHD_OK;
+        }))
+      return rc;
+  }
+  return MHD_OK;
+}
+
+// CFL rate of the current state into *rate (zeroed first).  With ghost
+// layers the rate covers the interior cells only (a ghost cell next to the
+// periodic wrap pairs faces from both ends of the axis), after a refill.
+int state_rate(mhd_s* m, unsigned* rate) {
+  if (int rc = fill_ghosts(m)) return rc;
+  const mhd::Box& b = m->layout == 2 ? m->zbox : (m->layout ? m->tbox : m->box);
+  mhd::CellRange r;
+  for (int a = 0; a < 3; a++) {
+    int k = a;
+    if (m->layout == 1 && a < 2) k = 1 - a;
+    if (m->layout == 2 && a != 1) k = 2 - a;
+    r.lo[k] = m->bc[a] ? mhd::kGhost : 0;
+    r.hi[k] = m->bc[a] ? b.n[k] - mhd::kGhost : b.n[k];
+  }
+  CK(cudaMemsetAsync(rate, 0, sizeof(unsigned), m->stream));
+  const float* cf[8];
+  field_ptrs(m, cf);
+  return traced(m, MHD_K_CONTROL, [&] {
+    CK(mhd::launch_cfl_rate(cf, b, (float)m->gamma, rate, m->stream, &r));
+    return MHD_OK;
+  });
+}
+
 int fluid(mhd_s* m, int d, bool rate) {
   const mhd::Box* box;
   int ka;
   int rc = sweep_frame(m, d, &box, &ka);
   if (rc) return rc;
+  if ((rc = fill_ghosts(m))) return rc;
   mhd::FluidArgs a;
   for (int q = 0; q < 8; q++) {
     a.in[q] = m->cur[q];
@@ -298,6 +346,7 @@ int magnetic(mhd_s* m, int d) {
   int ka;
   int rc = sweep_frame(m, d, &box, &ka);
   if (rc) return rc;
+  if ((rc = fill_ghosts(m))) return rc;
   mhd::MagArgs a;
   for (int q = 0; q < 8; q++) a.in[q] = m->cur[q];
   for (int q = 0; q < 3; q++) a.out[q] = m->spare[5 + q];
@@ -316,17 +365,20 @@ int magnetic(mhd_s* m, int d) {
 
 // The sweep schedule of one full step (Section II.B): x, y, z forward with
 // fluid before magnetic, then z, y, x with magnetic before fluid; the last
-// fluid sweep also accumulates the CFL rate of the new state.
+// fluid sweep also accumulates the CFL rate of the new state (with ghost
+// layers the rate is taken after refilling them instead).
 int full_step(mhd_s* m) {
   int rc;
+  const bool ghosts = any_bc(m);
   for (int d = 0; d < 3; d++) {
     if ((rc = fluid(m, d, false))) return rc;
     if ((rc = magnetic(m, d))) return rc;
   }
   for (int d = 2; d >= 0; d--) {
     if ((rc = magnetic(m, d))) return rc;
-    if ((rc = fluid(m, d, d == 0))) return rc;
+    if ((rc = fluid(m, d, d == 0 && !ghosts))) return rc;
   }
+  if (ghosts && (rc = state_rate(m, &m->sc->rate[1 - m->rcur]))) return rc;
   m->rcur ^= 1;
   return MHD_OK;
 }
@@ -515,10 +567,7 @@ int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
   CK(cudaMemsetAsync(m->sc, 0, sizeof(Scalars), m->stream));
   m->rcur = 0;
-  const float* cf[8];
-  field_ptrs(m, cf);
-  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[0], m->stream));
-  return MHD_OK;
+  return state_rate(m, &m->sc->rate[0]);
 }
 
 int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
@@ -600,9 +649,7 @@ int mhd_submit(mhd_t* m, const float* const in[8], float* const out[8], int nste
   CK(cudaEventRecord(m->ev_free[j], m->s_out));
   CK(cudaMemsetAsync(m->sc, 0, sizeof(Scalars), m->stream));
   m->rcur = 0;
-  const float* cf[8];
-  field_ptrs(m, cf);
-  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[0], m->stream));
+  if (int rc = state_rate(m, &m->sc->rate[0])) return rc;
   if (int rc = run_steps(m, nsteps, cfl)) return rc;
   CK(cudaEventRecord(m->ev_done, m->stream));
   CK(cudaStreamWaitEvent(m->s_out, m->ev_done, 0));
@@ -639,11 +686,24 @@ int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
   int rc = kind == 0 ? fluid(m, axis, false) : magnetic(m, axis);
   if (!rc) rc = ensure_layout(m, 0);
   if (rc) return rc;
-  CK(cudaMemsetAsync(&m->sc->rate[m->rcur], 0, sizeof(unsigned), m->stream));
-  const float* cf[8];
-  field_ptrs(m, cf);
-  CK(mhd::launch_cfl_rate(cf, m->box, (float)m->gamma, &m->sc->rate[m->rcur], m->stream));
-  return MHD_OK;
+  return state_rate(m, &m->sc->rate[m->rcur]);
+}
+
+int mhd_set_boundary(mhd_t* m, int axis, int mode) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (axis < 0 || axis > 2 || mode < 0 || mode > 2) return fail(MHD_E_ARG, "bad axis or boundary mode");
+  if (mode && m->n[axis] < 3 * mhd::kGhost)
+    return fail(MHD_E_ARG, "a non-periodic axis needs at least 12 cells (4 ghost cells at each end)");
+  if (int rc = join_pipeline(m)) return rc;
+  m->bc[axis] = mode;
+  // the rate of the current state under the new boundaries
+  return state_rate(m, &m->sc->rate[m->rcur]);
+}
+
+int mhd_fill_ghosts(mhd_t* m) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = join_pipeline(m)) return rc;
+  return fill_ghosts(m);
 }
 
 int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {

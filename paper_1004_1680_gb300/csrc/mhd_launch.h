@@ -60,6 +60,19 @@ struct MagArgs {
   int lim = 0;         // slope limiter (as FluidArgs::lim)
 };
 
+// Ghost layers of a non-periodic axis (boundary.cu): kernel axis `axis` of
+// the fields as stored in `box`; the normal momentum and face field of that
+// axis are f[1 + axis] and f[5 + axis].
+constexpr int kGhost = 4;
+struct GhostArgs {
+  float* f[8];
+  int axis;
+  int mode;                  // 1 outflow, 2 reflecting
+  int nk, n1, n2;            // extents: the axis, then the other two (n1 the faster)
+  long long sk, s1, s2;      // their strides
+};
+cudaError_t launch_ghost_fill(float* const f[8], const Box& box, int axis, int mode, cudaStream_t s);
+
 struct TransposeArgs {
   const float* in[8];
   float* out[8];
@@ -173,8 +186,12 @@ extern template cudaError_t prepare_mag_t<1>();
 extern template cudaError_t prepare_mag_t<2>();
 // one-time per-device kernel attributes (call on the current device before launching)
 cudaError_t prepare_mag_kernels();
+// cells [lo, hi) per kernel axis (the interior of a box with ghost layers)
+struct CellRange {
+  int lo[3], hi[3];
+};
 cudaError_t launch_cfl_rate(const float* const f[8], const Box& box, float gamma, unsigned* rate,
-                            cudaStream_t s);
+                            cudaStream_t s, const CellRange* range = nullptr);
 // device-side step control: tau = cfl / rate_cur (or the given tau if cfl<0),
 // time += 2 tau, rate_next = 0
 cudaError_t launch_step_control(const unsigned* rate_cur, unsigned* rate_next, float* tau,

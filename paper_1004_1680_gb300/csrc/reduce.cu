@@ -24,7 +24,7 @@ __global__ void cfl_rate_kernel(const float* __restrict__ rho, const float* __re
                                 const float* __restrict__ my, const float* __restrict__ mz,
                                 const float* __restrict__ en, const float* __restrict__ bx,
                                 const float* __restrict__ by, const float* __restrict__ bz, Box box,
-                                float gamma, unsigned* rate) {
+                                float gamma, unsigned* rate, CellRange r) {
   const long long N = (long long)box.n[0] * box.n[1] * box.n[2];
   float rmax = 0.f;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -32,6 +32,7 @@ __global__ void cfl_rate_kernel(const float* __restrict__ rho, const float* __re
     const int i = (int)(c % box.n[0]);
     const int j = (int)((c / box.n[0]) % box.n[1]);
     const int k = (int)(c / box.stride[2]);
+    if (i < r.lo[0] || i >= r.hi[0] || j < r.lo[1] || j >= r.hi[1] || k < r.lo[2] || k >= r.hi[2]) continue;
     float m[3] = {__ldg(mx + c), __ldg(my + c), __ldg(mz + c)};
     float b[3];
     b[0] = 0.5f * (__ldg(bx + c) + __ldg(bx + up1(c, i, box.n[0], box.stride[0])));
@@ -44,12 +45,17 @@ __global__ void cfl_rate_kernel(const float* __restrict__ rho, const float* __re
 }
 
 cudaError_t launch_cfl_rate(const float* const f[8], const Box& box, float gamma, unsigned* rate,
-                            cudaStream_t s) {
+                            cudaStream_t s, const CellRange* range) {
   const long long N = (long long)box.n[0] * box.n[1] * box.n[2];
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  CellRange r;
+  for (int d = 0; d < 3; d++) {
+    r.lo[d] = range ? range->lo[d] : 0;
+    r.hi[d] = range ? range->hi[d] : box.n[d];
+  }
   cfl_rate_kernel<<<(unsigned)blocks, 256, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7],
-                                                   box, gamma, rate);
+                                                   box, gamma, rate, r);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,8 @@ SIGNATURES = {
     "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_set_pressure_floor": (_I, [_P, _D]),
     "mhd_set_scheme": (_I, [_P, _I, _I]),
+    "mhd_set_boundary": (_I, [_P, _I, _I]),
+    "mhd_fill_ghosts": (_I, [_P]),
     "mhd_ens_set_pressure_floor": (_I, [_P, _D]),
     "mhd_diagnostics": (_I, [_P, _DP]),
     "mhd_profile": (_I, [_P, _I]),
@@ -234,6 +236,19 @@ class Box:
         """Scheme variant (ablation) for the following sweeps; the default is
         the paper's scheme."""
         _check(self.lib.mhd_set_scheme(self.h, self.LIMITERS[limiter], self.FREEZING[freezing]))
+
+    BOUNDARIES = {"periodic": 0, "outflow": 1, "reflecting": 2}
+    GHOST = 4
+
+    def set_boundary(self, axis: int, mode: str):
+        """Boundary of physical axis 0/1/2: periodic (the paper's), outflow or
+        reflecting; a non-periodic axis keeps GHOST ghost cells at each end
+        inside the box (at least 12 cells in all), refilled before every sweep."""
+        _check(self.lib.mhd_set_boundary(self.h, int(axis), self.BOUNDARIES[mode]))
+
+    def fill_ghosts(self):
+        """Refill the ghost layers of the non-periodic axes now."""
+        _check(self.lib.mhd_fill_ghosts(self.h))
 
     def set_xpath(self, mode: int):
         """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic;

@@ -90,3 +90,8 @@ def test_submit_rejects_null_handle(lib):
 
 def test_set_scheme_rejects_null_handle(lib):
     assert lib.mhd_set_scheme(None, 0, 0) == M.MHD_E_ARG
+
+
+def test_boundary_calls_reject_null_handle(lib):
+    assert lib.mhd_set_boundary(None, 0, 1) == M.MHD_E_ARG
+    assert lib.mhd_fill_ghosts(None) == M.MHD_E_ARG

@@ -109,12 +109,15 @@ def test_reflecting_walls_equal_the_mirror_doubled_periodic_box(oracle_lib, magn
     box = np.zeros((8, nz, ny, nx + 2 * GH))
     box[:, :, :, GH:GH + nx] = half
     box[5, :, :, GH + nx] = 0.0  # high wall face
-    dt = 0.25 / oracle.cfl_rate(full, G)
+    dts = []
     for _ in range(4):
-        oracle.step(full, dt, G)
+        dts.append(oracle.cfl_dt(full, G, 0.6))
+        oracle.step(full, dts[-1], G)
     with oracle.boundaries(x="reflecting"):
-        for _ in range(4):
-            oracle.step(box, dt, G)
+        for n in range(4):
+            # the rate over the interior equals the doubled box's (mirror cells)
+            assert oracle.cfl_dt(box, G, 0.6) == pytest.approx(dts[n], rel=1e-13)
+            oracle.step(box, dts[n], G)
     got = box[:, :, :, GH:GH + nx]
     want = full[:, :, :, :nx]
     scale = np.max(np.abs(want), axis=(1, 2, 3)) + 1e-30
