@@ -68,6 +68,11 @@ def parse():
                    help="pencil segment length for every axis (0: the library's choice)")
     p.add_argument("--freezing", choices=["bound", "fast"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
+    p.add_argument("--bc", default="",
+                   help="non-periodic axes, e.g. x=outflow,z=reflecting (4 ghost cells at each end "
+                        "inside the box; the paper's runs are periodic)")
+    p.add_argument("--mach", type=float, default=1.0, help="rms Mach number of the turbulence recipe")
+    p.add_argument("--beta", type=float, default=1.0, help="plasma beta of the turbulence recipe")
     p.add_argument("--learned-reps", type=int, default=20,
                    help="timed applications of the 64^3 learned correction (0: skip)")
     return p.parse_args()
@@ -405,8 +410,14 @@ def run_ours(args, rank, world, local):
         box.set_xpath(args.xpath)
     if args.seg:
         box.set_segments(args.seg, args.seg, args.seg)
+    bcs = {}
+    for item in filter(None, args.bc.split(",")):
+        axis, mode = item.split("=")
+        box.set_boundary("xyz".index(axis), mode)
+        bcs[axis] = mode
     stream = torch.cuda.current_stream()
-    st = ic.turbulence((n, n, n), seed=args.seed + rank, device="cuda", dtype=torch.float32)
+    st = ic.turbulence((n, n, n), seed=args.seed + rank, mach=args.mach, beta=args.beta, device="cuda",
+                       dtype=torch.float32)
     host = st.cpu().pin_memory()     # for the end-to-end leg
     box.set_state(st)
     torch.cuda.synchronize()
@@ -415,7 +426,9 @@ def run_ours(args, rank, world, local):
 
     box.run(args.warmup, args.cfl)
     box.cfl_dt(args.cfl)               # raises if the state went invalid
-    launches_per_step = 19             # 12 sweeps, step control, up to 6 transposes (x path 3)
+    # 12 sweeps, step control, up to 6 transposes (x path 3); with ghost
+    # layers a fill per non-periodic axis before every sweep
+    launches_per_step = 19 + 12 * len(bcs)
     box.profile(args.steps * launches_per_step + 16)
 
     uuid = None
@@ -535,11 +548,15 @@ def run_ours(args, rank, world, local):
                "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": f"decaying MHD turbulence {n}^3, periodic, FP32 state",
+               "config": {"workload": f"decaying MHD turbulence {n}^3, "
+                                      f"{'periodic' if not bcs else 'non-periodic ' + ','.join(sorted(bcs))}, FP32 state",
                           "n": n, "seed": args.seed, "cfl": args.cfl,
                           "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
                           "xpath": args.xpath or "auto",
+                          **({"boundaries": bcs, "interior_cells": int(np.prod([n - 8 if a in bcs else n for a in "xyz"]))}
+                             if bcs else {}),
+                          **({"mach": args.mach, "beta": args.beta} if (args.mach, args.beta) != (1.0, 1.0) else {}),
                           "segments": args.seg or "auto",
                           "l2": f"state {32 * N / 1e9:.1f} GB per copy > L2 (no flush needed)",
                           "parallelism": f"replicas x{world}"},

@@ -27,9 +27,20 @@ __global__ void __launch_bounds__(256) ghost_fill_kernel(GhostArgs a) {
   float* const bn = k == 0 ? a.f[5] : (k == 1 ? a.f[6] : a.f[7]);  // normal face field
   for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    const long long p = id % plane;
-    const int layer = (int)((id / plane) % kGhost);
-    const int side = (int)(id / (plane * kGhost));
+    // along the contiguous axis the 2 x kGhost ghost cells of a row are
+    // neighbouring threads (16 contiguous bytes per side); across it,
+    // neighbouring threads take neighbouring rows (contiguous along x)
+    long long p;
+    int layer, side;
+    if (k == 0) {
+      layer = (int)(id % kGhost);
+      side = (int)((id / kGhost) & 1);
+      p = id / (2 * kGhost);
+    } else {
+      p = id % plane;
+      layer = (int)((id / plane) % kGhost);
+      side = (int)(id / (plane * kGhost));
+    }
     const long long base = (p % a.n1) * a.s1 + (p / a.n1) * a.s2;
     const int dst = side ? nk - 1 - layer : layer;
     const int src = a.mode == 1 ? (side ? whi - 1 : wlo) : (side ? 2 * whi - 1 - dst : 2 * wlo - 1 - dst);

@@ -332,6 +332,14 @@ int fluid(mhd_s* m, int d, bool rate) {
   a.seg = m->seg[d];
   a.lim = m->lim;
   a.fast = m->fast;
+  for (int p = 0; p < 3; p++) {  // the fused rate covers the interior cells
+    if (!m->bc[p]) continue;
+    int k = p;
+    if (m->layout == 1 && p < 2) k = 1 - p;
+    if (m->layout == 2 && p != 1) k = 2 - p;
+    a.rate_lo[k] = mhd::kGhost;
+    a.rate_hi[k] = box->n[k] - mhd::kGhost;
+  }
   rc = traced(m, MHD_K_FLUID_X + d, [&] {
     CK(mhd::launch_fluid(ka, rate, a, m->stream));
     return MHD_OK;
@@ -365,20 +373,19 @@ int magnetic(mhd_s* m, int d) {
 
 // The sweep schedule of one full step (Section II.B): x, y, z forward with
 // fluid before magnetic, then z, y, x with magnetic before fluid; the last
-// fluid sweep also accumulates the CFL rate of the new state (with ghost
-// layers the rate is taken after refilling them instead).
+// fluid sweep also accumulates the CFL rate of the new state (of its interior
+// cells with ghost layers: those cells and the faces their rate reads are
+// final once the sweep has written them; a refill changes neither).
 int full_step(mhd_s* m) {
   int rc;
-  const bool ghosts = any_bc(m);
   for (int d = 0; d < 3; d++) {
     if ((rc = fluid(m, d, false))) return rc;
     if ((rc = magnetic(m, d))) return rc;
   }
   for (int d = 2; d >= 0; d--) {
     if ((rc = magnetic(m, d))) return rc;
-    if ((rc = fluid(m, d, d == 0 && !ghosts))) return rc;
+    if ((rc = fluid(m, d, d == 0))) return rc;
   }
-  if (ghosts && (rc = state_rate(m, &m->sc->rate[1 - m->rcur]))) return rc;
   m->rcur ^= 1;
   return MHD_OK;
 }

@@ -47,6 +47,10 @@ struct FluidArgs {
   int nblocks = 0;     // ensemble launches: number of work items
   int lim = 0;         // slope limiter: 0 van Leer (the paper's), 1 minmod, 2 superbee
   int fast = 0;        // freezing speed: 0 the bound, 1 the fast magnetosonic speed
+  // cells [rate_lo, rate_hi) per kernel axis enter the fused rate (the
+  // interior of a box with ghost layers; every cell by default)
+  int rate_lo[3] = {0, 0, 0};
+  int rate_hi[3] = {1 << 30, 1 << 30, 1 << 30};
 };
 
 struct MagArgs {

@@ -121,6 +121,8 @@ fluid_sweep_kernel(FluidArgs a) {
   pipe.init();
   float bc2[3] = {0.f, 0.f, 0.f}, bc3[3] = {0.f, 0.f, 0.f};  // b_c at t-1, t-2 (RATE only)
   float rmax = 0.f;
+  const bool rate_pencil = RATE && pa >= a.rate_lo[X::A] && pa < a.rate_hi[X::A] && pb >= a.rate_lo[X::O] &&
+                           pb < a.rate_hi[X::O];
 
   for (int c = 0; c < nchunk; c++) {
     const int p0 = s0 - 4 + CH * c;  // first position of this chunk
@@ -198,7 +200,9 @@ fluid_sweep_kernel(FluidArgs a) {
         o_m1[cell] = o[2];
         o_m2[cell] = o[3];
         o_en[cell] = o[4];
-        if (RATE) {
+        // the rate of interior cells only (ghost layers of non-periodic axes
+        // are left out; the whole box otherwise)
+        if (RATE && rate_pencil && po >= a.rate_lo[D] && po < a.rate_hi[D]) {
           float m[3], bg[3];
           m[D] = o[1]; m[X::T1] = o[2]; m[X::T2] = o[3];
           bg[D] = bc3[0]; bg[X::T1] = bc3[1]; bg[X::T2] = bc3[2];
