@@ -115,7 +115,7 @@ def set_pressure_floor(p_floor: float) -> None:
 
 
 LIMITERS = {"vanleer": 0, "minmod": 1, "superbee": 2}
-FREEZING = {"bound": 0, "fast": 1}
+FREEZING = {"bound": 0, "fast": 1, "pencil": 2}
 
 
 def set_scheme(limiter: str = "vanleer", freezing: str = "bound") -> None:

@@ -154,10 +154,14 @@ static long at(const int n[3], const int c[3]) {
  *     c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2)) / 2, s = a^2 + v_A^2,
  *     a^2 = gamma p / rho, v_A^2 = |b_c|^2 / rho, v_Ad^2 = b_d^2 / rho
  *     (the smallest freezing speed the relaxation scheme allows).
+ *   freezing 2 = the largest bound along the pencil, one value per pencil
+ *     and Runge-Kutta stage (the first stage's from U, the second's from
+ *     the half-step state), the classical global choice of relaxing TVD
+ *     schemes applied pencil by pencil.
  * The CFL rate keeps the bound in every variant. */
 static int g_limiter = 0, g_freezing = 0;
 int orc_set_scheme(int limiter, int freezing) {
-    if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 1) return 1;
+    if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 2) return 1;
     g_limiter = limiter;
     g_freezing = freezing;
     return 0;
@@ -220,6 +224,16 @@ double orc_freezing_speed(const double u[5], const double b[3], double gamma) {
  * and spacing h (Section II.B).  U[q][i] is updated in place; B[q][i] is the
  * frozen cell-centred field.  w is workspace of at least 25*n doubles.
  */
+/* freezing 2: every cell of the pencil takes the pencil's largest speed */
+static void pencil_max_speed(double *cs, int n) {
+    double m = 0.0;
+    int i;
+    if (g_freezing != 2) return;
+    for (i = 0; i < n; i++)
+        if (cs[i] > m) m = cs[i];
+    for (i = 0; i < n; i++) cs[i] = m;
+}
+
 static void fluid_pencil(int n, double h, double tau, double gamma,
                          double *U[5], double *B[3], double *w) {
     double *FR = w;            /* 5*n : right movers of the current stage */
@@ -230,16 +244,21 @@ static void fluid_pencil(int n, double h, double tau, double gamma,
     double u[5], b[3], F[5];
     int i, q;
 
-    /* stage 1: first-order upwind fluxes from U, half step tau/2 */
+    /* stage 1: first-order upwind fluxes from U, half step tau/2 (FR holds
+     * F until the freezing speeds are known) */
     for (i = 0; i < n; i++) {
         for (q = 0; q < 5; q++) u[q] = U[q][i];
         for (q = 0; q < 3; q++) b[q] = B[q][i];
         flux_and_speed(u, b, gamma, F, &cs[i]);
-        for (q = 0; q < 5; q++) {
-            FR[q * n + i] = 0.5 * (cs[i] * u[q] + F[q]);
-            FL[q * n + i] = 0.5 * (cs[i] * u[q] - F[q]);
-        }
+        for (q = 0; q < 5; q++) FR[q * n + i] = F[q];
     }
+    pencil_max_speed(cs, n);
+    for (i = 0; i < n; i++)
+        for (q = 0; q < 5; q++) {
+            const double Fq = FR[q * n + i];
+            FR[q * n + i] = 0.5 * (cs[i] * U[q][i] + Fq);
+            FL[q * n + i] = 0.5 * (cs[i] * U[q][i] - Fq);
+        }
     for (q = 0; q < 5; q++)
         for (i = 0; i < n; i++)
             fl[q * n + i] = FR[q * n + i] - FL[q * n + wrap(i + 1, n)];
@@ -253,11 +272,15 @@ static void fluid_pencil(int n, double h, double tau, double gamma,
         for (q = 0; q < 5; q++) u[q] = Uh[q * n + i];
         for (q = 0; q < 3; q++) b[q] = B[q][i];
         flux_and_speed(u, b, gamma, F, &cs[i]);
-        for (q = 0; q < 5; q++) {
-            FR[q * n + i] = 0.5 * (cs[i] * u[q] + F[q]);
-            FL[q * n + i] = 0.5 * (cs[i] * u[q] - F[q]);
-        }
+        for (q = 0; q < 5; q++) FR[q * n + i] = F[q];
     }
+    pencil_max_speed(cs, n);
+    for (i = 0; i < n; i++)
+        for (q = 0; q < 5; q++) {
+            const double Fq = FR[q * n + i];
+            FR[q * n + i] = 0.5 * (cs[i] * Uh[q * n + i] + Fq);
+            FL[q * n + i] = 0.5 * (cs[i] * Uh[q * n + i] - Fq);
+        }
     for (q = 0; q < 5; q++) {
         const double *R = FR + q * n, *L = FL + q * n;
         for (i = 0; i < n; i++) {

@@ -3,8 +3,9 @@ the minmod and superbee limiters against the defining properties of
 second-order TVD limiters (Sweby's region: minmod its lower edge, superbee
 its upper edge, van Leer inside), advection behaviour that follows from them
 (TVD, second order on a smooth profile, edge sharpness ordered superbee <
-van Leer < minmod), and the exact fast magnetosonic freezing speed against
-its dispersion relation and limiting cases."""
+van Leer < minmod), the exact fast magnetosonic freezing speed against
+its dispersion relation and limiting cases, and the per-pencil maximum
+freezing speed against what a constant speed along the pencil implies."""
 import math
 
 import numpy as np
@@ -13,7 +14,8 @@ import torch
 
 import oracle
 from paper_1004_1680_gb300 import initial_conditions as ic
-from tests.test_oracle_pins import G, _advect, order
+from tests import exact_riemann as er
+from tests.test_oracle_pins import G, _advect, _fast_error, _sod_exact, order, run_to
 
 
 @pytest.fixture
@@ -137,7 +139,50 @@ def test_fast_freezing_equals_bound_without_field(scheme):
     assert np.max(np.abs(res["fast"] - res["bound"])) < 1e-12
 
 
-@pytest.mark.parametrize("lim,fr", [("minmod", "bound"), ("superbee", "bound"), ("vanleer", "fast")])
+def test_pencil_freezing_restores_second_order_at_rest(scheme):
+    """A sound/fast wave at rest: the per-cell speed |v_d| + c_f has a kink
+    where v_d changes sign and the L1 order drops to about 1.5 (reading 4);
+    one speed per pencil removes the kink and the order is 2 again."""
+    scheme("vanleer", "pencil")
+    errs = [_fast_error((n, 1, 1), (1, 0, 0), (0.0, 1.0, 0.0), v0=0.0) for n in (64, 128, 256)]
+    assert order(errs[0][0], errs[1][0]) > 1.9 and order(errs[1][0], errs[2][0]) > 1.9
+    scheme("vanleer", "bound")
+    bound = _fast_error((256, 1, 1), (1, 0, 0), (0.0, 1.0, 0.0), v0=0.0)
+    assert errs[2][0] < bound[0]
+
+
+def test_pencil_freezing_equals_bound_when_uniform_along_pencils(scheme):
+    """Fields that vary only across the x pencils give every cell of a pencil
+    the same speed, so the x sweep is the same with either choice."""
+    st = ic.turbulence((16, 12, 10), seed=4, dtype=torch.float64, kmin=1.0, kmax=3.0).numpy().copy()
+    st[:] = st[:, :, :, :1]          # constant along x
+    st[5] = st[5, :, :, :1]          # b_x too (div b is not needed here)
+    res = {}
+    for fr in ("bound", "pencil"):
+        scheme("vanleer", fr)
+        s = st.copy()
+        oracle.fluid_sweep(s, 0, 0.3 / oracle.cfl_rate(st, G), G)
+        res[fr] = s
+    assert np.array_equal(res["bound"], res["pencil"])
+
+
+def test_pencil_freezing_shock_tube(scheme):
+    """The larger, constant speed is more diffusive but the scheme stays
+    monotone and converges to the exact Riemann solution."""
+    scheme("vanleer", "pencil")
+    errs = []
+    for n in (256, 512):
+        s = ic.sod((n, 1, 1)).numpy().copy()
+        run_to(s, 0.1)
+        x = (np.arange(n) + 0.5) / n
+        rho = s[0, 0, 0, :]
+        errs.append(np.mean(np.abs(rho - _sod_exact(x, 0.1)[0])))
+        assert rho.min() >= 0.125 - 1e-9 and rho.max() <= 1.0 + 1e-9
+    assert errs[1] < 0.015 and errs[1] < 0.75 * errs[0]
+
+
+@pytest.mark.parametrize("lim,fr", [("minmod", "bound"), ("superbee", "bound"), ("vanleer", "fast"),
+                                    ("vanleer", "pencil")])
 def test_variants_conserve_and_keep_div_b(scheme, lim, fr):
     scheme(lim, fr)
     st = ic.turbulence((16, 12, 20), seed=3, dtype=torch.float64, kmin=1.0, kmax=3.0).numpy().copy()
