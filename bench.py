@@ -66,7 +66,7 @@ def parse():
                    help="x sweep path (0 automatic; 3 = every axis through transposes, the paper's data flow)")
     p.add_argument("--seg", type=int, default=0,
                    help="pencil segment length for every axis (0: the library's choice)")
-    p.add_argument("--freezing", choices=["bound", "fast"], default="bound",
+    p.add_argument("--freezing", choices=["bound", "fast", "pencil"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
     p.add_argument("--bc", default="",
                    help="non-periodic axes, e.g. x=outflow,z=reflecting (4 ghost cells at each end "

@@ -134,9 +134,13 @@ int mhd_set_pressure_floor(mhd_t *m, double p_floor);
  * fluid and the magnetic sweeps; freezing 1 = |v_d| + the exact fast
  * magnetosonic speed along the sweep axis instead of the bound
  * |v_d| + sqrt((gamma p + |b|^2)/rho) (Section II.B leaves the freezing speed
- * open).  The CFL timestep keeps the bound.  One ablation at a time:
- * MHD_E_ARG for limiter and freezing both non-zero or out of range.
- * Ensembles always use the paper's scheme. */
+ * open); freezing 2 = one speed per pencil and Runge-Kutta stage, the largest
+ * bound along the pencil (for the second stage, over the first stage's
+ * half-step state), computed by a reduction pass before each fluid sweep.
+ * The CFL timestep keeps the bound.  One ablation at a time: MHD_E_ARG for
+ * limiter and freezing both non-zero or out of range; MHD_E_OOM if the
+ * per-pencil speeds cannot be allocated.  Ensembles always use the paper's
+ * scheme. */
 int mhd_set_scheme(mhd_t *m, int limiter, int freezing);
 
 /* Boundaries (an extension: the paper's runs are periodic).  mode 0 =

@@ -5,6 +5,7 @@
 // 8 fields; every sweep reads one copy and writes the other, field by field),
 // plus a few device scalars (sweep step, two CFL-rate accumulators, the
 // simulation time) and the FP64 diagnostics scratch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -70,6 +71,7 @@ struct mhd_s {
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
+  float* pencil_c = nullptr;  // freezing 2: per-pencil speeds of the sweep being run (2 x N / min n)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
@@ -340,6 +342,14 @@ int fluid(mhd_s* m, int d, bool rate) {
     a.rate_lo[k] = mhd::kGhost;
     a.rate_hi[k] = box->n[k] - mhd::kGhost;
   }
+  if (m->fast == 2) {  // per-pencil freezing speeds before the sweep
+    a.pencil_c = m->pencil_c;
+    if ((rc = traced(m, MHD_K_CONTROL, [&] {
+           CK(mhd::launch_pencil_speeds(ka, a, m->pencil_c, m->stream));
+           return MHD_OK;
+         })))
+      return rc;
+  }
   rc = traced(m, MHD_K_FLUID_X + d, [&] {
     CK(mhd::launch_fluid(ka, rate, a, m->stream));
     return MHD_OK;
@@ -543,6 +553,7 @@ void mhd_destroy(mhd_t* m) {
   if (!m) return;
   free_pipeline(m);
   drop_events(m);
+  cudaFree(m->pencil_c);
   cudaFree(m->arena);
   cudaFree(m->sc);
   cudaFree(m->diag_partial);
@@ -736,8 +747,15 @@ int mhd_set_xpath(mhd_t* m, int mode) {
 
 int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
   if (!check_box(m)) return MHD_E_ARG;
-  if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 1 || (limiter && freezing))
-    return fail(MHD_E_ARG, "limiter 0..2, freezing 0..1, one ablation at a time");
+  if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 2 || (limiter && freezing))
+    return fail(MHD_E_ARG, "limiter 0..2, freezing 0..2, one ablation at a time");
+  if (freezing == 2 && !m->pencil_c) {  // two speeds per pencil of the longest pencil family
+    const int nmin = std::min(m->n[0], std::min(m->n[1], m->n[2]));
+    if (cudaMalloc(&m->pencil_c, sizeof(float) * 2 * (size_t)(m->N / nmin)) != cudaSuccess) {
+      m->pencil_c = nullptr;
+      return fail(MHD_E_OOM, "per-pencil freezing speeds");
+    }
+  }
   m->lim = limiter;
   m->fast = freezing;
   return MHD_OK;

@@ -144,11 +144,14 @@ __device__ __forceinline__ V5 half_limited5(const V5& a, const V5& b) {
 // the relaxation freezing speed c = |v_d| + sqrt((gamma p + |b|^2)/rho), which
 // bounds the fastest local wave speed (Section II.B, relaxing TVD).
 // Returns the right and left movers FR = (cu + F)/2, FL = FR - F = (cu - F)/2.
-// FAST = true replaces the bound by |v_d| + the fast magnetosonic speed along
-// d, c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2))/2, s = a^2 + v_A^2 (an ablation:
-// the smallest freezing speed the relaxation allows).
-template <bool FAST = false>
-__device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, float gamma, V5& FR, V5& FL) {
+// FRZ selects the freezing speed: 0 the bound; 1 |v_d| + the fast
+// magnetosonic speed along d, c_f^2 = (s + sqrt(s^2 - 4 a^2 v_Ad^2))/2,
+// s = a^2 + v_A^2 (an ablation: the smallest freezing speed the relaxation
+// allows); 2 the given speed c_given (one value per pencil and stage: the
+// largest bound along the pencil, another ablation).
+template <int FRZ = 0>
+__device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, float gamma, V5& FR, V5& FL,
+                                           float c_given = 0.f) {
   const float md = u.p0.y;
   const float rinv = v_div(1.f, u.p0.x);
   const float vd = v_mul(md, rinv);
@@ -162,23 +165,38 @@ __device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, flo
   const float2 F01 = make_float2(md, v_fma(md, vd, v_fma(nb0, bd, pstar)));
   const float2 F23 = __ffma2_rn(u.p1, f2(vd), __fmul2_rn(f2(nb0), bt));
   const float F4 = v_fma(v_add(u.e, pstar), vd, v_mul(nb0, bv));
-  float cs;
-  if constexpr (FAST) {
+  float hc;
+  if constexpr (FRZ == 1) {
     const float a2 = v_mul(v_mul(gamma, p), rinv), va2 = v_mul(b2, rinv);
     const float vad2 = v_mul(v_mul(bd, bd), rinv);
     const float sum = v_add(a2, va2);
     const float disc = v_fma(v_mul(-4.f, a2), vad2, v_mul(sum, sum));
-    cs = v_sqrt(v_mul(0.5f, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))));
+    hc = v_mul(0.5f, v_add(v_abs(vd), v_sqrt(v_mul(0.5f, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))))));
+  } else if constexpr (FRZ == 2) {
+    hc = v_mul(0.5f, c_given);
   } else {
-    cs = v_sqrt(v_mul(v_fma(gamma, p, b2), rinv));
+    hc = v_mul(0.5f, v_add(v_abs(vd), v_sqrt(v_mul(v_fma(gamma, p, b2), rinv))));
   }
-  const float hc = v_mul(0.5f, v_add(v_abs(vd), cs));
   FR.p0 = __ffma2_rn(f2(hc), u.p0, __fmul2_rn(f2(0.5f), F01));
   FR.p1 = __ffma2_rn(f2(hc), u.p1, __fmul2_rn(f2(0.5f), F23));
   FR.e = v_fma(hc, u.e, v_mul(0.5f, F4));
   FL.p0 = sub2(FR.p0, F01);
   FL.p1 = sub2(FR.p1, F23);
   FL.e = v_sub(FR.e, F4);
+}
+
+// The bound |v_d| + sqrt((gamma p + |b|^2)/rho) of one cell in the sweep's
+// frame, with split_flux's arithmetic (the per-pencil freezing speed is its
+// maximum along the pencil).
+__device__ __forceinline__ float bound_speed(const V5& u, float bd, float2 bt, float gamma) {
+  const float md = u.p0.y;
+  const float rinv = v_div(1.f, u.p0.x);
+  const float vd = v_mul(md, rinv);
+  const float2 vt = __fmul2_rn(u.p1, f2(rinv));
+  const float b2 = v_fma(bd, bd, v_fma(bt.x, bt.x, v_mul(bt.y, bt.y)));
+  const float kin = v_mul(0.5f, v_fma(md, vd, v_fma(u.p1.x, vt.x, v_mul(u.p1.y, vt.y))));
+  const float p = v_mul(gamma - 1.f, v_fma(-0.5f, b2, v_sub(u.e, kin)));
+  return v_add(v_abs(vd), v_sqrt(v_mul(v_fma(gamma, p, b2), rinv)));
 }
 
 // Largest signal rate of one cell, max_d (|v_d| + c_f*) * n_d, in the global
@@ -212,7 +230,7 @@ __device__ __forceinline__ float floored_energy(const float u[5], const float b[
 __device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_rn(0.5f, __fadd_rn(lo, hi)); }
 
 // ---------------------------------------------------------------------------
-// Fluid marching pipeline (LIM: limiter, FAST: freezing speed; 0 / false is
+// Fluid marching pipeline (LIM: limiter, FRZ: freezing speed; 0 / 0 is
 // the paper's scheme).
 //
 // A thread walks its periodic pencil one position t at a time, receiving the
@@ -224,7 +242,7 @@ __device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_r
 //             Unew(t-3)    = U(t-3) - tau/h (F2(t-5/2) - F2(t-7/2))
 // so Unew at position t-3 is produced at step t (the 7-point stencil of
 // Section II.B).  Every intermediate value is held in registers.
-template <int LIM = 0, bool FAST = false>
+template <int LIM = 0, int FRZ = 0>
 struct FluidPipe {
   V5 U1, U2, U3;   // raw U at t-1, t-2, t-3
   float b1[3];     // frozen b at t-1
@@ -235,6 +253,7 @@ struct FluidPipe {
   V5 Lh2;          // stage-2 left mover at t-2
   V5 dL2;          // Lh(t-2) - Lh(t-3), carried from the previous step
   V5 F2m;          // stage-2 interface flux at t-7/2
+  float c1 = 0.f, c2 = 0.f;  // FRZ == 2: the pencil's freezing speeds of stage 1 and 2
 
   __device__ __forceinline__ void init() {
     U1 = U2 = U3 = FR1 = f1m = Rh2 = Rh3 = dR3 = Lh2 = dL2 = F2m = v5_zero();
@@ -247,11 +266,11 @@ struct FluidPipe {
                                        float c_full, float out[5]) {
     const V5 u = {make_float2(U[0], U[1]), make_float2(U[2], U[3]), U[4]};
     V5 FR, FL;
-    split_flux<FAST>(u, b[0], make_float2(b[1], b[2]), gamma, FR, FL);
+    split_flux<FRZ>(u, b[0], make_float2(b[1], b[2]), gamma, FR, FL, c1);
     const V5 f1 = v5_sub(FR1, FL);
     const V5 Uh = v5_fma(-c_half, v5_sub(f1, f1m), U1);
     V5 Rh, Lh;
-    split_flux<FAST>(Uh, b1[0], make_float2(b1[1], b1[2]), gamma, Rh, Lh);
+    split_flux<FRZ>(Uh, b1[0], make_float2(b1[1], b1[2]), gamma, Rh, Lh, c2);
     // the left-hand differences were the right-hand ones one step earlier
     const V5 dR2 = v5_sub(Rh2, Rh3), dL1 = v5_sub(Lh, Lh2);
     const V5 right = v5_add(Rh3, half_limited5<LIM>(dR3, dR2));

@@ -46,7 +46,8 @@ struct FluidArgs {
   EnsArgs ens;         // ensemble launches only
   int nblocks = 0;     // ensemble launches: number of work items
   int lim = 0;         // slope limiter: 0 van Leer (the paper's), 1 minmod, 2 superbee
-  int fast = 0;        // freezing speed: 0 the bound, 1 the fast magnetosonic speed
+  int fast = 0;        // freezing speed: 0 the bound, 1 the fast magnetosonic speed, 2 per pencil
+  const float* pencil_c = nullptr;  // fast == 2: per-pencil speeds, stage 1 then stage 2 (nA * nO each)
   // cells [rate_lo, rate_hi) per kernel axis enter the fused rate (the
   // interior of a box with ghost layers; every cell by default)
   int rate_lo[3] = {0, 0, 0};
@@ -172,16 +173,21 @@ cudaError_t launch_ens_control(const unsigned* rate_cur, unsigned* rate_next, fl
 cudaError_t launch_fluid(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
 cudaError_t launch_mag(int axis, const MagArgs& a, cudaStream_t s);
 // one instantiation per scheme variant, each in its own translation unit
-template <int LIM, bool FAST>
+template <int LIM, int FRZ>
 cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t s);
+// per-pencil freezing speeds of a fluid sweep along kernel axis `axis`
+// (sweep_pencil.cu): c[pencil] = largest bound along the pencil for U, then
+// c[nA nO + pencil] for the stage-1 half-step state built with it
+cudaError_t launch_pencil_speeds(int axis, const FluidArgs& a, float* c, cudaStream_t s);
 template <int LIM>
 cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s);
 template <int LIM>
 cudaError_t prepare_mag_t();
-extern template cudaError_t launch_fluid_t<0, false>(int, bool, const FluidArgs&, cudaStream_t);
-extern template cudaError_t launch_fluid_t<1, false>(int, bool, const FluidArgs&, cudaStream_t);
-extern template cudaError_t launch_fluid_t<2, false>(int, bool, const FluidArgs&, cudaStream_t);
-extern template cudaError_t launch_fluid_t<0, true>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<0, 0>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<1, 0>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<2, 0>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<0, 1>(int, bool, const FluidArgs&, cudaStream_t);
+extern template cudaError_t launch_fluid_t<0, 2>(int, bool, const FluidArgs&, cudaStream_t);
 extern template cudaError_t launch_mag_t<0>(int, const MagArgs&, cudaStream_t);
 extern template cudaError_t launch_mag_t<1>(int, const MagArgs&, cudaStream_t);
 extern template cudaError_t launch_mag_t<2>(int, const MagArgs&, cudaStream_t);

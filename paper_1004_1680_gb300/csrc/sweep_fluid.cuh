@@ -19,7 +19,7 @@
 // cell it writes (Section II.B: the next timestep) and folds the maximum into
 // *rate with one atomicMax per warp, saving a separate pass over the state.
 //
-// LIM selects the slope limiter and FAST the freezing speed (0 / false: the
+// LIM selects the slope limiter and FRZ the freezing speed (0 / 0: the
 // paper's scheme; the others are ablations).  This header holds the kernel
 // template; each scheme variant is instantiated in its own translation unit
 // (sweep_fluid.cu: the paper's scheme; sweep_variant_*.cu: the ablations).
@@ -71,7 +71,7 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
 // RATE variant spills a few words at that limit (it needs about 160), which
 // measured faster than 3 blocks per SM without spills (1.77 against 1.85 ms
 // at 512^3).
-template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, bool FAST>
+template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, int FRZ>
 __global__ void __launch_bounds__(32 * kFluidWarps, 4)
 fluid_sweep_kernel(FluidArgs a) {
   using X = Axes<D>;
@@ -117,8 +117,13 @@ fluid_sweep_kernel(FluidArgs a) {
   // warm-up cell so that x chunks start 16-byte aligned)
   const int nchunk = (G.seg + 7 + CH - 1) / CH;
 
-  FluidPipe<LIM, FAST> pipe;
+  FluidPipe<LIM, FRZ> pipe;
   pipe.init();
+  if constexpr (FRZ == 2) {  // the pencil's freezing speeds (two reduction passes before the sweep)
+    const int pc = ib * nA + ia;
+    pipe.c1 = __ldg(a.pencil_c + pc);
+    pipe.c2 = __ldg(a.pencil_c + (long long)nA * nO + pc);
+  }
   float bc2[3] = {0.f, 0.f, 0.f}, bc3[3] = {0.f, 0.f, 0.f};  // b_c at t-1, t-2 (RATE only)
   float rmax = 0.f;
   const bool rate_pencil = RATE && pa >= a.rate_lo[X::A] && pa < a.rate_hi[X::A] && pb >= a.rate_lo[X::O] &&
@@ -221,9 +226,9 @@ fluid_sweep_kernel(FluidArgs a) {
   }
 }
 
-// Launch of one fluid sweep with scheme (LIM, FAST): kernel axis, fused CFL
+// Launch of one fluid sweep with scheme (LIM, FRZ): kernel axis, fused CFL
 // rate, short axis and pressure floor select the instantiation.
-template <int LIM, bool FAST>
+template <int LIM, int FRZ>
 cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t s) {
   const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
   dim3 block(32, kFluidWarps);
@@ -237,11 +242,11 @@ cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t
 #define FLUID_CASE(DD, RR)                                                                            \
   if (axis == DD && rate == RR) {                                                                     \
     if (floor) {                                                                                      \
-      if (small) fluid_sweep_kernel<DD, RR, true, true, LIM, FAST><<<grid, block, 0, s>>>(a);         \
-      else fluid_sweep_kernel<DD, RR, false, true, LIM, FAST><<<grid, block, 0, s>>>(a);              \
+      if (small) fluid_sweep_kernel<DD, RR, true, true, LIM, FRZ><<<grid, block, 0, s>>>(a);         \
+      else fluid_sweep_kernel<DD, RR, false, true, LIM, FRZ><<<grid, block, 0, s>>>(a);              \
     } else {                                                                                          \
-      if (small) fluid_sweep_kernel<DD, RR, true, false, LIM, FAST><<<grid, block, 0, s>>>(a);        \
-      else fluid_sweep_kernel<DD, RR, false, false, LIM, FAST><<<grid, block, 0, s>>>(a);             \
+      if (small) fluid_sweep_kernel<DD, RR, true, false, LIM, FRZ><<<grid, block, 0, s>>>(a);        \
+      else fluid_sweep_kernel<DD, RR, false, false, LIM, FRZ><<<grid, block, 0, s>>>(a);             \
     }                                                                                                 \
   }
   FLUID_CASE(0, false) FLUID_CASE(0, true) FLUID_CASE(1, false) FLUID_CASE(1, true)

@@ -4,6 +4,6 @@
 
 namespace mhd {
 
-template cudaError_t launch_fluid_t<0, true>(int, bool, const FluidArgs&, cudaStream_t);
+template cudaError_t launch_fluid_t<0, 1>(int, bool, const FluidArgs&, cudaStream_t);
 
 }  // namespace mhd

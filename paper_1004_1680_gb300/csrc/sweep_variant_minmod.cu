@@ -5,7 +5,7 @@
 
 namespace mhd {
 
-template cudaError_t launch_fluid_t<1, false>(int, bool, const FluidArgs&, cudaStream_t);
+template cudaError_t launch_fluid_t<1, 0>(int, bool, const FluidArgs&, cudaStream_t);
 template cudaError_t launch_mag_t<1>(int, const MagArgs&, cudaStream_t);
 template cudaError_t prepare_mag_t<1>();
 

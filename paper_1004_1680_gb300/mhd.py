@@ -230,7 +230,7 @@ class Box:
         _check(self.lib.mhd_set_pressure_floor(self.h, float(p_floor)))
 
     LIMITERS = {"vanleer": 0, "minmod": 1, "superbee": 2}
-    FREEZING = {"bound": 0, "fast": 1}
+    FREEZING = {"bound": 0, "fast": 1, "pencil": 2}
 
     def set_scheme(self, limiter: str = "vanleer", freezing: str = "bound"):
         """Scheme variant (ablation) for the following sweeps; the default is

@@ -1,5 +1,6 @@
 """Scheme variants (ablations: minmod and superbee limiters, the exact fast
-freezing speed) on the GPU against the FP64 oracle running the same
+freezing speed, the per-pencil freezing speed) on the GPU against the FP64
+oracle running the same
 variant, with the tolerances of the default scheme's parity tests; the
 default scheme is unaffected by switching back and forth."""
 import numpy as np
@@ -11,7 +12,7 @@ from paper_1004_1680_gb300 import initial_conditions as ic
 from tests.parity_util import G, field_scales, from_gpu, l1_rel, rel_err, to_gpu
 
 pytestmark = pytest.mark.gpu
-VARIANTS = [("minmod", "bound"), ("superbee", "bound"), ("vanleer", "fast")]
+VARIANTS = [("minmod", "bound"), ("superbee", "bound"), ("vanleer", "fast"), ("vanleer", "pencil")]
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +42,7 @@ def box_of(mhd, st, lim, fr, xpath=0):
 @pytest.mark.parametrize("axis", [0, 1, 2])
 @pytest.mark.parametrize("kind", [0, 1])
 def test_variant_single_sweeps(mhd, variant_oracle, lim, fr, axis, kind):
-    if kind == 1 and fr == "fast":
+    if kind == 1 and fr in ("fast", "pencil"):
         pytest.skip("the freezing speed does not enter the magnetic sweep")
     st = ic.turbulence((48, 40, 36), seed=21, dtype=torch.float64, kmin=1.0, kmax=4.0)
     s = ic.as_oracle_input(st)
