@@ -427,8 +427,9 @@ def run_ours(args, rank, world, local):
     box.run(args.warmup, args.cfl)
     box.cfl_dt(args.cfl)               # raises if the state went invalid
     # 12 sweeps, step control, up to 6 transposes (x path 3); with ghost
-    # layers a fill per non-periodic axis before every sweep
-    launches_per_step = 19 + 12 * len(bcs)
+    # layers a fill per non-periodic axis before every sweep; with the
+    # per-pencil freezing speed a reduction pass before every fluid sweep
+    launches_per_step = 19 + 12 * len(bcs) + (6 if args.freezing == "pencil" else 0)  # + speed passes
     box.profile(args.steps * launches_per_step + 16)
 
     uuid = None
