@@ -375,6 +375,27 @@ int mhd_correct(int nx, int ny, int nz, float *const s[8], const float *const d[
 int mhd_adam(float *p, const float *g, float *m, float *v, int count, float lr, float beta1, float beta2,
              float eps, int step, void *stream);
 
+/* The whole correction network: 4 periodic 3x3x3 layers 8 -> 32 -> 32 ->
+ * 32 -> 8 with ReLU after the first three (mhd_conv3d per layer).  x: input
+ * [cell][8] BF16 (normalised); img[l]: forward weight images of layer l
+ * (mhd_conv_pack, transpose 0) of img_bytes[l] bytes; bias[l]: [cout_l] FP32
+ * or NULL; acts[0..2]: caller-owned BF16 [cell][32] buffers that receive the
+ * three hidden activations (the backward reads them); y: FP32 [cell][8].
+ * Same box requirements as mhd_conv3d. */
+int mhd_cnn_forward(int nx, int ny, int nz, const void *x, const void *const img[4], const size_t img_bytes[4],
+                    const float *const bias[4], void *const acts[3], float *y, void *stream);
+
+/* Backward of mhd_cnn_forward for the output gradient gy ([cell][8] BF16):
+ * layer by layer from the last, the weight and bias gradient
+ * (mhd_conv3d_wgrad, accumulated into gw[l] = [cout_l][cin_l][27] and
+ * gb[l] = [cout_l] FP32: the caller zeroes them) and, below the top layer,
+ * the input gradient through the ReLU mask of the saved activation
+ * (mhd_conv3d with the transposed images imgT[l], flip = 1) into two
+ * caller-owned BF16 [cell][32] scratch buffers. */
+int mhd_cnn_backward(int nx, int ny, int nz, const void *x, const void *const acts[3], const void *gy,
+                     const void *const imgT[4], const size_t imgT_bytes[4], float *const gw[4], float *const gb[4],
+                     void *const scratch[2], void *stream);
+
 /* Read and clear the flag raised by a convolution whose bounded tensor-core
  * wait gave up (MHD_E_TIMEOUT if set).  Synchronises the device. */
 int mhd_conv_error(int *flag);

@@ -117,6 +117,49 @@ int mhd_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void* x, c
   return MHD_OK;
 }
 
+namespace {
+constexpr int kLayerIn[4] = {8, 32, 32, 32}, kLayerOut[4] = {32, 32, 32, 8};
+}  // namespace
+
+int mhd_cnn_forward(int nx, int ny, int nz, const void* x, const void* const img[4], const size_t img_bytes[4],
+                    const float* const bias[4], void* const acts[3], float* y, void* stream) {
+  if (!x || !img || !img_bytes || !bias || !acts || !y)
+    return mhd::set_error(MHD_E_ARG, "mhd_cnn_forward", "null argument");
+  for (int l = 0; l < 4; l++)
+    if (!img[l] || (l < 3 && !acts[l])) return mhd::set_error(MHD_E_ARG, "mhd_cnn_forward", "null image or buffer");
+  const void* h = x;
+  for (int l = 0; l < 4; l++) {
+    const bool last = l == 3;
+    const int rc = mhd_conv3d(nx, ny, nz, kLayerIn[l], kLayerOut[l], h, img[l], img_bytes[l], bias[l], last ? 0 : 1,
+                              0, nullptr, last ? nullptr : acts[l], last ? y : nullptr, stream);
+    if (rc) return rc;
+    if (!last) h = acts[l];
+  }
+  return MHD_OK;
+}
+
+int mhd_cnn_backward(int nx, int ny, int nz, const void* x, const void* const acts[3], const void* gy,
+                     const void* const imgT[4], const size_t imgT_bytes[4], float* const gw[4], float* const gb[4],
+                     void* const scratch[2], void* stream) {
+  if (!x || !acts || !gy || !imgT || !imgT_bytes || !gw || !gb || !scratch || !scratch[0] || !scratch[1])
+    return mhd::set_error(MHD_E_ARG, "mhd_cnn_backward", "null argument");
+  for (int l = 0; l < 4; l++)
+    if (!imgT[l] || !gw[l] || (l < 3 && !acts[l])) return mhd::set_error(MHD_E_ARG, "mhd_cnn_backward", "null buffer");
+  const void* g = gy;  // gradient of the loss w.r.t. layer l's output
+  for (int l = 3; l >= 0; l--) {
+    const void* in = l ? acts[l - 1] : x;  // layer l's input
+    int rc = mhd_conv3d_wgrad(nx, ny, nz, kLayerIn[l], kLayerOut[l], in, g, gw[l], gb[l], stream);
+    if (rc) return rc;
+    if (l == 0) break;
+    void* gin = scratch[l & 1];  // gradient w.r.t. layer l's input, through its ReLU mask
+    rc = mhd_conv3d(nx, ny, nz, kLayerOut[l], kLayerIn[l], g, imgT[l], imgT_bytes[l], nullptr, 0, 1, acts[l - 1],
+                    gin, nullptr, stream);
+    if (rc) return rc;
+    g = gin;
+  }
+  return MHD_OK;
+}
+
 int mhd_conv_error(int* flag) {
   if (!flag) return mhd::set_error(MHD_E_ARG, "mhd_conv_error", "null argument");
   int* err = nullptr;

@@ -70,6 +70,9 @@ SIGNATURES = {
     "mhd_conv_pack": (_I, [_P, _I, _I, _I, _P, _P]),
     "mhd_conv3d": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.c_size_t, _P, _I, _I, _P, _P, _P, _P]),
     "mhd_conv3d_wgrad": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "mhd_cnn_forward": (_I, [_I, _I, _I, _P, _PP, ctypes.POINTER(ctypes.c_size_t), _PP, _PP, _P, _P]),
+    "mhd_cnn_backward": (_I, [_I, _I, _I, _P, _PP, _P, _PP, ctypes.POINTER(ctypes.c_size_t), _PP, _PP, _PP,
+                              _P]),
     "mhd_conv_error": (_I, [ctypes.POINTER(ctypes.c_int)]),
     "mhd_restrict": (_I, [_I, _I, _I, _I, _PP, _PP, _P]),
     "mhd_cnn_normalize": (_I, [_I, _I, _I, _PP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -404,6 +407,32 @@ def conv3d_wgrad(x: torch.Tensor, gy: torch.Tensor, n, cin: int, cout: int, gw: 
     """Accumulate the weight (and bias) gradient into gw (cout*cin*27) and gb."""
     lib = load()
     _check(lib.mhd_conv3d_wgrad(n[0], n[1], n[2], cin, cout, _ptr(x), _ptr(gy), _ptr(gw), _ptr(gb),
+                                _stream(stream)))
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[_ptr(t) for t in ts])
+
+
+def _bytes_array(ts):
+    return (ctypes.c_size_t * len(ts))(*[t.numel() * t.element_size() for t in ts])
+
+
+def cnn_forward(x: torch.Tensor, imgs, biases, acts, y: torch.Tensor, n, stream=None):
+    """The 4-layer correction network in one call (mhd_cnn_forward): x (cells, 8)
+    BF16 -> y (cells, 8) FP32; acts: three (cells, 32) BF16 buffers that
+    receive the hidden activations."""
+    lib = load()
+    _check(lib.mhd_cnn_forward(n[0], n[1], n[2], _ptr(x), _ptr_array(imgs), _bytes_array(imgs),
+                               _ptr_array(biases), _ptr_array(acts), _ptr(y), _stream(stream)))
+
+
+def cnn_backward(x: torch.Tensor, acts, gy: torch.Tensor, imgsT, gws, gbs, scratch, n, stream=None):
+    """Backward of cnn_forward for gy (cells, 8) BF16 (mhd_cnn_backward):
+    accumulates the weight and bias gradients into gws / gbs."""
+    lib = load()
+    _check(lib.mhd_cnn_backward(n[0], n[1], n[2], _ptr(x), _ptr_array(acts), _ptr(gy), _ptr_array(imgsT),
+                                _bytes_array(imgsT), _ptr_array(gws), _ptr_array(gbs), _ptr_array(scratch),
                                 _stream(stream)))
 
 

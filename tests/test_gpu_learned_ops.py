@@ -124,3 +124,37 @@ def test_adam_against_oracle(mhd):
         mhd.adam(p, g, m, v, 1e-2, step)
         cnn.adam(pr, g.cpu().double(), mr, vr, 1e-2, step)
     assert torch.allclose(p.cpu().double(), pr, rtol=1e-5, atol=1e-6)
+
+
+def test_network_entry_points_match_the_layer_calls():
+    """mhd_cnn_forward / mhd_cnn_backward give the layer-by-layer results of
+    the same kernels (forward bitwise; the gradients, whose block partials
+    are added with atomics in any order, to FP32 rounding)."""
+    from paper_1004_1680_gb300 import learned, mhd
+    n = (16, 16, 4)
+    cells = n[0] * n[1] * n[2]
+    torch.manual_seed(5)
+    net = learned.CorrectionNet(seed=3)
+    for b in net.b:
+        b.normal_(0.0, 0.1)
+    x = (torch.randn(cells, 8, device="cuda") * 0.5).to(torch.bfloat16)
+    y_ref, acts_ref = net.forward(x, n)
+    acts = [torch.empty(cells, 32, dtype=torch.bfloat16, device="cuda") for _ in range(3)]
+    y = torch.empty(cells, 8, device="cuda")
+    mhd.cnn_forward(x, net.img, net.b, acts, y, n)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_ref)
+    for a, r in zip(acts, acts_ref[1:]):
+        assert torch.equal(a, r)
+    gy = torch.randn(cells, 8, device="cuda").to(torch.bfloat16)
+    net.backward(gy, acts_ref, n)
+    gws = [torch.zeros_like(w) for w in net.W]
+    gbs = [torch.zeros_like(b) for b in net.b]
+    scratch = [torch.empty(cells, 32, dtype=torch.bfloat16, device="cuda") for _ in range(2)]
+    mhd.cnn_backward(x, acts, gy, net.imgT, gws, gbs, scratch, n)
+    torch.cuda.synchronize()
+    L = len(net.W)
+    for l in range(L):
+        for got, want in ((gws[l], net.grads[l]), (gbs[l], net.grads[L + l])):
+            scale = float(want.abs().max()) + 1e-30
+            assert float((got - want).abs().max()) <= 1e-5 * scale

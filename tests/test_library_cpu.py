@@ -95,3 +95,12 @@ def test_set_scheme_rejects_null_handle(lib):
 def test_boundary_calls_reject_null_handle(lib):
     assert lib.mhd_set_boundary(None, 0, 1) == M.MHD_E_ARG
     assert lib.mhd_fill_ghosts(None) == M.MHD_E_ARG
+
+
+def test_network_calls_reject_null_arguments(lib):
+    nul4 = (ctypes.c_void_p * 4)()
+    sz4 = (ctypes.c_size_t * 4)()
+    nul3 = (ctypes.c_void_p * 3)()
+    nul2 = (ctypes.c_void_p * 2)()
+    assert lib.mhd_cnn_forward(8, 16, 2, None, nul4, sz4, nul4, nul3, None, None) == M.MHD_E_ARG
+    assert lib.mhd_cnn_backward(8, 16, 2, None, nul3, None, nul4, sz4, nul4, nul4, nul2, None) == M.MHD_E_ARG
