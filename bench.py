@@ -383,8 +383,9 @@ def run_reference(args, rank, world):
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": f"turbulence {n}^3 sample of the {args.size}^3 recipe "
-                                  f"(FP64 CPU oracle)", "n": n, "seed": args.seed, "cfl": args.cfl},
+           "config": {"workload": f"decaying MHD turbulence {args.size}^3, periodic", "n": args.size,
+                      "seed": args.seed, "cfl": args.cfl,
+                      "sample": f"each step timed on a {n}^3 box of the same recipe (FP64 CPU oracle)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                             "sample": f"{n}^3 turbulence, {args.steps} timed full steps"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -550,7 +551,7 @@ def run_ours(args, rank, world, local):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
                "config": {"workload": f"decaying MHD turbulence {n}^3, "
-                                      f"{'periodic' if not bcs else 'non-periodic ' + ','.join(sorted(bcs))}, FP32 state",
+                                      f"{'periodic' if not bcs else 'non-periodic ' + ','.join(sorted(bcs))}",
                           "n": n, "seed": args.seed, "cfl": args.cfl,
                           "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
