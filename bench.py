@@ -10,7 +10,8 @@ between steps.
 Prints one JSON line (rank 0).  `value` is device time (CUDA events on the
 library's stream) with the state resident in HBM; `e2e` is the same metric
 through the C ABI with host buffers, the host->device copy of the state and
-the device->host copy of the result inside every timed step; `roofline` is
+the device->host copy of the result inside every timed step (with
+`e2e.link_bound`, the rate the measured host link allows); `roofline` is
 the dominant kernel's algorithmic bytes over its measured launch time;
 `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
 
@@ -356,6 +357,28 @@ def max_over_ranks(values, world, device="cuda"):
     return [float(v) for v in t.tolist()]
 
 
+def host_link_rate(host, out_host, reps=2):
+    """GB/s each way of pinned host <-> HBM copies running in both directions
+    at once (the regime of the pipelined end-to-end leg): each of the 8 fields
+    in, and one field's worth out, per field, on two streams."""
+    d_in = torch.empty_like(host[0], device="cuda")
+    d_out = torch.zeros_like(d_in)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    best = math.inf
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in range(host.shape[0]):
+            with torch.cuda.stream(sa):
+                d_in.copy_(host[q], non_blocking=True)
+            with torch.cuda.stream(sb):
+                out_host[q].copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    del d_in, d_out
+    return host.numel() * host.element_size() / best / 1e9
+
+
 def whole_job_rate(units_per_rank, world, secs):
     """Units processed by all ranks together (replicas: each rank the same
     amount) over the slowest rank's time."""
@@ -506,6 +529,7 @@ def run_ours(args, rank, world, local):
             box.get_state(out_host)      # D2H of the 8 fields (synchronises)
         torch.cuda.synchronize()
         ss = time.perf_counter() - w1
+        link = host_link_rate(host, out_host)
         es, ss = max_over_ranks([es, ss], world)
         e2e = {"value": whole_job_rate(N * args.e2e_steps, world, es), "unit": UNIT,
                "h2d_bytes_per_step": 8 * 4 * N, "d2h_bytes_per_step": 8 * 4 * N,
@@ -514,6 +538,12 @@ def run_ours(args, rank, world, local):
                "sync": {"value": whole_job_rate(N * args.e2e_steps, world, ss),
                         "ms_per_step": 1e3 * ss / args.e2e_steps,
                         "api": "mhd_set_state + mhd_run(1) + mhd_get_state per step"}}
+        # the host link bounds the pipelined API: 32 bytes per cell each way
+        bound = world * link * 1e9 / 32.0
+        e2e["link_bound"] = {"gbs_each_way": link, "value": bound, "unit": UNIT,
+                             "frac": e2e["value"] / bound,
+                             "how": "the same 8 fields copied host->device and "
+                                    "device->host at once on two streams (best of 2)"}
 
     ens_out = None
     if args.ensemble_steps > 0:
