@@ -22,6 +22,12 @@ __host__ __device__ inline int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Hint that the line holding *p will be read soon: it is fetched into L2
+// without occupying a register (p must be a valid address).
+__device__ __forceinline__ void prefetch_l2(const float* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Periodic image of a position within one period of [0, n) (SMALL = false,
 // valid for n >= 16) or anywhere (SMALL = true).  Branch-free, so the loads
 // of a whole chunk can be issued before the first one is used.

@@ -150,7 +150,8 @@ fluid_sweep_kernel(FluidArgs a) {
       bd_next = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD));  // high face of the last cell
       __syncwarp();
     } else {
-      // one coalesced row per plane
+      // one coalesced row per plane (an L2 prefetch of the next chunk's 10
+      // rows on top measured slower: 1.50 -> 1.60 ms along y at 512^3)
       float bdn[CH + 1], t1n[CH], t2n[CH];
 #pragma unroll
       for (int j = 0; j < CH; j++) {

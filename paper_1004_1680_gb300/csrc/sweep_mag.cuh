@@ -239,6 +239,10 @@ mag_sweep_kernel(MagArgs a) {
 //    Issuing them early measured 1.39 -> 1.15 ms per launch along y at
 //    512^3 (from mag_sweep_kernel), but 1.65 ms along z, where issuing them
 //    late gives 1.33 (mag_sweep_kernel: 1.41).
+//  * Along z an L2 prefetch of the next chunk's 5 lines per thread goes out
+//    before the arithmetic instead (no registers held): 1.34 -> 1.24 ms at
+//    512^3; two or three chunks ahead measured the same or slower.  Along
+//    y, a prefetch two chunks ahead of the early loads costs 1.15 -> 1.30.
 template <int D, bool SMALL, int LIM>
 __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_pipe_kernel(MagArgs a) {
@@ -388,6 +392,17 @@ mag_sweep_pipe_kernel(MagArgs a) {
     const bool more = c + 1 < nchunk;
     float n0[CH], n1[CH], n2[CH], n3[CH], n4[CH];
     if (kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
+    if (!kEarly && more) {  // the next chunk's lines into L2 during the arithmetic
+#pragma unroll
+      for (int j = 0; j < CH; j++) {
+        const int off = wrap_near<SMALL>(p0 + CH + j, nD) * sD;
+        prefetch_l2(p0r + off);
+        prefetch_l2(p1m + off);
+        prefetch_l2(p2 + off);
+        prefetch_l2(p3 + off);
+        prefetch_l2(p4 + off);
+      }
+    }
     float bDold[CH];  // raw b_D at the face each position's constraint updates
 #pragma unroll
     for (int j = 0; j < CH; j++) {
