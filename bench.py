@@ -361,6 +361,8 @@ def host_link_rate(host, out_host, reps=2):
     """GB/s each way of pinned host <-> HBM copies running in both directions
     at once (the regime of the pipelined end-to-end leg): each of the 8 fields
     in, and one field's worth out, per field, on two streams."""
+    import torch
+
     d_in = torch.empty_like(host[0], device="cuda")
     d_out = torch.zeros_like(d_in)
     sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
