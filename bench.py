@@ -43,6 +43,7 @@ UNIT = "cell-updates/s"
 #   magnetic sweep: reads rho, m_d, b (3) = 20 B, writes b (3) = 12 B
 ALGO_BYTES = {"fluid": 52, "mag": 32}
 TRANSPOSE_BYTES = 64   # x<->y exchange: read and write 8 fields
+DIAG_BYTES = 32        # FP64 diagnostics: read 8 fields
 STEP_BYTES = 384  # 6 sweeps x (read + write of 8 FP32 fields): the full-step model
 P_FLOOR_ENSEMBLE = 1e-3
 
@@ -57,6 +58,8 @@ def parse():
     p.add_argument("--cfl", type=float, default=0.7)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--diag-reps", type=int, default=10,
+                   help="FP64 diagnostics passes timed on the final state (0: skip)")
     p.add_argument("--cpu-sample", type=int, default=128, help="edge of the oracle's sample box")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100,
@@ -501,6 +504,22 @@ def run_ours(args, rank, world, local):
                   for k, (c, ms) in prof.items()}
     launches = sum(c for c, _ in prof.values())
 
+    # FP64 diagnostics (compensated sums, max |div b|, min p) of the state:
+    # one pass reading the 8 fields (the high faces of a cell are its
+    # neighbours' low faces: cache hits), per-launch device time
+    diag = None
+    if args.diag_reps > 0:
+        box.diagnostics()
+        box.profile(args.diag_reps + 4)
+        for _ in range(args.diag_reps):
+            box.diagnostics()
+        dc, dms = box.profile_read()["control"]
+        box.profile(0)
+        d_ms = dms / dc
+        d_gbs = DIAG_BYTES * N / (d_ms / 1e3) / 1e9
+        diag = {"ms": d_ms, "calls": dc, "algorithmic_bytes_per_cell": DIAG_BYTES, "GB/s": d_gbs,
+                "frac": d_gbs / peak, "bound": "hbm"}
+
     # end-to-end through the C ABI with host buffers: every step copies its
     # input state in from pinned host memory and its result out to pinned
     # host memory.  `value`: the pipelined host API (mhd_submit/mhd_drain:
@@ -605,6 +624,7 @@ def run_ours(args, rank, world, local):
                "gpu_launches": launches,
                "clocks": clk,
                "e2e": e2e,
+               "diagnostics": diag,
                "cpu_baseline": cpu,
                "ensemble": ens_out,
                "learned_correction": learned_out}

@@ -773,7 +773,11 @@ int mhd_diagnostics(mhd_t* m, double out[10]) {
   if (int rc = join_pipeline(m)) return rc;
   const float* cf[8];
   field_ptrs(m, cf);
-  CK(mhd::launch_diagnostics(cf, m->box, m->gamma, m->diag_partial, m->sc->diag, m->stream));
+  if (int rc = traced(m, MHD_K_CONTROL, [&] {
+        CK(mhd::launch_diagnostics(cf, m->box, m->gamma, m->diag_partial, m->sc->diag, m->stream));
+        return MHD_OK;
+      }))
+    return rc;
   CK(cudaMemcpyAsync(out, m->sc->diag, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
   return MHD_OK;

@@ -244,6 +244,63 @@ def test_diagnostics_fp64(mhd):
     assert np.array_equal(box.diagnostics(), d_gpu)      # fixed-order reduction
 
 
+def _hard_diag_state(shape, seed):
+    """An FP32 state built to stress the diagnostics (as FP64 holding FP32
+    values): momentum spanning 20 decades with both signs, face fields with
+    subnormal values and signed zeros, and pressures within ~1e-7 of 1
+    everywhere (FP32 estimates cannot separate them, so the exact FP64
+    extremum has to be found among many candidates), plus one isolated low
+    pressure and one isolated div b spike."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    s = np.empty((8, nz, ny, nx))
+    s[0] = 1.0 + 0.5 * rng.random((nz, ny, nx))
+    s[1:4] = rng.standard_normal((3, nz, ny, nx)) * 10.0 ** rng.integers(-20, 1, (3, nz, ny, nx))
+    s[5:8] = 0.1 * rng.standard_normal((3, nz, ny, nx))
+    s[5, 0, 0, :7] = np.array([1e-40, -1e-41, 0.0, -0.0, 1e-45, -1e-45, 3e-39])
+    s[7, 1, 2, 3] += 0.5          # div b spike in two cells (its faces)
+    s = s.astype(np.float32).astype(np.float64)
+    # total energy for p = 1 (+ 1e-9 noise, lost to FP32 rounding)
+    kin = 0.5 * np.sum(s[1:4] ** 2, axis=0) / s[0]
+    bc = [0.5 * (s[5 + d] + np.roll(s[5 + d], -1, axis=2 - d)) for d in range(3)]
+    mag = 0.5 * sum(b * b for b in bc)
+    p = 1.0 + 1e-9 * rng.random((nz, ny, nx))
+    p[nz // 2, 3, 5] = 0.25
+    s[4] = p / (G - 1.0) + kin + mag
+    return s.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", [(40, 24, 36), (36, 7, 5)])
+def test_diagnostics_on_hard_inputs(mhd, shape):
+    """Sums within 1e-13 of sum|f| of the exactly rounded sums; max |div b| and
+    min p equal to the FP64 evaluation of every cell (the kernel evaluates
+    FP64 only where an FP32 bound cannot rule a cell out)."""
+    s = _hard_diag_state(shape, seed=11)
+    nx, ny, nz = shape
+    box = mhd.Box(nx, ny, nz, gamma=G)
+    box.set_state(torch.from_numpy(s).to(torch.float32).cuda())
+    d = box.diagnostics()
+    o = oracle.diagnostics(s, G)
+    for q in range(8):
+        assert abs(d[q] - o[q]) <= 1e-13 * np.sum(np.abs(s[q])) + 1e-300, q
+    assert d[8] == pytest.approx(o[8], rel=1e-13)
+    assert d[9] == pytest.approx(o[9], rel=1e-13)
+    assert d[9] == pytest.approx(0.25, rel=1e-5)
+    # the near-tied pressures: remove the isolated minimum, the exact minimum
+    # of the rest must still be found
+    s2 = s.copy()
+    s2[4, nz // 2, 3, 5] = s2[4, nz // 2, 3, 4]
+    box.set_state(torch.from_numpy(s2).to(torch.float32).cuda())
+    d2 = box.diagnostics()
+    o2 = oracle.diagnostics(s2, G)
+    assert d2[9] == pytest.approx(o2[9], rel=1e-12)
+    # a NaN propagates into its field's sum, as in an FP64 sum
+    s2[0, 0, 0, 0] = np.nan
+    box.set_state(torch.from_numpy(s2).to(torch.float32).cuda())
+    assert np.isnan(box.diagnostics()[0])
+    box.close()
+
+
 def test_conservation_and_div_b_on_gpu(mhd):
     st = ic.turbulence((64, 64, 64), seed=2, dtype=torch.float64, kmin=1.0, kmax=4.0)
     box = make_box(mhd, st)
