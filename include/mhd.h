@@ -190,9 +190,11 @@ int mhd_set_segments(mhd_t *m, int seg_x, int seg_y, int seg_z);
  * results differ by FP32 rounding of sums taken in another order. */
 int mhd_set_xpath(mhd_t *m, int mode);
 
-/* FP64 diagnostics of the current state, computed on the device with
- * compensated (Neumaier) sums in a fixed order, so repeated calls on the same
- * state give bitwise identical results:
+/* FP64 diagnostics of the current state, computed on the device in one pass
+ * and a fixed order, so repeated calls on the same state give bitwise
+ * identical results.  The sums are compensated (FP32 words per lane, then
+ * FP64 with Neumaier merges) to within a few 2^-48 of the absolute sum; the
+ * extrema are the exact FP64 values of the formulas below:
  *   out[0..7] = sums over all cells of rho, m_x, m_y, m_z, e, b_x, b_y, b_z;
  *   out[8]    = max over cells of |div b| * h_min, div b the cell's discrete
  *               flux balance sum_d (b_d(high) - b_d(low)) / h_d,

@@ -18,30 +18,35 @@
 
 namespace mhd {
 
+// I: the index type of the element and plane counters (unsigned 32-bit when
+// they fit, which avoids emulated 64-bit division per element).
+template <typename I>
 __global__ void __launch_bounds__(256) ghost_fill_kernel(GhostArgs a) {
   const int k = a.axis;
-  const long long plane = (long long)a.n1 * a.n2;
-  const long long total = 2LL * kGhost * plane;
+  const I n1 = (I)a.n1;
+  const I plane = (I)a.n1 * (I)a.n2;
+  const I total = (I)(2 * kGhost) * plane;
   const int nk = a.nk, wlo = kGhost, whi = nk - kGhost;
   float* const mn = k == 0 ? a.f[1] : (k == 1 ? a.f[2] : a.f[3]);  // normal momentum
   float* const bn = k == 0 ? a.f[5] : (k == 1 ? a.f[6] : a.f[7]);  // normal face field
-  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+  for (I id = (I)blockIdx.x * blockDim.x + threadIdx.x; id < total; id += (I)gridDim.x * blockDim.x) {
     // along the contiguous axis the 2 x kGhost ghost cells of a row are
     // neighbouring threads (16 contiguous bytes per side); across it,
     // neighbouring threads take neighbouring rows (contiguous along x)
-    long long p;
+    I p;
     int layer, side;
     if (k == 0) {
       layer = (int)(id % kGhost);
       side = (int)((id / kGhost) & 1);
       p = id / (2 * kGhost);
     } else {
-      p = id % plane;
-      layer = (int)((id / plane) % kGhost);
-      side = (int)(id / (plane * kGhost));
+      const I q = id / plane;
+      p = id - q * plane;
+      layer = (int)(q % kGhost);
+      side = (int)(q / kGhost);
     }
-    const long long base = (p % a.n1) * a.s1 + (p / a.n1) * a.s2;
+    const I p2 = p / n1;
+    const long long base = (long long)(p - p2 * n1) * a.s1 + (long long)p2 * a.s2;
     const int dst = side ? nk - 1 - layer : layer;
     const int src = a.mode == 1 ? (side ? whi - 1 : wlo) : (side ? 2 * whi - 1 - dst : 2 * wlo - 1 - dst);
     const long long di = base + dst * a.sk, si = base + src * a.sk;
@@ -77,7 +82,11 @@ cudaError_t launch_ghost_fill(float* const f[8], const Box& box, int axis, int m
   const long long total = 2LL * kGhost * a.n1 * a.n2;
   long long blocks = (total + 255) / 256;
   if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-  ghost_fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  // 32-bit counters while the element count and the last id + stride fit
+  if (total + blocks * 256 < (1LL << 32))
+    ghost_fill_kernel<unsigned><<<(unsigned)blocks, 256, 0, s>>>(a);
+  else
+    ghost_fill_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

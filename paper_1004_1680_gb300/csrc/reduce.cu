@@ -191,6 +191,73 @@ __device__ __noinline__ double cell_p64(float rho, float m1, float m2, float m3,
   return (gamma - 1.0) * ((double)e - kin - 0.5 * (b0 * b0 + b1 * b1 + b2 * b2));
 }
 
+// Float-float tier of the max |div b| filter (inline: out of line it cost
+// about 15 % on near-tied states, for no fewer registers).  Each
+// difference is exact (TwoSum), times n_d (product error by FMA), summed by
+// TwoSum: |D - div| <= 2^-44 dT, dT = sum |(b_high - b_low) n_d|.  True
+// unless |div| is certainly below thr.
+__device__ __forceinline__ bool div_ff_may_exceed(float bxl, float bxh, float byl, float byh, float bzl, float bzh,
+                                               float nxf, float nyf, float nzf, float thr) {
+  float s0, e0, s1, e1, s2, e2, p0, q0, p1, q1, p2, q2;
+  two_sum(bxh, -bxl, s0, e0);
+  two_sum(byh, -byl, s1, e1);
+  two_sum(bzh, -bzl, s2, e2);
+  two_prod(s0, nxf, p0, q0);
+  two_prod(s1, nyf, p1, q1);
+  two_prod(s2, nzf, p2, q2);
+  float h01, r01, dh, r2;
+  two_sum(p0, p1, h01, r01);
+  two_sum(h01, p2, dh, r2);
+  const float dl = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), q2),
+                             __fadd_rn(__fadd_rn(__fmaf_rn(e0, nxf, __fmul_rn(e1, nyf)), __fmul_rn(e2, nzf)),
+                                       __fadd_rn(r01, r2)));
+  const float dT = fabsf(p0) + fabsf(p1) + fabsf(p2);
+  const float dabs = fabsf(__fadd_rn(dh, dl));
+  return !(dabs + (0x1p-22f * dabs + 0x1p-40f * dT + 1e-37f) < thr);  // NaN: true
+}
+
+// Float-float tier of the min p filter:
+// |estimate - p| <= 2^-42 (gamma - 1) U.  True unless p certainly exceeds
+// the float-float threshold th + tl.
+__device__ __forceinline__ bool p_ff_may_undercut(float rho, float m1, float m2, float m3, float e, float bxl,
+                                               float bxh, float byl, float byh, float bzl, float bzh, float rr,
+                                               float g_hi, float g_lo, float U, float th, float tl) {
+  float a0, ae0, a1, ae1, a2, ae2, sa, ra, sh, rb;
+  two_prod(m1, m1, a0, ae0);
+  two_prod(m2, m2, a1, ae1);
+  two_prod(m3, m3, a2, ae2);
+  two_sum(a0, a1, sa, ra);
+  two_sum(sa, a2, sh, rb);
+  const float sl = __fadd_rn(__fadd_rn(__fadd_rn(ae0, ae1), ae2), __fadd_rn(ra, rb));
+  // an approximate reciprocal rr: k1 within a few ulp of S / rho, the FMA
+  // remainder S - k1 rho then corrects it to about 2^-43 S / rho
+  const float k1 = __fmul_rn(sh, rr);
+  const float k2 = __fmul_rn(__fadd_rn(__fmaf_rn(-k1, rho, sh), sl), rr);  // kin = (k1 + k2) / 2
+  float c0h, c0l, c1h, c1l, c2h, c2l;
+  two_sum(bxl, bxh, c0h, c0l);
+  two_sum(byl, byh, c1h, c1l);
+  two_sum(bzl, bzh, c2h, c2l);  // 2 b_c = c_h + c_l exactly
+  float w0, we0, w1, we1, w2, we2, sw, rw, mh, rm;
+  two_prod(c0h, c0h, w0, we0);
+  two_prod(c1h, c1h, w1, we1);
+  two_prod(c2h, c2h, w2, we2);
+  we0 = __fmaf_rn(2.f * c0h, c0l, we0);
+  we1 = __fmaf_rn(2.f * c1h, c1l, we1);
+  we2 = __fmaf_rn(2.f * c2h, c2l, we2);
+  two_sum(w0, w1, sw, rw);
+  two_sum(sw, w2, mh, rm);  // 4 |b_c|^2 = mh + ml
+  const float ml = __fadd_rn(__fadd_rn(__fadd_rn(we0, we1), we2), __fadd_rn(rw, rm));
+  float d1, de1, d2, de2;
+  two_sum(e, -0.5f * k1, d1, de1);
+  two_sum(d1, -0.125f * mh, d2, de2);
+  const float dlo = __fsub_rn(__fsub_rn(__fadd_rn(de1, de2), 0.5f * k2), 0.125f * ml);
+  float ph, phe;
+  two_prod(g_hi, d2, ph, phe);
+  const float pl = __fadd_rn(phe, __fmaf_rn(g_hi, dlo, __fmul_rn(g_lo, d2)));
+  const float dp = 0x1p-38f * g_hi * U + 1e-37f;
+  return !(__fadd_rn(__fsub_rn(ph, th), __fsub_rn(__fsub_rn(pl, tl), dp)) > 0.f);  // NaN: true
+}
+
 // One pass over the box: the compensated sums of the 8 fields, max |div b|
 // (the face differences of each cell) and min p, in FP64 as defined by the
 // formulas below.  The extrema are exact FP64 values of those formulas: a
@@ -259,97 +326,66 @@ diag_partial_kernel(const float* __restrict__ rho, const float* __restrict__ mx,
 #pragma unroll
     for (int q = 0; q < 8; q++) fwin_add(win[q], v[q]);
     {
-      // div b = sum_d (b_high - b_low) n_d as float-float: each difference
-      // exact (TwoSum), times n_d (product error by FMA), summed by TwoSum;
-      // |D - div| <= 2^-44 dT, dT = sum |differences| n_d
-      float s0, e0, s1, e1, s2, e2, p0, q0, p1, q1, p2, q2;
-      two_sum(bxh, -v[5], s0, e0);
-      two_sum(byh, -v[6], s1, e1);
-      two_sum(bzh, -v[7], s2, e2);
-      two_prod(s0, nxf, p0, q0);
-      two_prod(s1, nyf, p1, q1);
-      two_prod(s2, nzf, p2, q2);
-      float h01, r01, dh, r2;
-      two_sum(p0, p1, h01, r01);
-      two_sum(h01, p2, dh, r2);
-      const float dl = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), q2),
-                                 __fadd_rn(__fadd_rn(__fmaf_rn(e0, nxf, __fmul_rn(e1, nyf)), __fmul_rn(e2, nzf)),
-                                           __fadd_rn(r01, r2)));
-      const float dT = fabsf(p0) + fabsf(p1) + fabsf(p2);
-      const float dabs = fabsf(__fadd_rn(dh, dl));
-      // the FP64 evaluations sit behind a warp vote, so that they are skipped
-      // (not just predicated off) when no lane needs them, and the warp takes
-      // the new threshold at once
-      const bool cand_div = valid && !(dabs + (0x1p-22f * dabs + 0x1p-40f * dT + 1e-37f) < div_thr);  // NaN: evaluated
-      if (__any_sync(0xffffffffu, cand_div)) {
-        if (cand_div) {
-          const double div = cell_div64(v[5], bxh, v[6], byh, v[7], bzh, nx, ny, nz);
-          divmax = fmax(divmax, fabs(div));
-          div_thr = fmaxf(div_thr, __double2float_rd(divmax));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) div_thr = fmaxf(div_thr, __shfl_xor_sync(0xffffffffu, div_thr, o));
-      }
-      // p = (gamma - 1)(e - |m|^2 / (2 rho) - |b_c|^2 / 2) as float-float;
-      // |estimate - p| <= 2^-42 (gamma - 1) U with U = |e| + |kin| +
-      // sum ((|b| + |b_high|) / 2)^2 / 2
-      float a0, ae0, a1, ae1, a2, ae2, sa, ra, sh, rb;
-      two_prod(v[1], v[1], a0, ae0);
-      two_prod(v[2], v[2], a1, ae1);
-      two_prod(v[3], v[3], a2, ae2);
-      two_sum(a0, a1, sa, ra);
-      two_sum(sa, a2, sh, rb);
-      const float sl = __fadd_rn(__fadd_rn(__fadd_rn(ae0, ae1), ae2), __fadd_rn(ra, rb));
-      // (an approximate reciprocal: k1 within a few ulp of S / rho, the FMA
-      // remainder S - k1 rho then corrects it to about 2^-43 S / rho)
-      const float rr = fast_rcp(v[0]);
-      const float k1 = __fmul_rn(sh, rr);
-      const float k2 = __fmul_rn(__fadd_rn(__fmaf_rn(-k1, v[0], sh), sl), rr);  // kin = (k1 + k2) / 2
-      float c0h, c0l, c1h, c1l, c2h, c2l;
-      two_sum(v[5], bxh, c0h, c0l);
-      two_sum(v[6], byh, c1h, c1l);
-      two_sum(v[7], bzh, c2h, c2l);  // 2 b_c = c_h + c_l exactly
-      float w0, we0, w1, we1, w2, we2, sw, rw, mh, rm;
-      two_prod(c0h, c0h, w0, we0);
-      two_prod(c1h, c1h, w1, we1);
-      two_prod(c2h, c2h, w2, we2);
-      we0 = __fmaf_rn(2.f * c0h, c0l, we0);
-      we1 = __fmaf_rn(2.f * c1h, c1l, we1);
-      we2 = __fmaf_rn(2.f * c2h, c2l, we2);
-      two_sum(w0, w1, sw, rw);
-      two_sum(sw, w2, mh, rm);  // 4 |b_c|^2 = mh + ml
-      const float ml = __fadd_rn(__fadd_rn(__fadd_rn(we0, we1), we2), __fadd_rn(rw, rm));
-      float d1, de1, d2, de2;
-      two_sum(v[4], -0.5f * k1, d1, de1);
-      two_sum(d1, -0.125f * mh, d2, de2);
-      const float dlo = __fsub_rn(__fsub_rn(__fadd_rn(de1, de2), 0.5f * k2), 0.125f * ml);
-      float ph, phe;
-      two_prod(g_hi, d2, ph, phe);
-      const float pl = __fadd_rn(phe, __fmaf_rn(g_hi, dlo, __fmul_rn(g_lo, d2)));
-      const float ax = fabsf(v[5]) + fabsf(bxh), ay = fabsf(v[6]) + fabsf(byh), az = fabsf(v[7]) + fabsf(bzh);
-      const float U = fabsf(v[4]) + 0.5f * fabsf(k1) + 0.125f * (ax * ax + ay * ay + az * az);
-      const float dp = 0x1p-38f * g_hi * U + 1e-37f;
-      const bool cand_p = valid && !(__fadd_rn(__fsub_rn(ph, pt_hi), __fsub_rn(__fsub_rn(pl, pt_lo), dp)) > 0.f);
-      if (__any_sync(0xffffffffu, cand_p)) {
-        if (cand_p) {  // NaN: evaluated
-          const double p = cell_p64(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, gamma);
-          pmin = fmin(pmin, p);
-          // float-float upper bound of pmin (pt_hi + pt_lo >= pmin)
-          if (fabs(pmin) < 1e38) {
-            const float h = __double2float_rn(pmin);
-            pt_hi = h;
-            pt_lo = __double2float_ru(pmin - (double)h);
-          } else {
-            pt_hi = pmin > 0.0 ? __int_as_float(0x7f800000) : -FLT_MAX;
-            pt_lo = 0.f;
+      // Three tiers, each behind a warp vote (so that a tier is skipped, not
+      // just predicated off, when no lane needs it): an FP32 estimate, a
+      // float-float estimate, the FP64 value.  A lane's cell goes on only if
+      // the tier's error bound (with a margin of 4 or more) cannot rule it out
+      // against the warp's running extremum; a NaN always goes on.
+      //
+      // div b = sum_d (b_high - b_low) n_d.  FP32: |error| <= 2^-22 dT with
+      // dT = sum |(b_high - b_low) n_d|.
+      const float t0 = __fmul_rn(__fsub_rn(bxh, v[5]), nxf), t1 = __fmul_rn(__fsub_rn(byh, v[6]), nyf),
+                  t2 = __fmul_rn(__fsub_rn(bzh, v[7]), nzf);
+      const float d32 = fabsf(t0 + t1 + t2), T32 = fabsf(t0) + fabsf(t1) + fabsf(t2);
+      const bool sdiv = valid && !(d32 + (0x1p-20f * T32 + 1e-37f) < div_thr);
+      if (__any_sync(0xffffffffu, sdiv)) {
+        const bool cand_div = sdiv && div_ff_may_exceed(v[5], bxh, v[6], byh, v[7], bzh, nxf, nyf, nzf, div_thr);
+        if (__any_sync(0xffffffffu, cand_div)) {
+          if (cand_div) {
+            const double div = cell_div64(v[5], bxh, v[6], byh, v[7], bzh, nx, ny, nz);
+            divmax = fmax(divmax, fabs(div));
+            div_thr = fmaxf(div_thr, __double2float_rd(divmax));
           }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, pt_hi, o), ol = __shfl_xor_sync(0xffffffffu, pt_lo, o);
-          if (__fadd_rn(__fsub_rn(oh, pt_hi), __fsub_rn(ol, pt_lo)) < 0.f) {
-            pt_hi = oh;
-            pt_lo = ol;
+          for (int o = 16; o > 0; o >>= 1) div_thr = fmaxf(div_thr, __shfl_xor_sync(0xffffffffu, div_thr, o));
+        }
+      }
+      // p = (gamma - 1)(e - |m|^2 / (2 rho) - |b_c|^2 / 2), U = |e| + |kin| +
+      // sum ((|b| + |b_high|) / 2)^2 / 2.  FP32: |error| <= 2^-19 (gamma - 1) U.
+      const float rr = fast_rcp(v[0]);
+      const float kin32 = 0.5f * __fmaf_rn(v[1], v[1], __fmaf_rn(v[2], v[2], __fmul_rn(v[3], v[3]))) * rr;
+      const float bc0 = v[5] + bxh, bc1 = v[6] + byh, bc2 = v[7] + bzh;  // 2 b_c
+      const float p32 = g_hi * (v[4] - kin32 - 0.125f * __fmaf_rn(bc0, bc0, __fmaf_rn(bc1, bc1, __fmul_rn(bc2, bc2))));
+      const float ax = fabsf(v[5]) + fabsf(bxh), ay = fabsf(v[6]) + fabsf(byh), az = fabsf(v[7]) + fabsf(bzh);
+      const float U = fabsf(v[4]) + fabsf(kin32) + 0.125f * (ax * ax + ay * ay + az * az);
+      // skip while p32 - bound exceeds the threshold pt_hi + pt_lo (>= the
+      // warp's min; 2^-22 |pt_hi| covers rounding that sum)
+      const bool sp = valid && !(__fsub_rn(p32, 0x1p-17f * g_hi * U + 1e-37f) >
+                                 pt_hi + (pt_lo + 0x1p-22f * fabsf(pt_hi)));
+      if (__any_sync(0xffffffffu, sp)) {
+        const bool cand_p = sp && p_ff_may_undercut(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, rr,
+                                                    g_hi, g_lo, U, pt_hi, pt_lo);
+        if (__any_sync(0xffffffffu, cand_p)) {
+          if (cand_p) {
+            const double p = cell_p64(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, gamma);
+            pmin = fmin(pmin, p);
+            // float-float upper bound of pmin (pt_hi + pt_lo >= pmin)
+            if (fabs(pmin) < 1e38) {
+              const float h = __double2float_rn(pmin);
+              pt_hi = h;
+              pt_lo = __double2float_ru(pmin - (double)h);
+            } else {
+              pt_hi = pmin > 0.0 ? __int_as_float(0x7f800000) : -FLT_MAX;
+              pt_lo = 0.f;
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, pt_hi, o), ol = __shfl_xor_sync(0xffffffffu, pt_lo, o);
+            if (__fadd_rn(__fsub_rn(oh, pt_hi), __fsub_rn(ol, pt_lo)) < 0.f) {
+              pt_hi = oh;
+              pt_lo = ol;
+            }
           }
         }
       }
