@@ -176,9 +176,8 @@ __device__ __forceinline__ void fwin_flush(FWin& w, double& acc) {
   w = FWin{0.f, 0.f, 0.f};
 }
 
-// The FP64 values of one cell, out of line: the filters below call them for
-// a few cells only, and a call keeps their FP64 instructions from being
-// issued (predicated off) for every cell.
+// The FP64 values of one cell (the formulas the diagnostics define), out of
+// line: the filters below reach them for a few cells only.
 __device__ __noinline__ double cell_div64(float bxl, float bxh, float byl, float byh, float bzl, float bzh,
                                           int nx, int ny, int nz) {
   return ((double)bxh - bxl) * nx + ((double)byh - byl) * ny + ((double)bzh - bzl) * nz;
@@ -196,8 +195,8 @@ __device__ __noinline__ double cell_p64(float rho, float m1, float m2, float m3,
 // difference is exact (TwoSum), times n_d (product error by FMA), summed by
 // TwoSum: |D - div| <= 2^-44 dT, dT = sum |(b_high - b_low) n_d|.  True
 // unless |div| is certainly below thr.
-__device__ __forceinline__ bool div_ff_may_exceed(float bxl, float bxh, float byl, float byh, float bzl, float bzh,
-                                               float nxf, float nyf, float nzf, float thr) {
+__device__ __forceinline__ bool div_ff_may_exceed(float bxl, float bxh, float byl, float byh, float bzl,
+                                                  float bzh, float nxf, float nyf, float nzf, float thr) {
   float s0, e0, s1, e1, s2, e2, p0, q0, p1, q1, p2, q2;
   two_sum(bxh, -bxl, s0, e0);
   two_sum(byh, -byl, s1, e1);
@@ -220,8 +219,8 @@ __device__ __forceinline__ bool div_ff_may_exceed(float bxl, float bxh, float by
 // |estimate - p| <= 2^-42 (gamma - 1) U.  True unless p certainly exceeds
 // the float-float threshold th + tl.
 __device__ __forceinline__ bool p_ff_may_undercut(float rho, float m1, float m2, float m3, float e, float bxl,
-                                               float bxh, float byl, float byh, float bzl, float bzh, float rr,
-                                               float g_hi, float g_lo, float U, float th, float tl) {
+                                                  float bxh, float byl, float byh, float bzl, float bzh, float rr,
+                                                  float g_hi, float g_lo, float U, float th, float tl) {
   float a0, ae0, a1, ae1, a2, ae2, sa, ra, sh, rb;
   two_prod(m1, m1, a0, ae0);
   two_prod(m2, m2, a1, ae1);
@@ -292,7 +291,7 @@ diag_partial_kernel(const float* __restrict__ rho, const float* __restrict__ mx,
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   int it = 0;
   // row r = j + ny k, stepped by nwarps rows without a division per row
-  // (64-bit integer division is emulated, partly on the FP64 pipe)
+  // (64-bit integer division is emulated in software)
   long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int j = (int)(r % ny);
   long long k = r / ny;
@@ -317,83 +316,83 @@ diag_partial_kernel(const float* __restrict__ rho, const float* __restrict__ mx,
     };
     load(0, nv);
     for (int i0 = 0; i0 < nx; i0 += 32, it++) {
-    const bool valid = i0 + lane < nx;
-    float v[8];
+      const bool valid = i0 + lane < nx;
+      float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; q++) v[q] = valid ? nv[q] : 0.f;
-    const float bxh = nv[8], byh = nv[9], bzh = nv[10];
-    if (i0 + 32 < nx) load(i0 + 32, nv);
+      for (int q = 0; q < 8; q++) v[q] = valid ? nv[q] : 0.f;
+      const float bxh = nv[8], byh = nv[9], bzh = nv[10];
+      if (i0 + 32 < nx) load(i0 + 32, nv);
 #pragma unroll
-    for (int q = 0; q < 8; q++) fwin_add(win[q], v[q]);
-    {
-      // Three tiers, each behind a warp vote (so that a tier is skipped, not
-      // just predicated off, when no lane needs it): an FP32 estimate, a
-      // float-float estimate, the FP64 value.  A lane's cell goes on only if
-      // the tier's error bound (with a margin of 4 or more) cannot rule it out
-      // against the warp's running extremum; a NaN always goes on.
-      //
-      // div b = sum_d (b_high - b_low) n_d.  FP32: |error| <= 2^-22 dT with
-      // dT = sum |(b_high - b_low) n_d|.
-      const float t0 = __fmul_rn(__fsub_rn(bxh, v[5]), nxf), t1 = __fmul_rn(__fsub_rn(byh, v[6]), nyf),
-                  t2 = __fmul_rn(__fsub_rn(bzh, v[7]), nzf);
-      const float d32 = fabsf(t0 + t1 + t2), T32 = fabsf(t0) + fabsf(t1) + fabsf(t2);
-      const bool sdiv = valid && !(d32 + (0x1p-20f * T32 + 1e-37f) < div_thr);
-      if (__any_sync(0xffffffffu, sdiv)) {
-        const bool cand_div = sdiv && div_ff_may_exceed(v[5], bxh, v[6], byh, v[7], bzh, nxf, nyf, nzf, div_thr);
-        if (__any_sync(0xffffffffu, cand_div)) {
-          if (cand_div) {
-            const double div = cell_div64(v[5], bxh, v[6], byh, v[7], bzh, nx, ny, nz);
-            divmax = fmax(divmax, fabs(div));
-            div_thr = fmaxf(div_thr, __double2float_rd(divmax));
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) div_thr = fmaxf(div_thr, __shfl_xor_sync(0xffffffffu, div_thr, o));
-        }
-      }
-      // p = (gamma - 1)(e - |m|^2 / (2 rho) - |b_c|^2 / 2), U = |e| + |kin| +
-      // sum ((|b| + |b_high|) / 2)^2 / 2.  FP32: |error| <= 2^-19 (gamma - 1) U.
-      const float rr = fast_rcp(v[0]);
-      const float kin32 = 0.5f * __fmaf_rn(v[1], v[1], __fmaf_rn(v[2], v[2], __fmul_rn(v[3], v[3]))) * rr;
-      const float bc0 = v[5] + bxh, bc1 = v[6] + byh, bc2 = v[7] + bzh;  // 2 b_c
-      const float p32 = g_hi * (v[4] - kin32 - 0.125f * __fmaf_rn(bc0, bc0, __fmaf_rn(bc1, bc1, __fmul_rn(bc2, bc2))));
-      const float ax = fabsf(v[5]) + fabsf(bxh), ay = fabsf(v[6]) + fabsf(byh), az = fabsf(v[7]) + fabsf(bzh);
-      const float U = fabsf(v[4]) + fabsf(kin32) + 0.125f * (ax * ax + ay * ay + az * az);
-      // skip while p32 - bound exceeds the threshold pt_hi + pt_lo (>= the
-      // warp's min; 2^-22 |pt_hi| covers rounding that sum)
-      const bool sp = valid && !(__fsub_rn(p32, 0x1p-17f * g_hi * U + 1e-37f) >
-                                 pt_hi + (pt_lo + 0x1p-22f * fabsf(pt_hi)));
-      if (__any_sync(0xffffffffu, sp)) {
-        const bool cand_p = sp && p_ff_may_undercut(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, rr,
-                                                    g_hi, g_lo, U, pt_hi, pt_lo);
-        if (__any_sync(0xffffffffu, cand_p)) {
-          if (cand_p) {
-            const double p = cell_p64(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, gamma);
-            pmin = fmin(pmin, p);
-            // float-float upper bound of pmin (pt_hi + pt_lo >= pmin)
-            if (fabs(pmin) < 1e38) {
-              const float h = __double2float_rn(pmin);
-              pt_hi = h;
-              pt_lo = __double2float_ru(pmin - (double)h);
-            } else {
-              pt_hi = pmin > 0.0 ? __int_as_float(0x7f800000) : -FLT_MAX;
-              pt_lo = 0.f;
+      for (int q = 0; q < 8; q++) fwin_add(win[q], v[q]);
+      {
+        // Three tiers, each behind a warp vote (so that a tier is skipped, not
+        // just predicated off, when no lane needs it): an FP32 estimate, a
+        // float-float estimate, the FP64 value.  A lane's cell goes on only if
+        // the tier's error bound (with a margin of 4 or more) cannot rule it out
+        // against the warp's running extremum; a NaN always goes on.
+        //
+        // div b = sum_d (b_high - b_low) n_d.  FP32: |error| <= 2^-22 dT with
+        // dT = sum |(b_high - b_low) n_d|.
+        const float t0 = __fmul_rn(__fsub_rn(bxh, v[5]), nxf), t1 = __fmul_rn(__fsub_rn(byh, v[6]), nyf),
+                    t2 = __fmul_rn(__fsub_rn(bzh, v[7]), nzf);
+        const float d32 = fabsf(t0 + t1 + t2), T32 = fabsf(t0) + fabsf(t1) + fabsf(t2);
+        const bool sdiv = valid && !(d32 + (0x1p-20f * T32 + 1e-37f) < div_thr);
+        if (__any_sync(0xffffffffu, sdiv)) {
+          const bool cand_div = sdiv && div_ff_may_exceed(v[5], bxh, v[6], byh, v[7], bzh, nxf, nyf, nzf, div_thr);
+          if (__any_sync(0xffffffffu, cand_div)) {
+            if (cand_div) {
+              const double div = cell_div64(v[5], bxh, v[6], byh, v[7], bzh, nx, ny, nz);
+              divmax = fmax(divmax, fabs(div));
+              div_thr = fmaxf(div_thr, __double2float_rd(divmax));
             }
-          }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, pt_hi, o), ol = __shfl_xor_sync(0xffffffffu, pt_lo, o);
-            if (__fadd_rn(__fsub_rn(oh, pt_hi), __fsub_rn(ol, pt_lo)) < 0.f) {
-              pt_hi = oh;
-              pt_lo = ol;
-            }
+            for (int o = 16; o > 0; o >>= 1) div_thr = fmaxf(div_thr, __shfl_xor_sync(0xffffffffu, div_thr, o));
           }
         }
-      }
-    }
-    if (it % kWin == kWin - 1) {
+        // p = (gamma - 1)(e - |m|^2 / (2 rho) - |b_c|^2 / 2), U = |e| + |kin| +
+        // sum ((|b| + |b_high|) / 2)^2 / 2.  FP32: |error| <= 2^-19 (gamma - 1) U.
+        const float rr = fast_rcp(v[0]);
+        const float kin32 = 0.5f * __fmaf_rn(v[1], v[1], __fmaf_rn(v[2], v[2], __fmul_rn(v[3], v[3]))) * rr;
+        const float bc0 = v[5] + bxh, bc1 = v[6] + byh, bc2 = v[7] + bzh;  // 2 b_c
+        const float p32 = g_hi * (v[4] - kin32 - 0.125f * __fmaf_rn(bc0, bc0, __fmaf_rn(bc1, bc1, __fmul_rn(bc2, bc2))));
+        const float ax = fabsf(v[5]) + fabsf(bxh), ay = fabsf(v[6]) + fabsf(byh), az = fabsf(v[7]) + fabsf(bzh);
+        const float U = fabsf(v[4]) + fabsf(kin32) + 0.125f * (ax * ax + ay * ay + az * az);
+        // skip while p32 - bound exceeds the threshold pt_hi + pt_lo (>= the
+        // warp's min; 2^-22 |pt_hi| covers rounding that sum)
+        const bool sp = valid && !(__fsub_rn(p32, 0x1p-17f * g_hi * U + 1e-37f) >
+                                   pt_hi + (pt_lo + 0x1p-22f * fabsf(pt_hi)));
+        if (__any_sync(0xffffffffu, sp)) {
+          const bool cand_p = sp && p_ff_may_undercut(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, rr,
+                                                      g_hi, g_lo, U, pt_hi, pt_lo);
+          if (__any_sync(0xffffffffu, cand_p)) {
+            if (cand_p) {
+              const double p = cell_p64(v[0], v[1], v[2], v[3], v[4], v[5], bxh, v[6], byh, v[7], bzh, gamma);
+              pmin = fmin(pmin, p);
+              // float-float upper bound of pmin (pt_hi + pt_lo >= pmin)
+              if (fabs(pmin) < 1e38) {
+                const float h = __double2float_rn(pmin);
+                pt_hi = h;
+                pt_lo = __double2float_ru(pmin - (double)h);
+              } else {
+                pt_hi = pmin > 0.0 ? __int_as_float(0x7f800000) : -FLT_MAX;
+                pt_lo = 0.f;
+              }
+            }
 #pragma unroll
-      for (int q = 0; q < 8; q++) fwin_flush(win[q], acc[q]);
-    }
+            for (int o = 16; o > 0; o >>= 1) {
+              const float oh = __shfl_xor_sync(0xffffffffu, pt_hi, o), ol = __shfl_xor_sync(0xffffffffu, pt_lo, o);
+              if (__fadd_rn(__fsub_rn(oh, pt_hi), __fsub_rn(ol, pt_lo)) < 0.f) {
+                pt_hi = oh;
+                pt_lo = ol;
+              }
+            }
+          }
+        }
+      }
+      if (it % kWin == kWin - 1) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) fwin_flush(win[q], acc[q]);
+      }
     }
     j += dj;
     k += dk;
