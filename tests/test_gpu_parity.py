@@ -378,32 +378,44 @@ def test_orszag_tang_256_first_step_full_parity(mhd):
     assert np.all(err < 1e-5), err
 
 
-def test_turbulence_512_sampled_sub_blocks(mhd):
-    """512^3 decaying turbulence, one step in the bench's launch configuration;
-    the oracle steps periodic sub-blocks with a 24-cell halo (one full step
-    reaches 14 cells) and the interiors are compared."""
-    n = 512
+def _sub_block_dev(t, lo, size):
+    """Periodic sub-block of a device state (as sub_block), copied to the host."""
+    idx = [torch.arange(lo[d], lo[d] + size[d], device=t.device) % t.shape[3 - d] for d in range(3)]
+    return t.index_select(1, idx[2]).index_select(2, idx[1]).index_select(3, idx[0]).cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_turbulence_full_size_sampled_sub_blocks(mhd, n):
+    """512^3 and 1024^3 decaying turbulence (the bench workloads), one step in
+    the bench's launch configuration; the oracle steps periodic sub-blocks
+    with a 24-cell halo (one full step reaches 14 cells) and the interiors
+    are compared.  Sub-blocks are cut on the device, so the 34 GB state of
+    the 1024^3 box never goes to the host."""
+    box = mhd.Box(n, n, n, gamma=G)  # before the input, as bench.py does (its buffers first)
     st32 = ic.turbulence((n, n, n), seed=0, device="cuda", dtype=torch.float32)
-    box = mhd.Box(n, n, n, gamma=G)
     box.set_state(st32)
-    init = st32.cpu().numpy()
+    torch.cuda.empty_cache()
     dt = box.cfl_dt(0.7)
     box.step(dt)
-    out = box.get_state().cpu().numpy()
-    del st32
+    out = box.get_state()
     H, L = 24, 24
     rng = np.random.default_rng(0)
-    corners = [(0, 0, 0), (n - L, n - L, n - L)] + [tuple(rng.integers(0, n, 3)) for _ in range(3)]
-    for lo in corners:
-        nb = L + 2 * H
-        blk = sub_block(init, [c - H for c in lo], [nb] * 3).astype(np.float64)
-        S = field_scales(blk)
-        # the sub-box is a unit cube of nb cells: scale dt so tau/h is unchanged
-        oracle.step(blk, dt * n / nb, G)
-        ref = blk[:, H:H + L, H:H + L, H:H + L]
-        got = sub_block(out, lo, [L] * 3)
-        err = rel_err(got.astype(np.float64), ref, S)
-        assert np.all(err < 1e-5), (lo, err)
+    corners = [(0, 0, 0), (n - L, n - L, n - L)] + [tuple(int(c) for c in rng.integers(0, n, 3)) for _ in range(3)]
+    try:
+        for lo in corners:
+            nb = L + 2 * H
+            blk = _sub_block_dev(st32, [c - H for c in lo], [nb] * 3).astype(np.float64)
+            S = field_scales(blk)
+            # the sub-box is a unit cube of nb cells: scale dt so tau/h is unchanged
+            oracle.step(blk, dt * n / nb, G)
+            ref = blk[:, H:H + L, H:H + L, H:H + L]
+            got = _sub_block_dev(out, lo, [L] * 3)
+            err = rel_err(got.astype(np.float64), ref, S)
+            assert np.all(err < 1e-5), (lo, err)
+    finally:
+        del st32, out
+        box.close()
+        torch.cuda.empty_cache()
 
 
 def test_pressure_floor_parity(mhd):
