@@ -72,6 +72,8 @@ def parse():
                    help="pencil segment length for every axis (0: the library's choice)")
     p.add_argument("--freezing", choices=["bound", "fast", "pencil"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
+    p.add_argument("--fusion", type=int, choices=[0, 1], default=1,
+                   help="1: the two middle z magnetic sweeps of a step as one launch (bitwise the same state)")
     p.add_argument("--bc", default="",
                    help="non-periodic axes, e.g. x=outflow,z=reflecting (4 ghost cells at each end "
                         "inside the box; the paper's runs are periodic)")
@@ -437,6 +439,7 @@ def run_ours(args, rank, world, local):
     box.set_scheme(args.limiter, args.freezing)
     if args.xpath:
         box.set_xpath(args.xpath)
+    box.set_fusion(bool(args.fusion))
     if args.seg:
         box.set_segments(args.seg, args.seg, args.seg)
     bcs = {}
@@ -607,6 +610,7 @@ def run_ours(args, rank, world, local):
                           "step": "CFL + 6 fluid + 6 magnetic sweeps (x,y,z then z,y,x)",
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
                           "xpath": args.xpath or "auto",
+                          "fusion": bool(args.fusion),
                           **({"boundaries": bcs, "interior_cells": int(np.prod([n - 8 if a in bcs else n for a in "xyz"]))}
                              if bcs else {}),
                           **({"mach": args.mach, "beta": args.beta} if (args.mach, args.beta) != (1.0, 1.0) else {}),

@@ -120,6 +120,18 @@ int mhd_time(const mhd_t *m, double *t);
  * the sweeps one by one. */
 int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
 
+/* Kernel fusion of the schedule (not a change of the method): with on = 1
+ * (the default) the two magnetic z sweeps in the middle of a full step,
+ * which follow each other with the same step tau = dt/2, run as one launch
+ * that reads and writes the fields once (two advection pipelines per
+ * transverse component, the second fed by the first; b_z takes both passes'
+ * edge fluxes).  Every value is rounded as in two launches, so the state is
+ * bitwise the same either way.  on = 0 runs the twelve sweeps of Section
+ * II.B one launch each.  Boxes with non-periodic axes (ghost layers are
+ * refilled between the two sweeps) and x path 3 always run them separately.
+ * MHD_E_ARG unless on is 0 or 1. */
+int mhd_set_fusion(mhd_t *m, int on);
+
 /* Optional floor on the gas pressure (not in the paper; 0 = off, the
  * default).  The total-energy scheme leaves e untouched in the magnetic
  * sweeps, so in strongly magnetised, supersonic flow the magnetic energy can
@@ -241,7 +253,8 @@ int mhd_profile_read(mhd_t *m, int counts[], double ms[]);
  *     return.
  * Scratch: a fixed 194 KiB array in the library's device memory, held by
  * every GPU that loads the library until the process exits.  Its device
- * address is looked up on the first call on each device, so call it once
+ * address is looked up in the current context on every call; the first call
+ * in a context also loads the library's device code there, so make it
  * before capturing a stream that will contain it.  All calls share the
  * array: calls that overlap on the GPU (different streams, threads or
  * processes sharing a context) race and must be serialised by the caller. */

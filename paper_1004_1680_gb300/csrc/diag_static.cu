@@ -10,39 +10,31 @@
 // fixed array below, which every GPU that loads this library holds until the
 // process exits.
 #include <cstdio>
-#include <mutex>
 
 #include "mhd.h"
 #include "mhd_launch.h"
 
 namespace {
 
-// The diagnostics grid never has more blocks than this (diag_blocks caps it),
-// so the partials of any box fit; the last 16 doubles take the 10 results.
-constexpr int kStaticDiagBlocks = 152 * 8;
+// The diagnostics grid never has more blocks than kDiagMaxBlocks (diag_blocks
+// caps it), so the partials of any box fit; the last 16 doubles take the 10
+// results.
+constexpr int kStaticDiagBlocks = mhd::kDiagMaxBlocks;
 constexpr int kStaticDiagDoubles = kStaticDiagBlocks * mhd::kDiagSlots + 16;
 __device__ __align__(256) double g_diag_scratch[kStaticDiagDoubles];  // 194 KiB per GPU
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_lock;
-
-// Device address of g_diag_scratch on the current device.  In host code the
-// name g_diag_scratch is only a host-side stand-in, not a device address; the
-// runtime resolves the real address once per device.
+// Device address of g_diag_scratch in the context current on this thread.
+// In host code the name g_diag_scratch is only a host-side stand-in, not a
+// device address, so the runtime is asked for the real one.  It is asked on
+// every call rather than cached: the address belongs to the context that
+// loaded the module, and a cached value would be wrong after a device reset
+// (the module is loaded again, possibly elsewhere) or in another context on
+// the same device.  The first call in a context loads the module there.
 int scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return mhd::set_error(MHD_E_CUDA, "cudaGetDevice", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return mhd::set_error(MHD_E_ARG, "device index", "out of range");
-  std::lock_guard<std::mutex> g(g_scratch_lock);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_diag_scratch);
-    if (e != cudaSuccess) return mhd::set_error(MHD_E_CUDA, "cudaGetSymbolAddress", cudaGetErrorString(e));
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_diag_scratch);
+  if (e != cudaSuccess) return mhd::set_error(MHD_E_CUDA, "cudaGetSymbolAddress", cudaGetErrorString(e));
+  *out = static_cast<double*>(p);
   return MHD_OK;
 }
 

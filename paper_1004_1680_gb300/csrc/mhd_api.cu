@@ -70,6 +70,7 @@ struct mhd_s {
   float p_floor = 0.f;  // optional pressure floor after fluid sweeps (0 = off)
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
+  int fuse = 1;         // 1: the two z magnetic sweeps of a step run as one launch
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
   float* pencil_c = nullptr;  // freezing 2: per-pencil speeds of the sweep being run (2 x N / min n)
   Scalars* sc = nullptr;
@@ -359,7 +360,9 @@ int fluid(mhd_s* m, int d, bool rate) {
   return MHD_OK;
 }
 
-int magnetic(mhd_s* m, int d) {
+// passes = 2: two magnetic sweeps along d with the same step in one launch
+// (bitwise equal to two launches; kernel axis 2 only, the caller checks).
+int magnetic(mhd_s* m, int d, int passes = 1) {
   const mhd::Box* box;
   int ka;
   int rc = sweep_frame(m, d, &box, &ka);
@@ -372,6 +375,7 @@ int magnetic(mhd_s* m, int d) {
   a.tau = &m->sc->tau;
   a.seg = m->seg[d];
   a.lim = m->lim;
+  a.passes = passes;
   rc = traced(m, MHD_K_MAG_X + d, [&] {
     CK(mhd::launch_mag(ka, a, m->stream));
     return MHD_OK;
@@ -385,14 +389,26 @@ int magnetic(mhd_s* m, int d) {
 // fluid before magnetic, then z, y, x with magnetic before fluid; the last
 // fluid sweep also accumulates the CFL rate of the new state (of its interior
 // cells with ghost layers: those cells and the faces their rate reads are
-// final once the sweep has written them; a refill changes neither).
+// final once the sweep has written them; a refill changes neither).  The two
+// z magnetic sweeps in the middle of the schedule follow each other with the
+// same step and run as one launch when fusion is on (bitwise the same
+// result), unless the z sweep runs along the contiguous axis (x path 3) or
+// ghost layers must be refilled between them.
 int full_step(mhd_s* m) {
   int rc;
-  for (int d = 0; d < 3; d++) {
+  for (int d = 0; d < 2; d++) {
     if ((rc = fluid(m, d, false))) return rc;
     if ((rc = magnetic(m, d))) return rc;
   }
-  for (int d = 2; d >= 0; d--) {
+  if ((rc = fluid(m, 2, false))) return rc;
+  if (m->fuse && m->xpath != 3 && !any_bc(m)) {
+    if ((rc = magnetic(m, 2, 2))) return rc;
+  } else {
+    if ((rc = magnetic(m, 2))) return rc;
+    if ((rc = magnetic(m, 2))) return rc;
+  }
+  if ((rc = fluid(m, 2, false))) return rc;
+  for (int d = 1; d >= 0; d--) {
     if ((rc = magnetic(m, d))) return rc;
     if ((rc = fluid(m, d, d == 0))) return rc;
   }
@@ -758,6 +774,13 @@ int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
   }
   m->lim = limiter;
   m->fast = freezing;
+  return MHD_OK;
+}
+
+int mhd_set_fusion(mhd_t* m, int on) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (on < 0 || on > 1) return fail(MHD_E_ARG, "fusion must be 0 or 1");
+  m->fuse = on;
   return MHD_OK;
 }
 

@@ -63,6 +63,7 @@ struct MagArgs {
   EnsArgs ens;
   int nblocks = 0;
   int lim = 0;         // slope limiter (as FluidArgs::lim)
+  int passes = 1;      // 2: two sweeps with the same step in one launch (kernel axis 2 only)
 };
 
 // Ghost layers of a non-periodic axis (boundary.cu): kernel axis `axis` of
@@ -211,6 +212,7 @@ cudaError_t launch_set_tau(float* tau, double value, cudaStream_t s);
 // FP64 diagnostics: per-block partials into `partial` (nblk*kDiagSlots
 // doubles), then a fixed-order final reduction into out[10] (device).
 constexpr int kDiagSlots = 20;  // 8 (sum, compensation) pairs + max|div b| + min p
+constexpr int kDiagMaxBlocks = 152 * 8;  // cap of the diagnostics grid (diag_blocks)
 int diag_blocks(const Box& box);
 cudaError_t launch_diagnostics(const float* const f[8], const Box& box, double gamma, double* partial,
                                double* out, cudaStream_t s);

@@ -463,7 +463,7 @@ __global__ void diag_final_kernel(const double* __restrict__ partial, int nblk, 
 int diag_blocks(const Box& box) {
   const long long N = (long long)box.n[0] * box.n[1] * box.n[2];
   long long b = (N + 4LL * kDiagThreads - 1) / (4LL * kDiagThreads);
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > kDiagMaxBlocks) b = kDiagMaxBlocks;
   if (b < 1) b = 1;
   return (int)b;
 }

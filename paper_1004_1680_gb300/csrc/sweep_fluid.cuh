@@ -106,6 +106,8 @@ fluid_sweep_kernel(FluidArgs a) {
   float* __restrict__ o_m2 = a.out[MX + X::T2] + G.off;
   float* __restrict__ o_en = a.out[EN] + G.off;
   float* xw = xs + (D == 0 ? threadIdx.y * kXTiles * kXTile : 0);  // this warp's tiles
+  // 32-bit unsigned indices from the block-uniform field pointers
+  const unsigned ub = (unsigned)base, ubT1 = (unsigned)baseT1, ubT2 = (unsigned)baseT2;
 
   const float gamma = a.gamma;
   const float tau = G.tau;
@@ -151,23 +153,33 @@ fluid_sweep_kernel(FluidArgs a) {
       __syncwarp();
     } else {
       // one coalesced row per plane (an L2 prefetch of the next chunk's 10
-      // rows on top measured slower: 1.50 -> 1.60 ms along y at 512^3)
+      // rows on top measured slower: 1.50 -> 1.60 ms along y at 512^3).
+      // Offsets along the pencil: only a chunk that crosses the periodic
+      // wrap needs the wrapped form; the others advance linearly.
       float bdn[CH + 1], t1n[CH], t2n[CH];
+      int off[CH + 1];
+      if (SMALL || p0 < 0 || p0 + CH >= nD) {
+#pragma unroll
+        for (int j = 0; j <= CH; j++) off[j] = wrap_near<SMALL>(p0 + j, nD) * sD;
+      } else {
+        const int o0 = p0 * sD;
+#pragma unroll
+        for (int j = 0; j <= CH; j++) off[j] = o0 + j * sD;
+      }
 #pragma unroll
       for (int j = 0; j < CH; j++) {
-        const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
-        U[j][0] = __ldg(rho + base + off);
-        U[j][1] = __ldg(md + base + off);
-        U[j][2] = __ldg(m1 + base + off);
-        U[j][3] = __ldg(m2 + base + off);
-        U[j][4] = __ldg(en + base + off);
-        bdn[j] = __ldg(bd + base + off);
-        B[j][1] = __ldg(b1 + base + off);
-        B[j][2] = __ldg(b2 + base + off);
-        t1n[j] = __ldg(b1 + baseT1 + off);
-        t2n[j] = __ldg(b2 + baseT2 + off);
+        U[j][0] = __ldg(rho + (ub + (unsigned)off[j]));
+        U[j][1] = __ldg(md + (ub + (unsigned)off[j]));
+        U[j][2] = __ldg(m1 + (ub + (unsigned)off[j]));
+        U[j][3] = __ldg(m2 + (ub + (unsigned)off[j]));
+        U[j][4] = __ldg(en + (ub + (unsigned)off[j]));
+        bdn[j] = __ldg(bd + (ub + (unsigned)off[j]));
+        B[j][1] = __ldg(b1 + (ub + (unsigned)off[j]));
+        B[j][2] = __ldg(b2 + (ub + (unsigned)off[j]));
+        t1n[j] = __ldg(b1 + (ubT1 + (unsigned)off[j]));
+        t2n[j] = __ldg(b2 + (ubT2 + (unsigned)off[j]));
       }
-      bdn[CH] = __ldg(bd + base + wrap_near<SMALL>(p0 + CH, nD) * sD);
+      bdn[CH] = __ldg(bd + (ub + (unsigned)off[CH]));
 #pragma unroll
       for (int j = 0; j < CH; j++) {
         // cell-centred field: mean of the low and high face of the cell
@@ -199,7 +211,7 @@ fluid_sweep_kernel(FluidArgs a) {
       const int t = p0 + j;
       const int po = t - 3;  // position of the finished cell
       if (active && po >= s0 && po < s1) {
-        const int cell = base + po * sD;  // po is inside [s0, s1)
+        const unsigned cell = ub + (unsigned)(po * sD);  // po is inside [s0, s1)
         if (FLOOR) o[4] = floored_energy(o, bc3, gamma, a.p_floor);  // optional (b_c of this cell is bc3)
         o_rho[cell] = o[0];
         o_md[cell] = o[1];

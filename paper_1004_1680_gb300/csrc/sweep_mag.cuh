@@ -29,6 +29,19 @@
 
 namespace mhd {
 
+// The constraint on b_D from the two transverse edge-flux differences,
+// applied in the order of the local frame (first transverse axis first), each
+// rounded once: b + k_A (fA1 - fA0) + k_O (fO1 - fO0).
+__device__ __forceinline__ float constrain(float b, float kA, float fa0, float fa1, float kO, float fo0,
+                                          float fo1, bool a_first) {
+  if (a_first) {
+    b = __fmaf_rn(kA, __fsub_rn(fa1, fa0), b);
+    return __fmaf_rn(kO, __fsub_rn(fo1, fo0), b);
+  }
+  b = __fmaf_rn(kO, __fsub_rn(fo1, fo0), b);
+  return __fmaf_rn(kA, __fsub_rn(fa1, fa0), b);
+}
+
 template <int D>
 struct MagAxes {
   static constexpr int A = (D == 0) ? 1 : 0;
@@ -74,10 +87,10 @@ __device__ __forceinline__ void stage_vel(float* tile, const float* __restrict__
     const float4 rr = __ldg(reinterpret_cast<const float4*>(rho + rb + off));
     const float4 mm = __ldg(reinterpret_cast<const float4*>(m + rb + off));
     float* t = tile + r * kMXPad + 4 * h;
-    t[0] = __fdividef(mm.x, rr.x);
-    t[1] = __fdividef(mm.y, rr.y);
-    t[2] = __fdividef(mm.z, rr.z);
-    t[3] = __fdividef(mm.w, rr.w);
+    t[0] = v_div(mm.x, rr.x);
+    t[1] = v_div(mm.y, rr.y);
+    t[2] = v_div(mm.z, rr.z);
+    t[3] = v_div(mm.w, rr.w);
   }
 }
 
@@ -178,8 +191,8 @@ mag_sweep_kernel(MagArgs a) {
       const float qAj = rw[3 * kMXTile + j];
       const float qOj = rw[4 * kMXTile + j];
       const float qDj = rw[5 * kMXTile + j];
-      const float uA = 0.5f * (vj + vAj);  // v_D on the b_A face
-      const float uO = 0.5f * (vj + vOj);  // v_D on the b_O face
+      const float uA = __fmul_rn(0.5f, __fadd_rn(vj, vAj));  // v_D on the b_A face
+      const float uO = __fmul_rn(0.5f, __fadd_rn(vj, vOj));  // v_D on the b_O face
       // the halo row needs only the flux along O, the halo column only along A
       float nA_new = 0.f, nO_new = 0.f, fa = 0.f, fo = 0.f;
       if (w != kMagWarps) fa = pA.step(qAj, uA, c_half, c_full, nA_new);
@@ -207,13 +220,7 @@ mag_sweep_kernel(MagArgs a) {
           const float fa0 = fA_s[c & 1][j][row][col], fa1 = fA_s[c & 1][j][row][col + 1];
           const float fo0 = fO_s[c & 1][j][row][col], fo1 = fO_s[c & 1][j][row + 1][col];
           float b = bDold[j];
-          if (X::T1 == X::A) {
-            b += kA * (fa1 - fa0);
-            b += kO * (fo1 - fo0);
-          } else {
-            b += kO * (fo1 - fo0);
-            b += kA * (fa1 - fa0);
-          }
+          b = constrain(b, kA, fa0, fa1, kO, fo0, fo1, X::T1 == X::A);
           o_bD[base + pf * sD] = b;  // pf is inside [s0, s1)
         }
       }
@@ -223,104 +230,134 @@ mag_sweep_kernel(MagArgs a) {
 
 // Sweeps along y and z (D = 1, 2; the x sweeps also run along y, on the
 // x <-> y exchanged copy): the same arithmetic as mag_sweep_kernel,
-// reorganised for memory-level parallelism.
+// reorganised for memory-level parallelism and a short instruction stream.
+//  * The three warp roles (interior rows, halo row, halo column) run their own
+//    specialised loop (mag_pipe_role), chosen once per warp: no role test is
+//    left inside the marching loop.  With the tests inside the loop, 124 of
+//    246 thread instructions per cell were integer, move and branch overhead
+//    (ncu instruction classes at 256^3).
 //  * Every thread loads 5 values per position.  An interior pencil loads
 //    rho, m_D, b_A, b_O, b_D.  The halo row loads rho, m_D, b_O and rho, m_D
 //    of the pencil row below the tile (-O).  The halo column loads rho, m_D,
-//    b_A and rho, m_D of the pencil column left of the tile (-A).  Before
-//    this, a thread loaded rho and m_D of its -A and -O neighbours itself: 9
-//    loads per position.
+//    b_A and rho, m_D of the pencil column left of the tile (-A).
 //  * v_D = m_D / rho of the -A and -O neighbours comes from shared memory,
 //    v_s[row + 1][col + 1] (row 0: the -O pencils, column 0: the -A ones).
 //  * The v_D of chunk c + 1 is written to the other half of v_s before
 //    chunk c's barrier, which therefore covers both exchanges.  Along y the
 //    loads of chunk c + 1 are issued before chunk c is computed; along z,
-//    whose positions are a whole plane apart, they are issued after it.
-//    Issuing them early measured 1.39 -> 1.15 ms per launch along y at
-//    512^3 (from mag_sweep_kernel), but 1.65 ms along z, where issuing them
-//    late gives 1.33 (mag_sweep_kernel: 1.41).
-//  * Along z an L2 prefetch of the next chunk's 5 lines per thread goes out
-//    before the arithmetic instead (no registers held): 1.34 -> 1.24 ms at
-//    512^3; two or three chunks ahead measured the same or slower.  Along
-//    y, a prefetch two chunks ahead of the early loads costs 1.15 -> 1.30.
-template <int D, bool SMALL, int LIM>
-__global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
-mag_sweep_pipe_kernel(MagArgs a) {
-  static_assert(D != 0, "x sweeps use the staged kernel");
+//    whose positions are a whole plane apart, they are issued after it, and
+//    an L2 prefetch of the next chunk's lines goes out before the arithmetic
+//    (no registers held): 1.34 -> 1.24 ms at 512^3.  Along y, a prefetch
+//    two chunks ahead of the early loads cost 1.15 -> 1.30.
+//  * NP = 2 runs two magnetic sweeps along D with the same step in one pass
+//    (the two z sweeps in the middle of the schedule, [M_z][M_z], see the same
+//    velocity field): each advected component goes through a second MagPipe
+//    fed with the first one's output three positions later, with the face
+//    velocity delayed to match, and b_D takes the second pass's fluxes on top
+//    of the first's.  Every value is rounded as in two separate launches, so
+//    the result is bitwise that of two NP = 1 sweeps, for one read and one
+//    write of the fields instead of two.
+constexpr int kMagCH = 4;  // positions per chunk (one barrier per chunk)
+
+template <int NP>
+struct MagShared {
+  float fA[NP][2][kMagCH][kMagWarps][33];      // flux of b_A, column 32 = halo column
+  float fO[NP][2][kMagCH][kMagWarps + 1][32];  // flux of b_O, row kMagWarps = halo row
+  float v[2][kMagCH][kMagWarps + 1][33];       // v_D of the tile's pencils and the -A, -O ones
+};
+
+enum { kRoleInterior = 0, kRoleHaloRow = 1, kRoleHaloCol = 2 };
+
+template <int D, bool SMALL, int LIM, int NP, int ROLE>
+__device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom& G, MagShared<NP>& sh) {
   constexpr bool kEarly = D == 1;  // next chunk's loads before the current chunk's arithmetic
   using X = MagAxes<D>;
-  constexpr int CH = 4;
-  __shared__ float fA_s[2][CH][kMagWarps][33];       // flux of b_A, column 32 = halo column
-  __shared__ float fO_s[2][CH][kMagWarps + 1][32];   // flux of b_O, row kMagWarps = halo row
-  __shared__ float v_s[2][CH][kMagWarps + 1][33];    // v_D of the tile's pencils and the -A, -O ones
-
+  constexpr int CH = kMagCH;
+  constexpr bool kA_ = ROLE != kRoleHaloRow;  // advects b_A (flux along A)
+  constexpr bool kO_ = ROLE != kRoleHaloCol;  // advects b_O (flux along O)
   const int lane = threadIdx.x, w = threadIdx.y;
-  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
   const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
   const int a0 = G.bx * 32, b0 = G.by * kMagWarps;
   const int cntA = min(32, nA - a0), cntO = min(kMagWarps, nO - b0);
 
-  // this thread's pencil (pa, pb), its extra pencil (ea, eb) for the halo
-  // warps, its role and its slots
-  int pa, pb, ea, eb;
-  bool interior = false;
-  int row, col;       // slot in the flux exchange arrays
-  int vr, vc;         // slot of the neighbour v_D this thread reads
-  int er = -1, ec = -1;  // slot its extra pencil's v_D goes to
-  if (w < kMagWarps) {
+  // this thread's pencil (pa, pb), the extra pencil (ea, eb) of a halo warp,
+  // its slots in the exchange arrays and those of the neighbour v_D it reads
+  int pa, pb, ea = 0, eb = 0, row, col;
+  bool interior = false, wr_row, wr_col, extra = false;
+  int vAr, vAc, vOr, vOc;  // v_s slots of the -A and -O neighbours
+  if constexpr (ROLE == kRoleInterior) {
     pa = a0 + min(lane, cntA - 1);
     pb = b0 + min(w, cntO - 1);
-    ea = pa;
-    eb = pb;
     interior = (lane < cntA) && (w < cntO);
     row = w;
     col = lane;
-    vr = w + 1;
-    vc = lane + 1;
-  } else if (w == kMagWarps) {             // halo row: pencils (a0+lane, b0+cntO)
+    wr_row = w < cntO;
+    wr_col = w < cntO && lane < cntA;
+    vAr = w + 1; vAc = lane;
+    vOr = w;     vOc = lane + 1;
+  } else if constexpr (ROLE == kRoleHaloRow) {  // pencils (a0+lane, b0+cntO)
     pa = a0 + min(lane, cntA - 1);
     pb = wrapi(b0 + cntO, nO);
     ea = pa;
     eb = wrapi(b0 - 1, nO);
+    extra = true;
     row = cntO;
     col = lane;
-    vr = cntO;                             // its -O neighbour: tile row cntO - 1
-    vc = lane + 1;
-    er = 0;
-    ec = lane + 1;
-  } else {                                 // halo column: pencils (a0+cntA, b0+lane)
+    wr_row = true;
+    wr_col = false;
+    vAr = vAc = 0;
+    vOr = cntO; vOc = lane + 1;               // its -O neighbour: tile row cntO - 1
+  } else {                                     // halo column: pencils (a0+cntA, b0+lane)
     pa = wrapi(a0 + cntA, nA);
     pb = b0 + min(lane, cntO - 1);
     ea = wrapi(a0 - 1, nA);
     eb = pb;
+    extra = lane < kMagWarps;
     row = min(lane, kMagWarps - 1);
     col = cntA;
-    vr = min(lane, cntO - 1) + 1;          // its -A neighbour: tile column cntA - 1
-    vc = cntA;
-    if (lane < kMagWarps) {
-      er = lane + 1;
-      ec = 0;
-    }
+    wr_row = false;
+    wr_col = lane < cntO;
+    vAr = min(lane, cntO - 1) + 1; vAc = cntA;  // its -A neighbour: tile column cntA - 1
+    vOr = vOc = 0;
   }
+  // where this thread's own v_D (interior) or its extra pencil's v_D (halo) goes
+  int pr, pc;
+  if constexpr (ROLE == kRoleInterior) { pr = w + 1; pc = lane + 1; }
+  else if constexpr (ROLE == kRoleHaloRow) { pr = 0; pc = lane + 1; }
+  else { pr = lane + 1; pc = 0; }
+
   const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
   const int base = pa * sA + pb * sO;
   const int ebase = ea * sA + eb * sO;
-
   const float* __restrict__ rho = a.in[RHO] + G.off;
   const float* __restrict__ md = a.in[MX + D] + G.off;
-  const float* __restrict__ bA = a.in[BX + X::A] + G.off;
-  const float* __restrict__ bO = a.in[BX + X::O] + G.off;
-  const float* __restrict__ bD = a.in[BX + D] + G.off;
+  // the role's loads (block-uniform field pointers, 32-bit unsigned
+  // indices): own rho and m_D, then interior b_A, b_O, b_D; halo row b_O,
+  // rho(-O), m_D(-O); halo column b_A, rho(-A), m_D(-A)
+  const float* __restrict__ p2;
+  const float* __restrict__ p3;
+  const float* __restrict__ p4;
+  unsigned i3, i4;
+  const unsigned ib = (unsigned)base;
+  if constexpr (ROLE == kRoleInterior) {
+    p2 = a.in[BX + X::A] + G.off;
+    p3 = a.in[BX + X::O] + G.off;
+    p4 = a.in[BX + D] + G.off;
+    i3 = i4 = ib;
+  } else if constexpr (ROLE == kRoleHaloRow) {
+    p2 = a.in[BX + X::O] + G.off;
+    p3 = rho;
+    p4 = md;
+    i3 = i4 = (unsigned)ebase;
+  } else {
+    p2 = a.in[BX + X::A] + G.off;
+    p3 = rho;
+    p4 = md;
+    i3 = i4 = (unsigned)ebase;
+  }
   float* __restrict__ o_bA = a.out[X::A] + G.off;
   float* __restrict__ o_bO = a.out[X::O] + G.off;
   float* __restrict__ o_bD = a.out[D] + G.off;
-  // the three role-dependent loads: interior b_A, b_O, b_D; halo row
-  // rho(-O), b_O, m_D(-O); halo column b_A, rho(-A), m_D(-A)
-  const float* __restrict__ p2 = (w == kMagWarps) ? rho + ebase : bA + base;
-  const float* __restrict__ p3 = (w == kMagWarps + 1) ? rho + ebase : bO + base;
-  const float* __restrict__ p4 = (w < kMagWarps) ? bD + base : md + ebase;
-  const float* __restrict__ p0r = rho + base;
-  const float* __restrict__ p1m = md + base;
 
   const float tau = G.tau;
   const float c_full = tau * (float)nD;        // tau / h_D
@@ -329,130 +366,163 @@ mag_sweep_pipe_kernel(MagArgs a) {
   const float kO = tau * (float)nO;             // tau / h_O
   const int s0 = G.bz * G.seg;
   const int s1 = s0 + G.seg;
-  // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
-  // warm-up cell, as in the staged x kernel)
-  const int nchunk = (G.seg + 7 + CH - 1) / CH;
-  const bool write_row = (w < kMagWarps) ? (w < cntO) : (w == kMagWarps);
-  const bool write_col = (w < kMagWarps) ? (w < cntO && lane < cntA)
-                                         : (w == kMagWarps + 1 && lane < cntO);
+  // each pass lags its input by 3 positions: positions s0-4NP .. s1+3NP-1
+  // feed outputs s0 .. s1-1 (one extra warm-up cell per pass, as in the
+  // staged x kernel)
+  const int nchunk = (G.seg + 7 * NP + CH - 1) / CH;
+  constexpr int kLag = 3 * NP;                 // final b_t at t - kLag, final b_D at face t - kLag + 1
 
-  MagPipe<LIM> pA, pO;
+  MagPipe<LIM> pA, pO;      // first pass
+  MagPipe<LIM> qA, qO;      // second pass (NP == 2)
   pA.init();
   pO.init();
+  qA.init();
+  qO.init();
+  float uA1 = 0.f, uA2 = 0.f, uA3 = 0.f, uO1 = 0.f, uO2 = 0.f, uO3 = 0.f;  // face velocities at t-1..t-3
   float bD1 = 0.f, bD2 = 0.f;  // raw b_D at t-1, t-2
+  float bP1 = 0.f, bP2 = 0.f, bP3 = 0.f;  // b_D after the first pass at faces t-3, t-4, t-5
 
-  // current chunk: own v_D and the role's b values (interior: b_A, b_O, b_D)
-  float cv[CH], c2[CH], c3[CH], c4[CH];
+  float cv[CH], cq2[CH], cq4[CH];  // own v_D; the advected value(s) of the current chunk
   auto load_chunk = [&](int p0, float (&r0)[CH], float (&r1)[CH], float (&r2)[CH], float (&r3)[CH],
                         float (&r4)[CH]) {
 #pragma unroll
     for (int j = 0; j < CH; j++) {
-      const int off = wrap_near<SMALL>(p0 + j, nD) * sD;
-      r0[j] = __ldg(p0r + off);
-      r1[j] = __ldg(p1m + off);
-      r2[j] = __ldg(p2 + off);
-      r3[j] = __ldg(p3 + off);
-      r4[j] = __ldg(p4 + off);
+      const unsigned off = (unsigned)(wrap_near<SMALL>(p0 + j, nD) * sD);
+      r0[j] = __ldg(rho + (ib + off));
+      r1[j] = __ldg(md + (ib + off));
+      r2[j] = __ldg(p2 + (ib + off));
+      r3[j] = __ldg(p3 + (i3 + off));
+      r4[j] = __ldg(p4 + (i4 + off));
     }
   };
-  // v_D of the loaded chunk into registers and v_s[buf]; the halo warps'
-  // extra pencils only into v_s
+  // v_D of the loaded chunk into registers and v_s[buf]; interior: b_A and
+  // b_O (cq2 / r3 kept in cq2, cq4) and b_D; halo warps: their advected field
+  // and their extra pencil's v_D
+  float cq3[CH];
   auto publish = [&](int buf, const float (&r0)[CH], const float (&r1)[CH], const float (&r2)[CH],
                      const float (&r3)[CH], const float (&r4)[CH]) {
 #pragma unroll
     for (int j = 0; j < CH; j++) {
-      cv[j] = __fdividef(r1[j], r0[j]);
-      if (w < kMagWarps) {
-        v_s[buf][j][vr][vc] = cv[j];
-        c2[j] = r2[j];
-        c3[j] = r3[j];
-        c4[j] = r4[j];
-      } else if (w == kMagWarps) {
-        if (er >= 0) v_s[buf][j][er][ec] = __fdividef(r4[j], r2[j]);
-        c2[j] = 0.f;
-        c3[j] = r3[j];
-        c4[j] = 0.f;
+      cv[j] = v_div(r1[j], r0[j]);
+      cq2[j] = r2[j];
+      if constexpr (ROLE == kRoleInterior) {
+        sh.v[buf][j][pr][pc] = cv[j];
+        cq3[j] = r3[j];
+        cq4[j] = r4[j];
       } else {
-        if (er >= 0) v_s[buf][j][er][ec] = __fdividef(r4[j], r3[j]);
-        c2[j] = r2[j];
-        c3[j] = 0.f;
-        c4[j] = 0.f;
+        if (extra) sh.v[buf][j][pr][pc] = v_div(r4[j], r3[j]);
       }
     }
   };
   {
     float r0[CH], r1[CH], r2[CH], r3[CH], r4[CH];
-    load_chunk(s0 - 4, r0, r1, r2, r3, r4);
+    load_chunk(s0 - 4 * NP, r0, r1, r2, r3, r4);
     publish(0, r0, r1, r2, r3, r4);
   }
   __syncthreads();
 
   for (int c = 0; c < nchunk; c++) {
-    const int p0 = s0 - 4 + CH * c;
+    const int p0 = s0 - 4 * NP + CH * c;
     const bool more = c + 1 < nchunk;
+    const int buf = c & 1;
     float n0[CH], n1[CH], n2[CH], n3[CH], n4[CH];
     if (kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
     if (!kEarly && more) {  // the next chunk's lines into L2 during the arithmetic
 #pragma unroll
       for (int j = 0; j < CH; j++) {
-        const int off = wrap_near<SMALL>(p0 + CH + j, nD) * sD;
-        prefetch_l2(p0r + off);
-        prefetch_l2(p1m + off);
-        prefetch_l2(p2 + off);
-        prefetch_l2(p3 + off);
-        prefetch_l2(p4 + off);
+        const unsigned off = (unsigned)(wrap_near<SMALL>(p0 + CH + j, nD) * sD);
+        prefetch_l2(rho + (ib + off));
+        prefetch_l2(md + (ib + off));
+        prefetch_l2(p2 + (ib + off));
+        prefetch_l2(p3 + (i3 + off));
+        prefetch_l2(p4 + (i4 + off));
       }
     }
     float bDold[CH];  // raw b_D at the face each position's constraint updates
 #pragma unroll
     for (int j = 0; j < CH; j++) {
       const float vj = cv[j];
-      float nA_new = 0.f, nO_new = 0.f, fa = 0.f, fo = 0.f;
-      if (w != kMagWarps) {  // flux along A: interior and halo column
-        const float vAj = (w < kMagWarps) ? v_s[c & 1][j][vr][vc - 1] : v_s[c & 1][j][vr][vc];
-        fa = pA.step(c2[j], 0.5f * (vj + vAj), c_half, c_full, nA_new);
+      float nA_new = 0.f, nO_new = 0.f;
+      if constexpr (kA_) {  // flux along A: interior and halo column
+        const float uA = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vAr][vAc]));
+        const float fa = pA.step(cq2[j], uA, c_half, c_full, nA_new);
+        if (wr_col) sh.fA[0][buf][j][row][col] = fa;
+        if constexpr (NP == 2) {
+          float q2;
+          const float fa2 = qA.step(nA_new, uA3, c_half, c_full, q2);
+          if (wr_col) sh.fA[1][buf][j][row][col] = fa2;
+          nA_new = q2;
+          uA3 = uA2;
+          uA2 = uA1;
+          uA1 = uA;
+        }
       }
-      if (w != kMagWarps + 1) {  // flux along O: interior and halo row
-        const float vOj = (w < kMagWarps) ? v_s[c & 1][j][vr - 1][vc] : v_s[c & 1][j][vr][vc];
-        fo = pO.step(c3[j], 0.5f * (vj + vOj), c_half, c_full, nO_new);
+      if constexpr (kO_) {  // flux along O: interior and halo row
+        const float qin = (ROLE == kRoleInterior) ? cq3[j] : cq2[j];
+        const float uO = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vOr][vOc]));
+        const float fo = pO.step(qin, uO, c_half, c_full, nO_new);
+        if (wr_row) sh.fO[0][buf][j][row][col] = fo;
+        if constexpr (NP == 2) {
+          float q2;
+          const float fo2 = qO.step(nO_new, uO3, c_half, c_full, q2);
+          if (wr_row) sh.fO[1][buf][j][row][col] = fo2;
+          nO_new = q2;
+          uO3 = uO2;
+          uO2 = uO1;
+          uO1 = uO;
+        }
       }
-      if (write_row) fO_s[c & 1][j][row][col] = fo;
-      if (write_col) fA_s[c & 1][j][row][col] = fa;
-      bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
-      bD2 = bD1;
-      bD1 = c4[j];
-      const int t = p0 + j;
-      const int po = t - 3;
-      if (interior && po >= s0 && po < s1) {
-        const int cell = base + po * sD;  // po is inside [s0, s1)
-        o_bA[cell] = nA_new;
-        o_bO[cell] = nO_new;
+      if constexpr (ROLE == kRoleInterior) {
+        bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
+        bD2 = bD1;
+        bD1 = cq4[j];
+        const int po = p0 + j - kLag;
+        if (interior && po >= s0 && po < s1) {
+          const unsigned cell = ib + (unsigned)(po * sD);  // po is inside [s0, s1)
+          o_bA[cell] = nA_new;
+          o_bO[cell] = nO_new;
+        }
       }
     }
     if (!kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
     if (more) publish((c + 1) & 1, n0, n1, n2, n3, n4);
     __syncthreads();
-    if (interior) {
+    if constexpr (ROLE == kRoleInterior) {
+      if (interior) {
 #pragma unroll
-      for (int j = 0; j < CH; j++) {
-        const int t = p0 + j;
-        const int pf = t - 2;  // b_D face updated by the edge flux f(t-5/2)
-        if (pf >= s0 && pf < s1) {
-          const float fa0 = fA_s[c & 1][j][row][col], fa1 = fA_s[c & 1][j][row][col + 1];
-          const float fo0 = fO_s[c & 1][j][row][col], fo1 = fO_s[c & 1][j][row + 1][col];
-          float b = bDold[j];
-          if (X::T1 == X::A) {
-            b += kA * (fa1 - fa0);
-            b += kO * (fo1 - fo0);
-          } else {
-            b += kO * (fo1 - fo0);
-            b += kA * (fa1 - fa0);
+        for (int j = 0; j < CH; j++) {
+          const int t = p0 + j;
+          // first pass: face t-2 takes the edge fluxes f(t-5/2)
+          float b = constrain(bDold[j], kA, sh.fA[0][buf][j][row][col], sh.fA[0][buf][j][row][col + 1], kO,
+                              sh.fO[0][buf][j][row][col], sh.fO[0][buf][j][row + 1][col], X::T1 == X::A);
+          if constexpr (NP == 2) {
+            // second pass: face t-5 (first-pass value from three positions ago)
+            const float b2 = constrain(bP3, kA, sh.fA[1][buf][j][row][col], sh.fA[1][buf][j][row][col + 1],
+                                       kO, sh.fO[1][buf][j][row][col], sh.fO[1][buf][j][row + 1][col],
+                                       X::T1 == X::A);
+            bP3 = bP2;
+            bP2 = bP1;
+            bP1 = b;
+            b = b2;
           }
-          o_bD[base + pf * sD] = b;  // pf is inside [s0, s1)
+          const int pf = t - kLag + 1;
+          if (pf >= s0 && pf < s1) o_bD[ib + (unsigned)(pf * sD)] = b;  // pf is inside [s0, s1)
         }
       }
     }
   }
+}
+
+template <int D, bool SMALL, int LIM, int NP>
+__global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
+mag_sweep_pipe_kernel(MagArgs a) {
+  static_assert(D != 0, "x sweeps use the staged kernel");
+  static_assert(NP == 1 || NP == 2, "one or two passes");
+  __shared__ MagShared<NP> sh;
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
+  if (threadIdx.y < kMagWarps) mag_pipe_role<D, SMALL, LIM, NP, kRoleInterior>(a, G, sh);
+  else if (threadIdx.y == kMagWarps) mag_pipe_role<D, SMALL, LIM, NP, kRoleHaloRow>(a, G, sh);
+  else mag_pipe_role<D, SMALL, LIM, NP, kRoleHaloCol>(a, G, sh);
 }
 
 // The x sweep stages rows in more than 48 KB of shared memory; the limit is
@@ -481,13 +551,19 @@ cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
   }
   MAG_CASE(0, kMagXSmem)
 #undef MAG_CASE
+  if (a.passes == 2 && axis == 0) return cudaErrorInvalidValue;  // the staged x kernel runs one pass
   if (axis == 1) {
-    if (small) mag_sweep_pipe_kernel<1, true, LIM><<<grid, block, 0, s>>>(a);
-    else mag_sweep_pipe_kernel<1, false, LIM><<<grid, block, 0, s>>>(a);
+    if (small) mag_sweep_pipe_kernel<1, true, LIM, 1><<<grid, block, 0, s>>>(a);
+    else mag_sweep_pipe_kernel<1, false, LIM, 1><<<grid, block, 0, s>>>(a);
   }
   if (axis == 2) {
-    if (small) mag_sweep_pipe_kernel<2, true, LIM><<<grid, block, 0, s>>>(a);
-    else mag_sweep_pipe_kernel<2, false, LIM><<<grid, block, 0, s>>>(a);
+    if (a.passes == 2) {
+      if (small) mag_sweep_pipe_kernel<2, true, LIM, 2><<<grid, block, 0, s>>>(a);
+      else mag_sweep_pipe_kernel<2, false, LIM, 2><<<grid, block, 0, s>>>(a);
+    } else {
+      if (small) mag_sweep_pipe_kernel<2, true, LIM, 1><<<grid, block, 0, s>>>(a);
+      else mag_sweep_pipe_kernel<2, false, LIM, 1><<<grid, block, 0, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -46,6 +46,7 @@ SIGNATURES = {
     "mhd_sweep": (_I, [_P, _I, _I, _D]),
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
+    "mhd_set_fusion": (_I, [_P, _I]),
     "mhd_set_pressure_floor": (_I, [_P, _D]),
     "mhd_set_scheme": (_I, [_P, _I, _I]),
     "mhd_set_boundary": (_I, [_P, _I, _I]),
@@ -252,6 +253,11 @@ class Box:
     def fill_ghosts(self):
         """Refill the ghost layers of the non-periodic axes now."""
         _check(self.lib.mhd_fill_ghosts(self.h))
+
+    def set_fusion(self, on: bool):
+        """Run the two middle z magnetic sweeps of a step as one launch (on,
+        the default) or as two (off); the state is bitwise the same."""
+        _check(self.lib.mhd_set_fusion(self.h, int(bool(on))))
 
     def set_xpath(self, mode: int):
         """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic;

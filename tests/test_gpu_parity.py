@@ -129,6 +129,32 @@ def test_segmentation_is_bitwise_neutral(mhd, segs):
     assert torch.equal(a.get_state(), b.get_state())
 
 
+@pytest.mark.parametrize("dims,segs", [((48, 40, 36), None), ((40, 36, 36), (8, 12, 12)),
+                                       ((32, 24, 8), None), ((12, 5, 3), None), ((64, 16, 96), (16, 16, 16))])
+def test_fused_z_magnetic_pair_is_bitwise_two_sweeps(mhd, dims, segs):
+    """The two middle z magnetic sweeps of a step in one launch give bitwise
+    the state of two launches: ragged tiles, z shorter than 16 (periodic
+    images of the warm-up wrap more than once), segmented pencils."""
+    st = ic.turbulence(dims, seed=23, dtype=torch.float64, kmin=1.0, kmax=1.0 if min(dims) < 8 else 3.0,
+                       mach=0.5)
+    a = make_box(mhd, st)
+    b = make_box(mhd, st)
+    b.set_fusion(False)
+    if segs:
+        a.set_segments(*segs)
+        b.set_segments(*segs)
+    for _ in range(3):
+        dt = a.cfl_dt(0.7)
+        assert dt == b.cfl_dt(0.7)
+        a.step(dt)
+        b.step(dt)
+        assert torch.equal(a.get_state(), b.get_state())
+    a.run(2, 0.7)
+    b.run(2, 0.7)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert a.time() == b.time()
+
+
 # --------------------------------------------------------------------------
 # full steps on the small workloads: 32^3 Alfven wave and 32^3 shock tube
 
