@@ -68,6 +68,7 @@ def _load():
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_pressure_floor.argtypes = [ctypes.c_double]
+            lib.orc_set_resolution.argtypes = [ctypes.c_double] * 3
             lib.orc_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.orc_set_scheme.restype = ctypes.c_int
             lib.orc_limiter.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -112,6 +113,13 @@ def set_threads(t: int) -> None:
 def set_pressure_floor(p_floor: float) -> None:
     """Optional floor on the gas pressure after each fluid sweep (0 = off)."""
     _load().orc_set_pressure_floor(float(p_floor))
+
+
+def set_resolution(cx: float = 0.0, cy: float = 0.0, cz: float = 0.0) -> None:
+    """Cells per unit length along x, y, z (1/h; 0 = the box's own cell count,
+    the periodic unit cube).  A slab of a larger periodic box keeps the whole
+    box's h along the cut axis this way."""
+    _load().orc_set_resolution(float(cx), float(cy), float(cz))
 
 
 LIMITERS = {"vanleer": 0, "minmod": 1, "superbee": 2}

@@ -38,7 +38,9 @@
  *     half [magnetic_d, fluid_d] for d = z, y, x, every sweep with tau = dt/2;
  *   - CFL: dt = 2 * cfl / max_cells max_d (|v_d| + c_f*) / h_d;
  *   - domain is the periodic unit cube, h_d = 1 / n_d (non-periodic axes: see
- *     the boundaries below).
+ *     the boundaries below); orc_set_resolution gives another number of
+ *     cells per unit length along an axis (a box that is part of a larger
+ *     periodic domain, such as a slab of it).
  *
  * Layout: 8 arrays (rho, m_x, m_y, m_z, e, b_x, b_y, b_z), each nx*ny*nz
  * doubles, flat index i + nx*(j + ny*k).
@@ -57,6 +59,17 @@ enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
  * which the total-energy scheme drives p negative. */
 static double g_pfloor = 0.0;
 void orc_set_pressure_floor(double p_floor) { g_pfloor = p_floor > 0.0 ? p_floor : 0.0; }
+
+/* Cells per unit length along each axis, 1 / h_d (0 = the box's own cell
+ * count n_d: the periodic unit cube).  A slab of nz_s planes cut from a
+ * periodic unit box of nz planes keeps h_z = 1 / nz by giving nz here. */
+static double g_cpl[3] = {0.0, 0.0, 0.0};
+void orc_set_resolution(double cx, double cy, double cz) {
+    g_cpl[0] = cx > 0.0 ? cx : 0.0;
+    g_cpl[1] = cy > 0.0 ? cy : 0.0;
+    g_cpl[2] = cz > 0.0 ? cz : 0.0;
+}
+static double cells_per_length(const int n[3], int d) { return g_cpl[d] > 0.0 ? g_cpl[d] : (double)n[d]; }
 
 /* Boundaries (an extension: the paper's runs are periodic).  An axis is
  * periodic (0, the default), outflow (1) or reflecting (2).  A non-periodic
@@ -342,7 +355,7 @@ void orc_fluid_sweep(const int n[3], double gamma, double *f[8], int d, double t
     if (any_boundary()) orc_fill_ghosts(n, f);
     int t1 = t1_of(d), t2 = t2_of(d);
     int nd = n[d];
-    double h = 1.0 / nd;
+    double h = 1.0 / cells_per_length(n, d);
     int np = n[t1] * n[t2];
     int p;
 #pragma omp parallel for schedule(static)
@@ -400,7 +413,7 @@ void orc_fluid_sweep(const int n[3], double gamma, double *f[8], int d, double t
 void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
     if (any_boundary()) orc_fill_ghosts(n, f);
     int nd = n[d];
-    double hd = 1.0 / nd;
+    double hd = 1.0 / cells_per_length(n, d);
     long N = (long)n[0] * n[1] * n[2];
     int ts[2] = {t1_of(d), t2_of(d)};
     double *E[2];
@@ -441,7 +454,7 @@ void orc_mag_sweep(const int n[3], double *f[8], int d, double tau) {
     /* apply: advection of each b_t, then the constraint on b_d */
     for (k = 0; k < 2; k++) {
         int t = ts[k];
-        double ht = 1.0 / n[t];
+        double ht = 1.0 / cells_per_length(n, t);
         long id;
 #pragma omp parallel for schedule(static)
         for (id = 0; id < N; id++) {
@@ -501,7 +514,7 @@ double orc_cfl_rate(const int n[3], double gamma, double *const f[8]) {
         p = (gamma - 1.0) * (f[EN][id] - kin - 0.5 * b2);
         cf = sqrt((gamma * p + b2) / rho);
         for (a = 0; a < 3; a++) {
-            double ra = (fabs(v[a]) + cf) * n[a];
+            double ra = (fabs(v[a]) + cf) * cells_per_length(n, a);
             if (ra > r) r = ra;
         }
         if (r > rmax) rmax = r;

@@ -399,6 +399,59 @@ def test_one_step_reach_and_sub_block_equivalence(oracle_lib):
     assert np.array_equal(blk[:, H:H + L, H:H + L, H:H + L], sub_block(a, lo, [L] * 3))
 
 
+def test_resolution_scales_like_the_equations(oracle_lib):
+    """The ideal-MHD equations are invariant under x -> x/2, t -> t/2: with
+    twice the cells per unit length on every axis (h halved) and half the
+    timestep, every tau/h of the scheme is unchanged, so the state after a
+    step is bitwise that of the unit box, and the CFL timestep halves
+    exactly.  Giving the box's own cell counts is the default."""
+    n = (16, 12, 20)
+    st = ic.turbulence(n, seed=5, dtype=torch.float64, kmin=1.0, kmax=3.0).numpy().copy()
+    try:
+        dt = oracle.cfl_dt(st, G, 0.7)
+        a = st.copy()
+        oracle.step(a, dt, G)
+        oracle.set_resolution(*n)
+        assert oracle.cfl_dt(st, G, 0.7) == dt
+        b = st.copy()
+        oracle.step(b, dt, G)
+        assert np.array_equal(a, b)
+        oracle.set_resolution(*(2 * c for c in n))
+        assert oracle.cfl_dt(st, G, 0.7) == dt / 2
+        c = st.copy()
+        oracle.step(c, dt / 2, G)
+        assert np.array_equal(a, c)
+    finally:
+        oracle.set_resolution()
+
+
+def test_slab_with_the_whole_box_resolution_reproduces_the_step(oracle_lib):
+    """A slab of planes cut from a periodic box along z, widened by H = 16
+    halo planes at each end (one full step reaches 14 cells), stepped with
+    the whole box's cells per unit length along z and the whole box's dt,
+    reproduces the whole-box step on its own planes bit for bit; the largest
+    CFL rate of the halo-widened slabs is the whole box's."""
+    from tests.parity_util import sub_block
+    n = (24, 20, 64)
+    st = ic.turbulence(n, seed=7, dtype=torch.float64, kmin=1.0, kmax=4.0).numpy().copy()
+    whole = st.copy()
+    dt = oracle.cfl_dt(whole, G, 0.7)
+    rate = oracle.cfl_rate(whole, G)
+    oracle.step(whole, dt, G)
+    H, L = 16, 16
+    rates = []
+    try:
+        oracle.set_resolution(0, 0, n[2])
+        for z0 in range(0, n[2], L):
+            slab = sub_block(st, (0, 0, z0 - H), (n[0], n[1], L + 2 * H))
+            rates.append(oracle.cfl_rate(slab, G))
+            oracle.step(slab, dt, G)
+            assert np.array_equal(slab[:, H:H + L], whole[:, z0:z0 + L])
+    finally:
+        oracle.set_resolution()
+    assert max(rates) == rate
+
+
 # --------------------------------------------------------------------------
 # optional pressure floor (not in the paper; off by default)
 
