@@ -51,7 +51,7 @@ P_FLOOR_ENSEMBLE = 1e-3
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--size", type=int, default=512)
@@ -72,6 +72,9 @@ def parse():
                    help="pencil segment length for every axis (0: the library's choice)")
     p.add_argument("--freezing", choices=["bound", "fast", "pencil"], default="bound",
                    help="freezing speed (the bound is the paper-reading default; fast is an ablation)")
+    p.add_argument("--shard", action="store_true",
+                   help="one box of --size^3 cut into z-slabs over the ranks (strong scaling; the default "
+                        "for several GPUs is one box per rank, weak scaling)")
     p.add_argument("--fusion", type=int, choices=[0, 1], default=1,
                    help="1: the two middle z magnetic sweeps of a step as one launch (bitwise the same state)")
     p.add_argument("--bc", default="",
@@ -209,6 +212,26 @@ def measured_issue(kernel: str):
     return r.get("warp_instructions_per_cell")
 
 
+def precision_record():
+    """Per-field error of the FP32 path against the FP64 oracle
+    (tests/precision_report.py --full --json), if it was taken on the current
+    kernel source (else None): the worst max error of every field over all
+    cases, and the 512^3 sampled case in full."""
+    path = os.path.join(ROOT, "profiles", "precision.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    cases = rec.get("cases", {})
+    big = {k: v for k, v in cases.items() if k.startswith("turbulence 512^3")}
+    return {"fields": rec["fields"], "worst_max_over_cases": rec.get("worst_max"),
+            "cases": len(cases), "turbulence_512": next(iter(big.values()), None),
+            "source": "profiles/precision.json", "command": rec.get("command")}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -262,7 +285,13 @@ def ensemble_leg(args, world=1):
     torch.cuda.synchronize()
     secs = max_over_ranks([e0.elapsed_time(e1) / 1e3], world)[0]
     invalid = int(np.sum(ens.cfl_dt_safe(args.cfl) == 0.0))
+    peak, peak_kind = peaks()
+    gbs = STEP_BYTES * cells * args.ensemble_steps / secs / 1e9
     out = {"value": whole_job_rate(cells * args.ensemble_steps, world, secs), "unit": UNIT, "boxes": len(dims),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "model_bytes_per_cell": STEP_BYTES, "peak_kind": peak_kind,
+                        "note": "full-step model (6 sweeps x read + write of 8 fields) over all boxes; "
+                                f"state {2 * 32 * cells / 1e9:.1f} GB in two copies > L2"},
            "cells": cells, "steps": args.ensemble_steps, "ms_per_step": 1e3 * secs / args.ensemble_steps,
            "tuning": {"xpath": xp, "segdiv": sd}, "pressure_floor": P_FLOOR_ENSEMBLE,
            "invalid_boxes": invalid,
@@ -458,11 +487,11 @@ def run_ours(args, rank, world, local):
 
     box.run(args.warmup, args.cfl)
     box.cfl_dt(args.cfl)               # raises if the state went invalid
+    start = box.get_state()            # the traced pass below repeats the same steps
     # 12 sweeps, step control, up to 6 transposes (x path 3); with ghost
     # layers a fill per non-periodic axis before every sweep; with the
     # per-pencil freezing speed a reduction pass before every fluid sweep
     launches_per_step = 19 + 12 * len(bcs) + (6 if args.freezing == "pencil" else 0)  # + speed passes
-    box.profile(args.steps * launches_per_step + 16)
 
     uuid = None
     try:
@@ -485,8 +514,16 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     secs = e0.elapsed_time(e1) / 1e3
     box.cfl_dt(args.cfl)               # state still valid after the timed run
+    # per-launch figures from a second, traced pass of the same steps from
+    # the same state (CUDA events around every launch; the timed pass above
+    # has none)
+    box.set_state(start)
+    del start
+    box.profile(args.steps * launches_per_step + 16)
+    box.run(args.steps, args.cfl)
     prof = box.profile_read()
     box.profile(0)
+    box.cfl_dt(args.cfl)
     secs = max_over_ranks([secs], world)[0]
     value = whole_job_rate(N * args.steps, world, secs)
 
@@ -626,6 +663,7 @@ def run_ours(args, rank, world, local):
                                  "frac": STEP_BYTES * N * args.steps / secs / 1e9 / peak},
                "per_kernel": per_kernel,
                "gpu_launches": launches,
+               "precision": precision_record(),
                "clocks": clk,
                "e2e": e2e,
                "diagnostics": diag,
@@ -639,11 +677,73 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def run_shard(args, rank, world, local):
+    """One periodic box of --size^3 cells cut into z-slabs, one per rank (GPU):
+    every step exchanges 16 halo planes of the 8 fields with both z
+    neighbours (NCCL), agrees on the CFL timestep (allreduce min) and runs
+    the library's step on the slab box.  Whole-box cell-updates/s over the
+    slowest rank's time."""
+    import torch
+
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    from paper_1004_1680_gb300 import slab
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    n = args.size
+    L = slab.SlabLayout((n, n, n), world, rank)
+    st = ic.turbulence((n, n, n), seed=args.seed, mach=args.mach, beta=args.beta, device="cuda",
+                       dtype=torch.float32)
+    box = slab.make_box(L)
+    box.set_state(L.cut(st))
+    del st
+    torch.cuda.empty_cache()
+    ex = slab.SlabExchange(L)
+    get = box.get_planes
+    put = box.set_planes
+
+    def step():
+        ex.exchange(get, put)
+        box.step(ex.agree_dt(box.cfl_dt(args.cfl), device="cuda"))
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(None)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    clk = clocks.stop()
+    secs = max_over_ranks([secs], world)[0]
+    if rank == 0:
+        out = {"metric": METRIC, "value": n ** 3 * args.steps / secs, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"decaying MHD turbulence {n}^3, periodic, one box in z-slabs",
+                          "n": n, "seed": args.seed, "cfl": args.cfl,
+                          "slab": {"own_planes": L.own, "halo_planes": L.halo, "local_dims": L.local_dims},
+                          "parallelism": f"z-slabs x{world}",
+                          "timing": "wall clock around the steps (host-driven exchange), max over ranks"},
+               "clocks": clk, "e2e": None}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    box.close()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.shard:
+        return run_shard(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -120,6 +120,36 @@ int mhd_time(const mhd_t *m, double *t);
  * the sweeps one by one. */
 int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
 
+/* ---- Boxes that are part of a larger periodic domain ------------------
+ * Section II.B evolves a periodic unit box (h_d = 1/n_d).  Sharding that box
+ * across GPUs (the paper's future-work item: MPI across nodes, Section VI)
+ * cuts it into slabs along z; each slab box holds its own planes plus halo
+ * planes copied from its neighbours.  These calls let one mhd_t be such a
+ * slab.  (Extensions: the paper has no counterpart.) */
+
+/* Cells per unit length along x, y, z, i.e. 1/h_d of the sweeps (tau/h_d)
+ * and of the CFL rate ((|v_d| + c_f*)/h_d).  0 (the default) means n_d, the
+ * unit box.  A slab of a box of nz planes passes cz = nz so that its h_z is
+ * the whole box's.  Recomputes the CFL rate.  MHD_E_ARG for a negative or
+ * non-finite value. */
+int mhd_set_resolution(mhd_t *m, double cx, double cy, double cz);
+
+/* Cells [lo, hi) along axis (0..2) are the box's own; the others are halo
+ * copies of cells that another box owns.  The CFL rate (mhd_cfl_dt, the
+ * device-resident timestep of mhd_run) covers own cells only (and, on a
+ * non-periodic axis, interior cells only), so that the largest rate over all
+ * slabs is the whole box's.  Default: the whole box.  Recomputes the rate.
+ * MHD_E_ARG unless 0 <= lo < hi <= n_axis. */
+int mhd_set_interior(mhd_t *m, int axis, int lo, int hi);
+
+/* Copy the z-planes z0 .. z0+nplanes-1 of all 8 fields between the box and
+ * f[q] (nplanes*ny*nx floats each, layout as mhd_set_state): into_box = 1
+ * writes the box, 0 reads it.  on_device: f[q] are device pointers (stream
+ * ordered, asynchronous); otherwise host pointers (synchronises).  The CFL
+ * rate is left as it was (halo planes are not own cells).  MHD_E_ARG for
+ * planes outside the box or a NULL pointer. */
+int mhd_copy_planes(mhd_t *m, int z0, int nplanes, float *const f[8], int into_box, int on_device);
+
 /* Kernel fusion of the schedule (not a change of the method): with on = 1
  * (the default) the two magnetic z sweeps in the middle of a full step,
  * which follow each other with the same step tau = dt/2, run as one launch

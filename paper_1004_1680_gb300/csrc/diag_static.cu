@@ -51,13 +51,7 @@ extern "C" int mhd_diagnostics_static(int nx, int ny, int nz, double gamma, cons
   if (!f || !out) return mhd::set_error(MHD_E_ARG, "mhd_diagnostics_static", "null argument");
   for (int q = 0; q < 8; q++)
     if (!f[q]) return mhd::set_error(MHD_E_ARG, "mhd_diagnostics_static", "null field pointer");
-  mhd::Box box;
-  box.n[0] = nx;
-  box.n[1] = ny;
-  box.n[2] = nz;
-  box.stride[0] = 1;
-  box.stride[1] = nx;
-  box.stride[2] = (long long)nx * ny;
+  const mhd::Box box = mhd::make_box(nx, ny, nz);
   if (mhd::diag_blocks(box) > kStaticDiagBlocks)
     return mhd::set_error(MHD_E_ARG, "mhd_diagnostics_static", "partials exceed the static scratch");
   double* scratch = nullptr;

@@ -72,6 +72,9 @@ struct mhd_s {
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   int fuse = 1;         // 1: the two z magnetic sweeps of a step run as one launch
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
+  double cpl[3] = {0.0, 0.0, 0.0};  // cells per unit length per physical axis (0: n, the unit box)
+  int own_lo[3] = {0, 0, 0};        // own cells [own_lo, own_hi) per physical axis (the others are
+  int own_hi[3] = {1 << 30, 1 << 30, 1 << 30};  // halo copies of another box's cells)
   float* pencil_c = nullptr;  // freezing 2: per-pencil speeds of the sweep being run (2 x N / min n)
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
@@ -101,6 +104,34 @@ namespace {
 // L2 (direct x sweeps read 32 different lines per warp and position, which
 // only L2 can absorb).
 int auto_xpath(const mhd_s* m) { return m->N * 32LL > (64LL << 20) ? 2 : 1; }
+
+// Cells per unit length of each layout's axes (the exchanged layouts permute
+// the physical axes).
+void set_geometry(mhd_s* m) {
+  float ih[3];
+  for (int d = 0; d < 3; d++) ih[d] = (float)(m->cpl[d] > 0.0 ? m->cpl[d] : (double)m->n[d]);
+  for (int d = 0; d < 3; d++) m->box.ih[d] = ih[d];
+  m->tbox.ih[0] = ih[1];
+  m->tbox.ih[1] = ih[0];
+  m->tbox.ih[2] = ih[2];
+  m->zbox.ih[0] = ih[2];
+  m->zbox.ih[1] = ih[1];
+  m->zbox.ih[2] = ih[0];
+}
+
+// Kernel axis of physical axis p in the current layout.
+int kernel_axis_of(const mhd_s* m, int p) {
+  if (m->layout == 1 && p < 2) return 1 - p;
+  if (m->layout == 2 && p != 1) return 2 - p;
+  return p;
+}
+
+// Cells along physical axis p whose CFL rate counts: the own cells, less
+// the ghost layers of a non-periodic axis.
+void rate_window(const mhd_s* m, int p, int* lo, int* hi) {
+  *lo = std::max(m->bc[p] ? mhd::kGhost : 0, m->own_lo[p]);
+  *hi = std::min(m->bc[p] ? m->n[p] - mhd::kGhost : m->n[p], m->own_hi[p]);
+}
 
 // Segment length along each axis.  Splitting pencils into segments adds 7
 // cells of warm-up per segment but gives the GPU more threads.  First split
@@ -300,13 +331,7 @@ int state_rate(mhd_s* m, unsigned* rate) {
   if (int rc = fill_ghosts(m)) return rc;
   const mhd::Box& b = m->layout == 2 ? m->zbox : (m->layout ? m->tbox : m->box);
   mhd::CellRange r;
-  for (int a = 0; a < 3; a++) {
-    int k = a;
-    if (m->layout == 1 && a < 2) k = 1 - a;
-    if (m->layout == 2 && a != 1) k = 2 - a;
-    r.lo[k] = m->bc[a] ? mhd::kGhost : 0;
-    r.hi[k] = m->bc[a] ? b.n[k] - mhd::kGhost : b.n[k];
-  }
+  for (int a = 0; a < 3; a++) rate_window(m, a, &r.lo[kernel_axis_of(m, a)], &r.hi[kernel_axis_of(m, a)]);
   CK(cudaMemsetAsync(rate, 0, sizeof(unsigned), m->stream));
   const float* cf[8];
   field_ptrs(m, cf);
@@ -335,14 +360,8 @@ int fluid(mhd_s* m, int d, bool rate) {
   a.seg = m->seg[d];
   a.lim = m->lim;
   a.fast = m->fast;
-  for (int p = 0; p < 3; p++) {  // the fused rate covers the interior cells
-    if (!m->bc[p]) continue;
-    int k = p;
-    if (m->layout == 1 && p < 2) k = 1 - p;
-    if (m->layout == 2 && p != 1) k = 2 - p;
-    a.rate_lo[k] = mhd::kGhost;
-    a.rate_hi[k] = box->n[k] - mhd::kGhost;
-  }
+  for (int p = 0; p < 3; p++)  // the fused rate covers the interior, own cells
+    rate_window(m, p, &a.rate_lo[kernel_axis_of(m, p)], &a.rate_hi[kernel_axis_of(m, p)]);
   if (m->fast == 2) {  // per-pencil freezing speeds before the sweep
     a.pencil_c = m->pencil_c;
     if ((rc = traced(m, MHD_K_CONTROL, [&] {
@@ -512,9 +531,7 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   m->box.n[0] = nx;
   m->box.n[1] = ny;
   m->box.n[2] = nz;
-  m->box.stride[0] = 1;
-  m->box.stride[1] = nx;
-  m->box.stride[2] = (long long)nx * ny;
+  m->box = mhd::make_box(nx, ny, nz);
   cudaError_t e = mhd::prepare_mag_kernels();
   if (e != cudaSuccess) {
     cuda_fail(e, "kernel attributes");
@@ -543,6 +560,7 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   m->zbox.stride[0] = 1;
   m->zbox.stride[1] = nz;
   m->zbox.stride[2] = (long long)nz * ny;
+  set_geometry(m);
   m->xpath = auto_xpath(m);
   {
     int dev = 0;
@@ -774,6 +792,49 @@ int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
   }
   m->lim = limiter;
   m->fast = freezing;
+  return MHD_OK;
+}
+
+int mhd_set_resolution(mhd_t* m, double cx, double cy, double cz) {
+  if (!check_box(m)) return MHD_E_ARG;
+  const double c[3] = {cx, cy, cz};
+  for (int d = 0; d < 3; d++)
+    if (!(c[d] >= 0.0) || !std::isfinite(c[d]) || c[d] > 3.0e38) return fail(MHD_E_ARG, "cells per unit length must be finite and >= 0");
+  if (int rc = join_pipeline(m)) return rc;
+  for (int d = 0; d < 3; d++) m->cpl[d] = c[d];
+  set_geometry(m);
+  return state_rate(m, &m->sc->rate[m->rcur]);
+}
+
+int mhd_set_interior(mhd_t* m, int axis, int lo, int hi) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (axis < 0 || axis > 2 || lo < 0 || hi > m->n[axis] || lo >= hi)
+    return fail(MHD_E_ARG, "need 0 <= lo < hi <= n along the axis");
+  if (int rc = join_pipeline(m)) return rc;
+  m->own_lo[axis] = lo;
+  m->own_hi[axis] = hi;
+  return state_rate(m, &m->sc->rate[m->rcur]);
+}
+
+int mhd_copy_planes(mhd_t* m, int z0, int nplanes, float* const f[8], int into_box, int on_device) {
+  if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  for (int q = 0; q < 8; q++)
+    if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  if (z0 < 0 || nplanes < 0 || z0 + nplanes > m->n[2]) return fail(MHD_E_ARG, "planes outside the box");
+  if (m->layout) return fail(MHD_E_ARG, "internal: state left in the exchanged layout");
+  if (int rc = join_pipeline(m)) return rc;
+  const size_t plane = (size_t)m->n[0] * m->n[1];
+  const size_t bytes = sizeof(float) * plane * nplanes;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                        : (into_box ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  for (int q = 0; q < 8; q++) {
+    float* boxp = m->cur[q] + plane * z0;
+    if (into_box)
+      CK(cudaMemcpyAsync(boxp, f[q], bytes, kind, m->stream));
+    else
+      CK(cudaMemcpyAsync(f[q], boxp, bytes, kind, m->stream));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
   return MHD_OK;
 }
 

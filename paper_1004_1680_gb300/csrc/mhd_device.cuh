@@ -15,6 +15,7 @@ enum Field { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
 struct Box {
   int n[3];             // cells along x, y, z
   long long stride[3];  // flat-index stride of a unit step along x, y, z
+  float ih[3];          // cells per unit length, 1/h, along x, y, z (n: the unit box)
 };
 
 __host__ __device__ inline int wrapi(int i, int n) {
@@ -223,16 +224,16 @@ __device__ __forceinline__ float bound_speed(const V5& u, float bd, float2 bt, f
 // frame (v, b indexed by axis).  Invalid cells (NaN, rho <= 0, p <= 0) report
 // +inf so that a max-reduction flags them.  Explicitly rounded (see below).
 __device__ __forceinline__ float cell_rate(float rho, const float m[3], float e, const float b[3],
-                                           float gamma, const int n[3]) {
+                                           float gamma, const float ih[3]) {
   const float rinv = fast_rcp(rho);
   const float v0 = __fmul_rn(m[0], rinv), v1 = __fmul_rn(m[1], rinv), v2 = __fmul_rn(m[2], rinv);
   const float b2 = __fmaf_rn(b[0], b[0], __fmaf_rn(b[1], b[1], __fmul_rn(b[2], b[2])));
   const float kin = __fmul_rn(0.5f, __fmaf_rn(m[0], v0, __fmaf_rn(m[1], v1, __fmul_rn(m[2], v2))));
   const float p = __fmul_rn(gamma - 1.f, __fmaf_rn(-0.5f, b2, __fsub_rn(e, kin)));
   const float cf = fast_sqrt(__fmul_rn(__fmaf_rn(gamma, p, b2), rinv));
-  const float r = fmaxf(fmaxf(__fmul_rn(__fadd_rn(fabsf(v0), cf), (float)n[0]),
-                              __fmul_rn(__fadd_rn(fabsf(v1), cf), (float)n[1])),
-                        __fmul_rn(__fadd_rn(fabsf(v2), cf), (float)n[2]));
+  const float r = fmaxf(fmaxf(__fmul_rn(__fadd_rn(fabsf(v0), cf), ih[0]),
+                              __fmul_rn(__fadd_rn(fabsf(v1), cf), ih[1])),
+                        __fmul_rn(__fadd_rn(fabsf(v2), cf), ih[2]));
   const bool ok = (rho > 0.f) && (p > 0.f) && (r <= 3.0e38f);
   return ok ? r : __int_as_float(0x7f800000);
 }

@@ -87,6 +87,21 @@ struct TransposeArgs {
   int nblocks = 0;
 };
 
+// A box of nx x ny x nz cells, x fastest, on the periodic unit cube.
+inline Box make_box(int nx, int ny, int nz) {
+  Box b;
+  b.n[0] = nx;
+  b.n[1] = ny;
+  b.n[2] = nz;
+  b.stride[0] = 1;
+  b.stride[1] = nx;
+  b.stride[2] = (long long)nx * ny;
+  b.ih[0] = (float)nx;
+  b.ih[1] = (float)ny;
+  b.ih[2] = (float)nz;
+  return b;
+}
+
 // Resolved geometry of the block a kernel is running: the box as the kernel
 // sees it, the block's coordinates, segment, step and CFL accumulator, and
 // the offset of the box in the field arrays.
@@ -113,6 +128,9 @@ __device__ __forceinline__ BlockGeom block_geom(const EnsArgs& e, const Box& box
     g.box.stride[0] = 1;
     g.box.stride[1] = n0;
     g.box.stride[2] = (long long)n0 * n1;
+    g.box.ih[0] = (float)n0;  // ensemble boxes are periodic unit boxes
+    g.box.ih[1] = (float)n1;
+    g.box.ih[2] = (float)eb.n[2];
     g.bx = it.y;
     g.by = it.z;
     g.bz = it.w;

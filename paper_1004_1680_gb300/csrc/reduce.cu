@@ -44,7 +44,7 @@ __global__ void cfl_rate_kernel(const float* __restrict__ rho, const float* __re
         b[0] = 0.5f * (__ldg(bx + c) + __ldg(bx + (i + 1 < nx ? c + 1 : c - (nx - 1))));
         b[1] = 0.5f * (__ldg(by + c) + __ldg(by + c + yoff));
         b[2] = 0.5f * (__ldg(bz + c) + __ldg(bz + c + zoff));
-        rmax = fmaxf(rmax, cell_rate(__ldg(rho + c), m, __ldg(en + c), b, gamma, box.n));
+        rmax = fmaxf(rmax, cell_rate(__ldg(rho + c), m, __ldg(en + c), b, gamma, box.ih));
       }
     }
     j += dj;

@@ -111,7 +111,7 @@ fluid_sweep_kernel(FluidArgs a) {
 
   const float gamma = a.gamma;
   const float tau = G.tau;
-  const float c_full = tau * (float)nD;  // tau / h_D
+  const float c_full = tau * G.box.ih[D];  // tau / h_D
   const float c_half = 0.5f * c_full;    // tau / (2 h_D)
   const int s0 = G.bz * G.seg;
   const int s1 = s0 + G.seg;
@@ -224,7 +224,7 @@ fluid_sweep_kernel(FluidArgs a) {
           float m[3], bg[3];
           m[D] = o[1]; m[X::T1] = o[2]; m[X::T2] = o[3];
           bg[D] = bc3[0]; bg[X::T1] = bc3[1]; bg[X::T2] = bc3[2];
-          rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, G.box.n));
+          rmax = fmaxf(rmax, cell_rate(o[0], m, o[4], bg, gamma, G.box.ih));
         }
       }
       if (RATE || FLOOR) {  // window of b_c: bc2 = b_c(t-1), bc3 = b_c(t-2) for the next step

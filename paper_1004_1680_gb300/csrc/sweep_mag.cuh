@@ -149,10 +149,10 @@ mag_sweep_kernel(MagArgs a) {
   float* xw = xs_dyn + w * kMXTiles * kMXTile;
 
   const float tau = G.tau;
-  const float c_full = tau * (float)nD;        // tau / h_D
+  const float c_full = tau * G.box.ih[D];      // tau / h_D
   const float c_half = 0.5f * c_full;
-  const float kA = tau * (float)nA;             // tau / h_A
-  const float kO = tau * (float)nO;             // tau / h_O
+  const float kA = tau * G.box.ih[X::A];       // tau / h_A
+  const float kO = tau * G.box.ih[X::O];       // tau / h_O
   const int s0 = G.bz * G.seg;
   const int s1 = s0 + G.seg;
   // positions s0-4 .. s1+2 feed outputs s0 .. s1-1 (3 cells of lag, 1 extra
@@ -360,10 +360,10 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
   float* __restrict__ o_bD = a.out[D] + G.off;
 
   const float tau = G.tau;
-  const float c_full = tau * (float)nD;        // tau / h_D
+  const float c_full = tau * G.box.ih[D];      // tau / h_D
   const float c_half = 0.5f * c_full;
-  const float kA = tau * (float)nA;             // tau / h_A
-  const float kO = tau * (float)nO;             // tau / h_O
+  const float kA = tau * G.box.ih[X::A];       // tau / h_A
+  const float kO = tau * G.box.ih[X::O];       // tau / h_O
   const int s0 = G.bz * G.seg;
   const int s1 = s0 + G.seg;
   // each pass lags its input by 3 positions: positions s0-4NP .. s1+3NP-1

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(128) pencil_speed_kernel(FluidArgs a, float* _
   const float* __restrict__ b1 = a.in[BX + X::T1];
   const float* __restrict__ b2 = a.in[BX + X::T2];
   const float gamma = a.gamma;
-  const float c_half = 0.5f * (__ldg(a.tau) * (float)nD);  // tau / (2 h_D), as in the sweep
+  const float c_half = 0.5f * (__ldg(a.tau) * a.box.ih[D]);  // tau / (2 h_D), as in the sweep
 
   // state and cell-centred field of position i of the pencil (periodic), in
   // the sweep's local frame

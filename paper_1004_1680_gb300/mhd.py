@@ -47,6 +47,9 @@ SIGNATURES = {
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_set_fusion": (_I, [_P, _I]),
+    "mhd_set_resolution": (_I, [_P, _D, _D, _D]),
+    "mhd_set_interior": (_I, [_P, _I, _I, _I]),
+    "mhd_copy_planes": (_I, [_P, _I, _I, _PP, _I, _I]),
     "mhd_set_pressure_floor": (_I, [_P, _D]),
     "mhd_set_scheme": (_I, [_P, _I, _I]),
     "mhd_set_boundary": (_I, [_P, _I, _I]),
@@ -253,6 +256,32 @@ class Box:
     def fill_ghosts(self):
         """Refill the ghost layers of the non-periodic axes now."""
         _check(self.lib.mhd_fill_ghosts(self.h))
+
+    def set_resolution(self, cx: float = 0.0, cy: float = 0.0, cz: float = 0.0):
+        """Cells per unit length along x, y, z (1/h; 0 = the box's own cell
+        count, the unit box)."""
+        _check(self.lib.mhd_set_resolution(self.h, float(cx), float(cy), float(cz)))
+
+    def set_interior(self, axis: int, lo: int, hi: int):
+        """Cells [lo, hi) along axis are this box's own (the CFL rate covers
+        them only); the rest are halo copies."""
+        _check(self.lib.mhd_set_interior(self.h, int(axis), int(lo), int(hi)))
+
+    def get_planes(self, z0: int, nplanes: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """z-planes z0 .. z0+nplanes-1 of the 8 fields as a (8, nplanes, ny, nx)
+        float32 CUDA tensor (stream ordered)."""
+        nx, ny, nz = self.n
+        if out is None:
+            out = torch.empty((8, nplanes, ny, nx), dtype=torch.float32, device="cuda")
+        _check(self.lib.mhd_copy_planes(self.h, int(z0), int(nplanes), _field_ptrs(out), 0, 1))
+        return out
+
+    def set_planes(self, z0: int, planes: torch.Tensor):
+        """Write a (8, nplanes, ny, nx) float32 CUDA tensor into z-planes
+        z0 .. z0+nplanes-1 (stream ordered)."""
+        if not planes.is_cuda or planes.dtype != torch.float32 or not planes.is_contiguous():
+            raise ValueError("planes must be a contiguous float32 CUDA tensor")
+        _check(self.lib.mhd_copy_planes(self.h, int(z0), int(planes.shape[1]), _field_ptrs(planes), 1, 1))
 
     def set_fusion(self, on: bool):
         """Run the two middle z magnetic sweeps of a step as one launch (on,
