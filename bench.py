@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--shard", action="store_true",
                    help="one box of --size^3 cut into z-slabs over the ranks (strong scaling; the default "
                         "for several GPUs is one box per rank, weak scaling)")
+    p.add_argument("--fp64", action="store_true",
+                   help="time the FP64 path (mhd_create_f64, an ablation) instead of the FP32 one")
     p.add_argument("--fusion", type=int, choices=[0, 1], default=1,
                    help="1: the two middle z magnetic sweeps of a step as one launch (bitwise the same state)")
     p.add_argument("--bc", default="",
@@ -677,6 +679,47 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def run_fp64(args, rank, world, local):
+    """The FP64 path (an ablation of the paper's FP32 computation): the same
+    workload and step, every operation in IEEE double; the timestep through
+    the host (one synchronisation per step).  CUDA events around the steps."""
+    import torch
+
+    from paper_1004_1680_gb300 import initial_conditions as ic
+    from paper_1004_1680_gb300 import mhd
+    torch.cuda.set_device(local)
+    n = args.size
+    st = ic.turbulence((n, n, n), seed=args.seed, mach=args.mach, beta=args.beta, device="cuda",
+                       dtype=torch.float64)
+    box = mhd.Box64(n, n, n)
+    box.set_state(st)
+    del st
+    torch.cuda.empty_cache()
+    box.run(args.warmup, args.cfl)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(None)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    box.run(args.steps, args.cfl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    clk = clocks.stop()
+    if rank == 0:
+        out = {"metric": METRIC, "value": n ** 3 * args.steps / secs, "unit": UNIT, "n_gpus": 1,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": f"decaying MHD turbulence {n}^3, periodic, FP64 path", "n": n,
+                          "seed": args.seed, "cfl": args.cfl},
+               "clocks": clk, "e2e": None}
+        print(json.dumps(out), flush=True)
+    box.close()
+    return 0
+
+
 def run_shard(args, rank, world, local):
     """One periodic box of --size^3 cells cut into z-slabs, one per rank (GPU):
     every step exchanges 16 halo planes of the 8 fields with both z
@@ -744,6 +787,8 @@ def main():
         return run_reference(args, rank, world)
     if args.shard:
         return run_shard(args, rank, world, local)
+    if args.fp64:
+        return run_fp64(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -120,6 +120,28 @@ int mhd_time(const mhd_t *m, double *t);
  * the sweeps one by one. */
 int mhd_sweep(mhd_t *m, int axis, int kind, double tau);
 
+/* ---- FP64 boxes -----------------------------------------------------------
+ * The same grid update computed in FP64 on the GPU (an ablation: the paper
+ * computes in FP32, Section III): the scheme of Section II.B with every
+ * operation an IEEE double operation rounded once.  FP64 arithmetic runs at
+ * a small fraction of the FP32 rate on this GPU; these kernels favour
+ * clarity (one thread per whole pencil, the magnetic edge fluxes through a
+ * scratch array, the timestep through the host).  An FP64 box supports
+ * mhd_set_stream, mhd_cfl_dt, mhd_step, mhd_run (one host synchronisation
+ * per step), mhd_time, mhd_sweep, mhd_set_resolution and mhd_destroy, and
+ * the paper's scheme only; the other calls return MHD_E_ARG.
+ *
+ * Create: periodic box, any nx, ny, nz >= 1 (at most 2^31 - 1 cells), gamma
+ * > 1; allocates 18 N doubles (two state copies and the edge fluxes) on the
+ * current device.  NULL on failure (mhd_last_error). */
+mhd_t *mhd_create_f64(int nx, int ny, int nz, double gamma);
+
+/* Copy the 8 FP64 fields in / out (layout of mhd_set_state; host or device
+ * pointers, caller-owned).  set_state_f64 resets the time.  get_state_f64
+ * synchronises.  MHD_E_ARG for a NULL pointer or a box that is not FP64. */
+int mhd_set_state_f64(mhd_t *m, const double *const f[8], int on_device);
+int mhd_get_state_f64(const mhd_t *m, double *const f[8], int on_device);
+
 /* ---- Boxes that are part of a larger periodic domain ------------------
  * Section II.B evolves a periodic unit box (h_d = 1/n_d).  Sharding that box
  * across GPUs (the paper's future-work item: MPI across nodes, Section VI)

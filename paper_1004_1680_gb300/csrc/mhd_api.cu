@@ -79,6 +79,14 @@ struct mhd_s {
   Scalars* sc = nullptr;
   double* diag_partial = nullptr;
   int rcur = 0;
+  // FP64 boxes (mhd_create_f64): the state in double, whole-pencil kernels
+  bool f64 = false;
+  double* arena64 = nullptr;
+  double* cur64[8];
+  double* spare64[8];
+  double* e64 = nullptr;                 // edge fluxes of a magnetic sweep (2 N)
+  unsigned long long* rate64 = nullptr;  // CFL rate (double bits)
+  double time64 = 0.0;
   cudaStream_t stream = nullptr;
   int seg[3];
   int sms = 0;          // multiprocessors of the device (segment choice)
@@ -492,6 +500,83 @@ int run_steps(mhd_s* m, int nsteps, double cfl) {
   return ensure_layout(m, 0);  // consecutive steps share their x-sweep layout
 }
 
+// ---- FP64 boxes ----------------------------------------------------------
+
+int fluid64(mhd_s* m, int d, double tau) {
+  mhd::Fluid64Args a;
+  for (int q = 0; q < 8; q++) {
+    a.in[q] = m->cur64[q];
+    a.out[q] = m->spare64[q];
+  }
+  for (int k = 0; k < 3; k++) {
+    a.n[k] = m->n[k];
+    a.ih[k] = m->cpl[k] > 0.0 ? m->cpl[k] : (double)m->n[k];
+  }
+  a.gamma = m->gamma;
+  a.tau = tau;
+  CK(mhd::launch_fluid64(d, a, m->stream));
+  for (int q = 0; q < 5; q++) std::swap(m->cur64[q], m->spare64[q]);
+  return MHD_OK;
+}
+
+int magnetic64(mhd_s* m, int d, double tau) {
+  mhd::Mag64Args a;
+  for (int q = 0; q < 8; q++) {
+    a.in[q] = m->cur64[q];
+    a.out[q] = m->spare64[q];
+  }
+  a.E[0] = m->e64;
+  a.E[1] = m->e64 + m->N;
+  for (int k = 0; k < 3; k++) {
+    a.n[k] = m->n[k];
+    a.ih[k] = m->cpl[k] > 0.0 ? m->cpl[k] : (double)m->n[k];
+  }
+  a.tau = tau;
+  CK(mhd::launch_mag64(d, a, m->stream));
+  for (int q = 5; q < 8; q++) std::swap(m->cur64[q], m->spare64[q]);
+  return MHD_OK;
+}
+
+// the schedule of Section II.B, every sweep with tau = dt/2
+int full_step64(mhd_s* m, double dt) {
+  const double tau = 0.5 * dt;
+  int rc;
+  for (int d = 0; d < 3; d++) {
+    if ((rc = fluid64(m, d, tau))) return rc;
+    if ((rc = magnetic64(m, d, tau))) return rc;
+  }
+  for (int d = 2; d >= 0; d--) {
+    if ((rc = magnetic64(m, d, tau))) return rc;
+    if ((rc = fluid64(m, d, tau))) return rc;
+  }
+  return MHD_OK;
+}
+
+int cfl_dt64(mhd_s* m, double cfl, double* dt) {
+  double ih[3];
+  for (int k = 0; k < 3; k++) ih[k] = m->cpl[k] > 0.0 ? m->cpl[k] : (double)m->n[k];
+  CK(cudaMemsetAsync(m->rate64, 0, sizeof(unsigned long long), m->stream));
+  const double* cf[8];
+  for (int q = 0; q < 8; q++) cf[q] = m->cur64[q];
+  CK(mhd::launch_cfl64(cf, m->n, ih, m->gamma, m->rate64, m->stream));
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, m->rate64, sizeof bits, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  double r;
+  std::memcpy(&r, &bits, sizeof r);
+  if (!(r > 0.0) || !std::isfinite(r)) {
+    *dt = 0.0;
+    return fail(MHD_E_STATE, "invalid state: NaN, rho <= 0 or p <= 0 in some cell");
+  }
+  *dt = 2.0 * cfl / r;
+  return MHD_OK;
+}
+
+// calls that FP32 boxes only support
+int fp32_only(const mhd_t* m) {
+  return m->f64 ? fail(MHD_E_ARG, "not available for FP64 boxes (mhd_create_f64)") : MHD_OK;
+}
+
 bool check_box(const mhd_t* m) {
   if (!m) {
     fail(MHD_E_ARG, "null mhd_t");
@@ -583,8 +668,74 @@ mhd_t* mhd_create(int nx, int ny, int nz, double gamma) {
   return m;
 }
 
+mhd_t* mhd_create_f64(int nx, int ny, int nz, double gamma) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(gamma > 1.0)) {
+    fail(MHD_E_ARG, "need nx, ny, nz >= 1 and gamma > 1");
+    return nullptr;
+  }
+  const long long N = (long long)nx * ny * nz;
+  if (N >= (1LL << 31)) {
+    fail(MHD_E_ARG, "box too large: a field must hold fewer than 2^31 cells");
+    return nullptr;
+  }
+  mhd_s* m = new (std::nothrow) mhd_s;
+  if (!m) {
+    fail(MHD_E_OOM, "host allocation failed");
+    return nullptr;
+  }
+  m->n[0] = nx;
+  m->n[1] = ny;
+  m->n[2] = nz;
+  m->gamma = gamma;
+  m->N = N;
+  m->box = mhd::make_box(nx, ny, nz);
+  m->f64 = true;
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->arena64, sizeof(double) * (size_t)N * 18)) != cudaSuccess ||
+      (e = cudaMalloc(&m->rate64, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMemset(m->arena64, 0, sizeof(double) * (size_t)N * 18)) != cudaSuccess) {
+    cuda_fail(e, "mhd_create_f64");
+    cudaFree(m->arena64);
+    cudaFree(m->rate64);
+    delete m;
+    return nullptr;
+  }
+  for (int q = 0; q < 8; q++) {
+    m->cur64[q] = m->arena64 + (size_t)N * q;
+    m->spare64[q] = m->arena64 + (size_t)N * (8 + q);
+  }
+  m->e64 = m->arena64 + (size_t)N * 16;
+  return m;
+}
+
+int mhd_set_state_f64(mhd_t* m, const double* const f[8], int on_device) {
+  if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  if (!m->f64) return fail(MHD_E_ARG, "not an FP64 box (mhd_create_f64)");
+  for (int q = 0; q < 8; q++)
+    if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  for (int q = 0; q < 8; q++)
+    CK(cudaMemcpyAsync(m->cur64[q], f[q], sizeof(double) * (size_t)m->N,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+  m->time64 = 0.0;
+  return MHD_OK;
+}
+
+int mhd_get_state_f64(const mhd_t* m, double* const f[8], int on_device) {
+  if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  if (!m->f64) return fail(MHD_E_ARG, "not an FP64 box (mhd_create_f64)");
+  for (int q = 0; q < 8; q++)
+    if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
+  for (int q = 0; q < 8; q++)
+    CK(cudaMemcpyAsync(f[q], m->cur64[q], sizeof(double) * (size_t)m->N,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return MHD_OK;
+}
+
 void mhd_destroy(mhd_t* m) {
   if (!m) return;
+  cudaFree(m->arena64);
+  cudaFree(m->rate64);
   free_pipeline(m);
   drop_events(m);
   cudaFree(m->pencil_c);
@@ -602,6 +753,7 @@ int mhd_set_stream(mhd_t* m, void* cuda_stream) {
 
 int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
   if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  if (int rc = fp32_only(m)) return rc;
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   if (int rc = join_pipeline(m)) return rc;
@@ -624,6 +776,7 @@ int mhd_set_state(mhd_t* m, const float* const f[8], int on_device) {
 
 int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
   if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  if (int rc = fp32_only(m)) return rc;
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   const size_t bytes = sizeof(float) * (size_t)m->N;
@@ -639,6 +792,7 @@ int mhd_get_state(const mhd_t* m, float* const f[8], int on_device) {
 int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
   if (!check_box(m) || !dt_full) return fail(MHD_E_ARG, "null argument");
   if (!(cfl > 0.0)) return fail(MHD_E_ARG, "cfl must be > 0");
+  if (m->f64) return cfl_dt64(m, cfl, dt_full);
   unsigned bits = 0;
   CK(cudaMemcpyAsync(&bits, &m->sc->rate[m->rcur], sizeof bits, cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
@@ -655,6 +809,11 @@ int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
 int mhd_step(mhd_t* m, double dt_full) {
   if (!check_box(m)) return MHD_E_ARG;
   if (!(dt_full >= 0.0) || !std::isfinite(dt_full)) return fail(MHD_E_ARG, "dt must be finite and >= 0");
+  if (m->f64) {
+    if (int rc = full_step64(m, dt_full)) return rc;
+    m->time64 += dt_full;
+    return MHD_OK;
+  }
   if (int rc = join_pipeline(m)) return rc;
   int rc = traced(m, MHD_K_CONTROL, [&] {
     CK(mhd::launch_step_control(&m->sc->rate[m->rcur], &m->sc->rate[1 - m->rcur], &m->sc->tau,
@@ -668,6 +827,15 @@ int mhd_step(mhd_t* m, double dt_full) {
 int mhd_run(mhd_t* m, int nsteps, double cfl) {
   if (!check_box(m)) return MHD_E_ARG;
   if (nsteps < 0 || !(cfl > 0.0)) return fail(MHD_E_ARG, "need nsteps >= 0 and cfl > 0");
+  if (m->f64) {  // the timestep through the host: one synchronisation per step
+    for (int s = 0; s < nsteps; s++) {
+      double dt;
+      if (int rc = cfl_dt64(m, cfl, &dt)) return rc;
+      if (int rc = full_step64(m, dt)) return rc;
+      m->time64 += dt;
+    }
+    return MHD_OK;
+  }
   if (int rc = join_pipeline(m)) return rc;
   return run_steps(m, nsteps, cfl);
 }
@@ -684,6 +852,7 @@ int mhd_run(mhd_t* m, int nsteps, double cfl) {
 // copy of k-1.
 int mhd_submit(mhd_t* m, const float* const in[8], float* const out[8], int nsteps, double cfl) {
   if (!check_box(m) || !in || !out) return fail(MHD_E_ARG, "null argument");
+  if (int rc = fp32_only(m)) return rc;
   for (int q = 0; q < 8; q++)
     if (!in[q] || !out[q]) return fail(MHD_E_ARG, "null field pointer");
   if (nsteps < 0 || !(cfl > 0.0)) return fail(MHD_E_ARG, "need nsteps >= 0 and cfl > 0");
@@ -722,6 +891,10 @@ int mhd_drain(mhd_t* m) {
 
 int mhd_time(const mhd_t* m, double* t) {
   if (!check_box(m) || !t) return fail(MHD_E_ARG, "null argument");
+  if (m->f64) {
+    *t = m->time64;
+    return MHD_OK;
+  }
   CK(cudaMemcpyAsync(t, &m->sc->time, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
   return MHD_OK;
@@ -731,6 +904,7 @@ int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
   if (!check_box(m)) return MHD_E_ARG;
   if (axis < 0 || axis > 2 || kind < 0 || kind > 1 || !(tau >= 0.0))
     return fail(MHD_E_ARG, "bad axis/kind/tau");
+  if (m->f64) return kind == 0 ? fluid64(m, axis, tau) : magnetic64(m, axis, tau);
   // a single sweep does not advance the simulation time; afterwards the CFL
   // rate is recomputed for the new state
   if (int rc = join_pipeline(m)) return rc;
@@ -743,6 +917,7 @@ int mhd_sweep(mhd_t* m, int axis, int kind, double tau) {
 
 int mhd_set_boundary(mhd_t* m, int axis, int mode) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   if (axis < 0 || axis > 2 || mode < 0 || mode > 2) return fail(MHD_E_ARG, "bad axis or boundary mode");
   if (mode && m->n[axis] < 3 * mhd::kGhost)
     return fail(MHD_E_ARG, "a non-periodic axis needs at least 12 cells (4 ghost cells at each end)");
@@ -754,12 +929,14 @@ int mhd_set_boundary(mhd_t* m, int axis, int mode) {
 
 int mhd_fill_ghosts(mhd_t* m) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   if (int rc = join_pipeline(m)) return rc;
   return fill_ghosts(m);
 }
 
 int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   const int seg[3] = {seg_x, seg_y, seg_z};
   for (int d = 0; d < 3; d++)
     if (seg[d] != 0 && (seg[d] < 4 || seg[d] % 4 != 0 || m->n[d] % seg[d] != 0))
@@ -770,6 +947,7 @@ int mhd_set_segments(mhd_t* m, int seg_x, int seg_y, int seg_z) {
 
 int mhd_set_xpath(mhd_t* m, int mode) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   if (mode < 0 || mode > 3) return fail(MHD_E_ARG, "x path mode must be 0, 1, 2 or 3");
   if (mode == 3 && (m->n[0] % 4 || m->n[1] % 4 || m->n[2] % 4 || m->n[1] > 65535))
     return fail(MHD_E_ARG, "x path 3 needs every extent a multiple of 4 (and ny <= 65535)");
@@ -781,6 +959,8 @@ int mhd_set_xpath(mhd_t* m, int mode) {
 
 int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (m->f64 && (limiter || freezing)) return fail(MHD_E_ARG, "FP64 boxes run the paper's scheme only");
+  if (m->f64) return MHD_OK;
   if (limiter < 0 || limiter > 2 || freezing < 0 || freezing > 2 || (limiter && freezing))
     return fail(MHD_E_ARG, "limiter 0..2, freezing 0..2, one ablation at a time");
   if (freezing == 2 && !m->pencil_c) {  // two speeds per pencil of the longest pencil family
@@ -800,14 +980,16 @@ int mhd_set_resolution(mhd_t* m, double cx, double cy, double cz) {
   const double c[3] = {cx, cy, cz};
   for (int d = 0; d < 3; d++)
     if (!(c[d] >= 0.0) || !std::isfinite(c[d]) || c[d] > 3.0e38) return fail(MHD_E_ARG, "cells per unit length must be finite and >= 0");
-  if (int rc = join_pipeline(m)) return rc;
   for (int d = 0; d < 3; d++) m->cpl[d] = c[d];
+  if (m->f64) return MHD_OK;  // the FP64 CFL rate is computed when asked
+  if (int rc = join_pipeline(m)) return rc;
   set_geometry(m);
   return state_rate(m, &m->sc->rate[m->rcur]);
 }
 
 int mhd_set_interior(mhd_t* m, int axis, int lo, int hi) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   if (axis < 0 || axis > 2 || lo < 0 || hi > m->n[axis] || lo >= hi)
     return fail(MHD_E_ARG, "need 0 <= lo < hi <= n along the axis");
   if (int rc = join_pipeline(m)) return rc;
@@ -818,6 +1000,7 @@ int mhd_set_interior(mhd_t* m, int axis, int lo, int hi) {
 
 int mhd_copy_planes(mhd_t* m, int z0, int nplanes, float* const f[8], int into_box, int on_device) {
   if (!check_box(m) || !f) return fail(MHD_E_ARG, "null argument");
+  if (int rc = fp32_only(m)) return rc;
   for (int q = 0; q < 8; q++)
     if (!f[q]) return fail(MHD_E_ARG, "null field pointer");
   if (z0 < 0 || nplanes < 0 || z0 + nplanes > m->n[2]) return fail(MHD_E_ARG, "planes outside the box");
@@ -847,6 +1030,7 @@ int mhd_set_fusion(mhd_t* m, int on) {
 
 int mhd_set_pressure_floor(mhd_t* m, double p_floor) {
   if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
   if (!(p_floor >= 0.0)) return fail(MHD_E_ARG, "pressure floor must be >= 0");
   m->p_floor = (float)p_floor;
   return MHD_OK;
@@ -854,6 +1038,7 @@ int mhd_set_pressure_floor(mhd_t* m, double p_floor) {
 
 int mhd_diagnostics(mhd_t* m, double out[10]) {
   if (!check_box(m) || !out) return fail(MHD_E_ARG, "null argument");
+  if (int rc = fp32_only(m)) return rc;
   if (int rc = join_pipeline(m)) return rc;
   const float* cf[8];
   field_ptrs(m, cf);

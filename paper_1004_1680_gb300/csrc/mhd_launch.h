@@ -182,6 +182,28 @@ cudaError_t launch_conv_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* gy, c
 cudaError_t launch_conv_wgrad_cuda_cores(const __nv_bfloat16* x, const __nv_bfloat16* gy, const int n[3], int cin,
                                          int cout, float* gw, float* gb, cudaStream_t s);
 
+// FP64 path (sweep_f64.cu): whole-pencil kernels on the plain layout
+struct Fluid64Args {
+  const double* in[8];
+  double* out[8];  // fields 0..4 written
+  int n[3];
+  double ih[3];    // cells per unit length
+  double gamma;
+  double tau;
+};
+struct Mag64Args {
+  const double* in[8];
+  double* out[8];  // fields 5..7 written
+  double* E[2];    // edge fluxes of the transverse axes (D+1)%3, (D+2)%3 (N each)
+  int n[3];
+  double ih[3];
+  double tau;
+};
+cudaError_t launch_fluid64(int axis, const Fluid64Args& a, cudaStream_t s);
+cudaError_t launch_mag64(int axis, const Mag64Args& a, cudaStream_t s);
+cudaError_t launch_cfl64(const double* const f[8], const int n[3], const double ih[3], double gamma,
+                         unsigned long long* rate, cudaStream_t s);
+
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_transpose01(const TransposeArgs& a, cudaStream_t s);
 cudaError_t launch_transpose02(const TransposeArgs& a, cudaStream_t s);  // single box only

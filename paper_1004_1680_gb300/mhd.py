@@ -47,6 +47,9 @@ SIGNATURES = {
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_set_fusion": (_I, [_P, _I]),
+    "mhd_create_f64": (_P, [_I, _I, _I, _D]),
+    "mhd_set_state_f64": (_I, [_P, _PP, _I]),
+    "mhd_get_state_f64": (_I, [_P, _PP, _I]),
     "mhd_set_resolution": (_I, [_P, _D, _D, _D]),
     "mhd_set_interior": (_I, [_P, _I, _I, _I]),
     "mhd_copy_planes": (_I, [_P, _I, _I, _PP, _I, _I]),
@@ -309,6 +312,68 @@ class Box:
         out = (ctypes.c_double * 10)()
         _check(self.lib.mhd_diagnostics(self.h, out))
         return np.array(out[:], dtype=np.float64)
+
+
+class Box64:
+    """One periodic box computed in FP64 on the GPU (wraps an mhd_t made by
+    mhd_create_f64): the paper's scheme in double precision, an ablation of
+    the FP32 path."""
+
+    def __init__(self, nx: int, ny: int, nz: int, gamma: float = 5.0 / 3.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.lib = load()
+        self.shape = (8, nz, ny, nx)
+        self.n = (nx, ny, nz)
+        self.gamma = gamma
+        h = self.lib.mhd_create_f64(nx, ny, nz, gamma)
+        if not h:
+            raise MHDError(MHD_E_ARG, self.lib.mhd_last_error().decode())
+        self.h = ctypes.c_void_p(h)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(self.lib.mhd_set_stream(self.h, ctypes.c_void_p(s.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, state: torch.Tensor):
+        if state.shape != self.shape or state.dtype != torch.float64 or not state.is_contiguous():
+            raise ValueError("state must be a contiguous float64 tensor (8, nz, ny, nx)")
+        _check(self.lib.mhd_set_state_f64(self.h, _field_ptrs(state), 1 if state.is_cuda else 0))
+        if not state.is_cuda:
+            torch.cuda.synchronize()
+
+    def get_state(self, device="cuda") -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float64, device=device)
+        _check(self.lib.mhd_get_state_f64(self.h, _field_ptrs(out), 1 if out.is_cuda else 0))
+        return out
+
+    def cfl_dt(self, cfl: float = 0.7) -> float:
+        dt = ctypes.c_double()
+        _check(self.lib.mhd_cfl_dt(self.h, cfl, ctypes.byref(dt)))
+        return dt.value
+
+    def step(self, dt: float):
+        _check(self.lib.mhd_step(self.h, float(dt)))
+
+    def run(self, nsteps: int, cfl: float = 0.7):
+        _check(self.lib.mhd_run(self.h, int(nsteps), float(cfl)))
+
+    def sweep(self, axis: int, kind: int, tau: float):
+        _check(self.lib.mhd_sweep(self.h, int(axis), int(kind), float(tau)))
+
+    def time(self) -> float:
+        t = ctypes.c_double()
+        _check(self.lib.mhd_time(self.h, ctypes.byref(t)))
+        return t.value
 
 
 class Ensemble:
