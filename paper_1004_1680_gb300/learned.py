@@ -12,7 +12,12 @@ after each coarse step:
     positive.
 Training pairs come from the solver itself: input R(U_f(t)) (a 256^3 state
 restricted to 64^3), target R(U_f(t + dt)) - C(R(U_f(t))) where C is one
-coarse step of length dt and the fine run advances by the same dt.
+coarse step of length dt and the fine run advances by the same dt.  With
+rollout > 1 a pair's input may also be a coarse state that has run freely
+for a few steps from R(U_f) (target: R(U_f) at the end of the next step
+minus that step's result), so that the network also sees the drift that a
+coarse run accumulates.  The scale of the applied correction is chosen on
+validation seeds (choose_alpha), never on the seeds the comparison uses.
 
 Every arithmetic step runs in the CUDA library (convolutions, projection,
 loss, Adam, restriction, solver); this module sequences the calls.
@@ -135,33 +140,70 @@ def advance_fine(fine: mhd.Box, dt: float, cfl: float):
         fine.step(dt / k)
 
 
-def generate_pairs(seeds, steps_per_seed: int, nf: int = 256, r: int = 4, cfl: float = 0.7,
-                   p_floor: float = 1e-3, mach: float = 1.0, beta: float = 1.0):
-    """Pairs (coarse input, target residual) along fine trajectories.
-    Returns two tensors (P, 8, nc, nc, nc) on the GPU."""
+def generate_pairs(seeds, steps_per_seed: int = 1, nf: int = 256, r: int = 4, cfl: float = 0.7,
+                   p_floor: float = 1e-3, mach: float = 1.0, beta: float = 1.0, t_max: int = 0,
+                   rollout: int = 1, rng_seed: int = 12345, kmin: float = 2.0, kmax: float = 8.0, log=None):
+    """Pairs (coarse input, target residual) from a fine run of each seed.
+
+    A seed's fine run gives `steps_per_seed` segments, at coarse step counts
+    k drawn without repetition from [0, t_max) and sorted (t_max = 0: the
+    first steps_per_seed steps, k = 0, 1, ...); between them the fine run
+    takes r of its own CFL steps per coarse step (its cells are r times
+    smaller, so a coarse CFL step spans about r fine ones).  A segment
+    restricts the fine state to the coarse grid and lets the coarse box run
+    `rollout` steps freely next to the fine run; step j of the segment gives
+    the pair (coarse state before the step, R(fine after the step) - coarse
+    state after the step).  Returns two tensors (P, 8, nc, nc, nc) on the
+    GPU."""
     nc = nf // r
     fine = mhd.Box(nf, nf, nf)
     coarse = mhd.Box(nc, nc, nc)
     fine.set_pressure_floor(p_floor)
     coarse.set_pressure_floor(p_floor)
+    rng = np.random.default_rng(rng_seed)
     ins, tgts = [], []
-    for seed in seeds:
-        st = ic.turbulence((nf, nf, nf), seed=seed, mach=mach, beta=beta, device="cuda", dtype=torch.float32)
+    skipped = []
+    t0 = time.perf_counter()
+    for si, seed in enumerate(seeds):
+        st = ic.turbulence((nf, nf, nf), seed=seed, mach=mach, beta=beta, device="cuda", dtype=torch.float32,
+                           kmin=kmin, kmax=kmax)
         fine.set_state(st)
         del st
-        for _ in range(steps_per_seed):
-            uf = fine.get_state()
-            uc0 = mhd.restrict(uf, r)
-            coarse.set_state(uc0)
-            dt = coarse.cfl_dt(cfl)
-            coarse.step(dt)
-            uc1 = coarse.get_state()
-            advance_fine(fine, dt, cfl)
-            target = mhd.restrict(fine.get_state(), r) - uc1
-            ins.append(uc0)
-            tgts.append(target)
+        if t_max > 0:
+            ks = np.sort(rng.choice(t_max, size=steps_per_seed, replace=False))
+        else:
+            ks = np.arange(steps_per_seed)
+        k = 0
+        seed_ins, seed_tgts = [], []
+        try:
+            for kt in ks:
+                if kt > k:           # r fine CFL steps per coarse step (h is r times smaller)
+                    fine.run(int(r * (kt - k)), cfl)
+                    k = int(kt)
+                fine.cfl_dt(cfl)     # raises if the fine run left the valid states
+                coarse.set_state(mhd.restrict(fine.get_state(), r))
+                for _ in range(rollout):
+                    uc0 = coarse.get_state()
+                    dt = coarse.cfl_dt(cfl)
+                    coarse.step(dt)
+                    uc1 = coarse.get_state()
+                    advance_fine(fine, dt, cfl)
+                    seed_ins.append(uc0)
+                    seed_tgts.append(mhd.restrict(fine.get_state(), r) - uc1)
+                    coarse.cfl_dt(cfl)
+                k += rollout
+        except mhd.MHDError as e:  # an invalid state (p <= 0 or NaN): the seed gives no pairs
+            skipped.append(seed)
+            if log:
+                log(f"seed {seed} skipped: {e}")
+            continue
+        ins += seed_ins
+        tgts += seed_tgts
+        if log and (si + 1) % 50 == 0:
+            log(f"pairs: {si + 1} seeds, {len(ins)} pairs, {time.perf_counter() - t0:.0f} s")
     fine.close()
     coarse.close()
+    generate_pairs.skipped = skipped
     return torch.stack(ins), torch.stack(tgts)
 
 
@@ -225,25 +267,38 @@ def nrmse(run: torch.Tensor, ref: torch.Tensor) -> np.ndarray:
     return (rms / sd).cpu().numpy()
 
 
-def evaluate(corrector: Corrector | None, seed: int, nsteps: int = 200, every: int = 20, nf: int = 256,
-             cfl: float = 0.7, p_floor: float = 1e-3, mach: float = 1.0, beta: float = 1.0):
-    """Errors of learned 64^3, plain 64^3, plain 128^3 against R(256^3) at the
-    same times (all runs follow the plain 64^3 run's CFL dt), and GPU times."""
-    st = ic.turbulence((nf, nf, nf), seed=seed, mach=mach, beta=beta, device="cuda", dtype=torch.float32)
-    boxes = {"ref": mhd.Box(nf, nf, nf), "plain64": mhd.Box(64, 64, 64), "learned64": mhd.Box(64, 64, 64),
-             "plain128": mhd.Box(128, 128, 128)}
+def evaluate(corrector, seed: int, nsteps: int = 200, every: int = 20, nf: int = 256,
+             cfl: float = 0.7, p_floor: float = 1e-3, mach: float = 1.0, beta: float = 1.0, nc: int = 64,
+             kmin: float = 2.0, kmax: float = 8.0):
+    """Errors of learned nc^3, plain nc^3 and plain (2 nc)^3 runs against the
+    fine nf^3 run restricted to nc^3 at the same times (all runs follow the
+    plain nc^3 run's CFL dt), and GPU times.  (The result keys keep the
+    names of the 256^3 -> 64^3 workload: learned64, plain64, plain128.)
+    `corrector` is a Corrector, None (no correction), or a list of
+    Correctors: then every one of them runs its own learned coarse box next
+    to the same reference, under the keys learned64/<i>."""
+    st = ic.turbulence((nf, nf, nf), seed=seed, mach=mach, beta=beta, device="cuda", dtype=torch.float32,
+                       kmin=kmin, kmax=kmax)
+    correctors = corrector if isinstance(corrector, (list, tuple)) else [corrector]
+    lkeys = ["learned64"] if not isinstance(corrector, (list, tuple)) else \
+        [f"learned64/{i}" for i in range(len(correctors))]
+    boxes = {"ref": mhd.Box(nf, nf, nf), "plain64": mhd.Box(nc, nc, nc), "plain128": mhd.Box(2 * nc, 2 * nc, 2 * nc)}
+    for k in lkeys:
+        boxes[k] = mhd.Box(nc, nc, nc)
     for b in boxes.values():
         b.set_pressure_floor(p_floor)
     boxes["ref"].set_state(st)
-    boxes["plain64"].set_state(mhd.restrict(st, nf // 64))
-    boxes["learned64"].set_state(mhd.restrict(st, nf // 64))
-    boxes["plain128"].set_state(mhd.restrict(st, nf // 128))
+    boxes["plain64"].set_state(mhd.restrict(st, nf // nc))
+    for k in lkeys:
+        boxes[k].set_state(mhd.restrict(st, nf // nc))
+    boxes["plain128"].set_state(mhd.restrict(st, nf // (2 * nc)))
     del st
     ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in boxes}
     gpu_ms = {k: 0.0 for k in boxes}
-    errs = {"plain64": [], "learned64": [], "plain128": []}
-    lstate = boxes["learned64"].get_state()
+    errs = {k: [] for k in ["plain64", "plain128"] + lkeys}
+    lstate = boxes[lkeys[0]].get_state()
     nclip = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cmap = dict(zip(lkeys, correctors))
     for s in range(1, nsteps + 1):
         dt = boxes["plain64"].cfl_dt(cfl)
         for k, b in boxes.items():
@@ -254,14 +309,15 @@ def evaluate(corrector: Corrector | None, seed: int, nsteps: int = 200, every: i
                 kk = max(2, fine_substeps(b, dt, cfl))
                 for _ in range(kk):
                     b.step(dt / kk)
-            elif k == "learned64":
-                if corrector is not None:
+            elif k in cmap:
+                c = cmap[k]
+                if c is not None:
                     b.get_state(out=lstate)
-                    d = corrector.predict(lstate)
+                    d = c.predict(lstate)
                 b.step(dt)
-                if corrector is not None:
+                if c is not None:
                     b.get_state(out=lstate)
-                    corrector.apply(lstate, d, nclip=nclip)
+                    c.apply(lstate, d, nclip=nclip)
                     b.set_state(lstate)   # (its own time and CFL rate are not used)
             else:
                 b.step(dt)
@@ -269,11 +325,47 @@ def evaluate(corrector: Corrector | None, seed: int, nsteps: int = 200, every: i
             torch.cuda.synchronize()
             gpu_ms[k] += ev[k][0].elapsed_time(ev[k][1])
         if s % every == 0:
-            ref = mhd.restrict(boxes["ref"].get_state(), nf // 64)
+            ref = mhd.restrict(boxes["ref"].get_state(), nf // nc)
             errs["plain64"].append(nrmse(boxes["plain64"].get_state(), ref))
-            errs["learned64"].append(nrmse(boxes["learned64"].get_state(), ref))
+            for k in lkeys:
+                errs[k].append(nrmse(boxes[k].get_state(), ref))
             errs["plain128"].append(nrmse(mhd.restrict(boxes["plain128"].get_state(), 2), ref))
     t = boxes["plain64"].time()
     for b in boxes.values():
         b.close()
     return {k: np.array(v) for k, v in errs.items()}, gpu_ms, t, int(nclip.item())
+
+
+def evaluate_safe(corrector, seed: int, log=None, **kw):
+    """evaluate(), or None if one of the runs leaves the valid states (the
+    seed is then left out and counted)."""
+    try:
+        return evaluate(corrector, seed, **kw)
+    except mhd.MHDError as e:
+        if log:
+            log(f"seed {seed} left out: {e}")
+        return None
+
+
+def choose_alpha(net: CorrectionNet, norm: Norm, seeds, alphas=(0.0, 0.25, 0.5, 0.75, 1.0), nsteps: int = 200,
+                 nf: int = 256, nc: int = 64, every: int = 20, log=None, **kw):
+    """The scale of the applied correction with the lowest mean error on
+    validation seeds (alpha 0 is the plain coarse run): every alpha runs
+    next to the same reference runs.  Returns (best alpha, {alpha: mean
+    NRMSE})."""
+    cs = [Corrector(net, norm, (nc, nc, nc), alpha=a) for a in alphas]
+    tot = np.zeros(len(alphas))
+    used = 0
+    for seed in seeds:
+        r = evaluate_safe(cs, seed, log=log, nsteps=nsteps, nf=nf, nc=nc, every=min(every, nsteps), **kw)
+        if r is None:
+            continue
+        errs = r[0]
+        used += 1
+        for i in range(len(alphas)):
+            tot[i] += errs[f"learned64/{i}"].mean()
+        if log:
+            log(f"validation seed {seed}: " + " ".join(f"{a}:{errs[f'learned64/{i}'].mean():.4f}"
+                                                      for i, a in enumerate(alphas)))
+    means = {a: float(t / max(used, 1)) for a, t in zip(alphas, tot)}
+    return min(means, key=means.get), means

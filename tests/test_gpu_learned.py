@@ -68,3 +68,32 @@ def test_training_reduces_loss_on_solver_pairs():
     norm = learned.make_norm(inputs, targets, inputs.shape[-1])
     net, hist = learned.train(inputs, targets, norm, epochs=6, lr=2e-3)
     assert hist[-1] < hist[0]
+
+
+def test_trained_correction_beats_the_plain_coarse_run_on_held_out_seeds():
+    """What the trained network gains: coarse 16^3 runs (turbulence with
+    1 <= k/2pi <= 4, Mach 1) against the 64^3 run restricted to 16^3, 12
+    coarse steps.  The network is trained on one-step residuals along
+    training trajectories (seeds 0..7), the scale of the applied correction
+    is chosen on validation seeds (50, 51), and on held-out seeds 100..103
+    the corrected run's error (mean NRMSE over the 8 fields, sampled every 4
+    steps) is below the plain coarse run's on every seed and by at least 5 %
+    on average.  (Measured when written: 14-18 % lower on each of 6 seeds.)"""
+    import numpy as np
+
+    from paper_1004_1680_gb300 import learned
+    kw = dict(nf=64, kmin=1.0, kmax=4.0)
+    inputs, targets = learned.generate_pairs(range(8), steps_per_seed=24, r=4, **kw)
+    norm = learned.make_norm(inputs, targets, inputs.shape[-1])
+    net, _ = learned.train(inputs, targets, norm, epochs=8, lr=2e-3)
+    del inputs, targets
+    alpha, means = learned.choose_alpha(net, norm, [50, 51], alphas=(0.0, 0.5, 1.0), nsteps=12, nc=16, every=4,
+                                        **kw)
+    assert alpha > 0.0, means                       # the correction helps on validation
+    corr = learned.Corrector(net, norm, (16, 16, 16), alpha=alpha)
+    ratios = []
+    for seed in range(100, 104):
+        errs, _, _, _ = learned.evaluate(corr, seed, nsteps=12, every=4, nc=16, **kw)
+        ratios.append(errs["learned64"].mean() / errs["plain64"].mean())
+    assert max(ratios) < 1.0, ratios
+    assert np.mean(ratios) < 0.95, ratios
