@@ -373,8 +373,10 @@ int mhd_ens_autotune(mhd_ens_t *e, double cfl, int *xpath_out, int *segdiv_out);
  *
  * Weights w[cout][cin][3][3][3] (FP32, cross-correlation: output cell
  * (i,j,k) sees input (i+kx-1, j+ky-1, k+kz-1), periodic) are packed into a
- * BF16 tensor-core image of mhd_conv_pack_bytes() bytes; transpose = 1 packs
- * the image used for the input gradient. */
+ * BF16 tensor-core image of mhd_conv_pack_bytes() bytes (the three z taps
+ * side by side along the GEMM's N); transpose = 1 packs the image used for
+ * the input gradient, with the channels exchanged and the taps already
+ * mirrored. */
 size_t mhd_conv_pack_bytes(int cin, int cout, int transpose);
 int mhd_conv_pack(const float *w, int cin, int cout, int transpose, void *img, void *stream);
 
@@ -384,8 +386,10 @@ int mhd_conv_pack(const float *w, int cin, int cout, int transpose, void *img, v
  * mask[cell][co] <= 0 are zeroed (backward through a ReLU); written as BF16
  * (y_bf16) and/or FP32 (y_f32).  The input gradient of a layer with cin_f,
  * cout_f is mhd_conv3d(cin = cout_f, cout = cin_f, img = transposed pack,
- * flip = 1).  img_bytes must equal the size of the image for these channel
- * counts (MHD_E_ARG otherwise). */
+ * flip = 1): the mirrored taps come with the transposed pack, so flip = 1
+ * goes with a transposed pack and flip = 0 with a forward one.  img_bytes
+ * must equal the size of the image for these channel counts (MHD_E_ARG
+ * otherwise). */
 int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void *x, const void *img,
                size_t img_bytes, const float *bias, int relu, int flip, const void *mask, void *y_bf16,
                float *y_f32, void *stream);

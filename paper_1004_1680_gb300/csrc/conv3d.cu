@@ -113,7 +113,6 @@ struct ConvRing {
   static constexpr int SLOT = G * PLANE;              // one z plane of the halo
   static constexpr int NSLOT = 6;
   static constexpr int NACC = TY / 16;                // 128-row accumulators per tile
-  static constexpr int TMEM_COLS = 2 * NACC * 32;     // two buffers of NACC x 32 columns
 };
 
 // The block's contiguous run of tiles, z fastest: tile t is column t / nz
@@ -145,16 +144,35 @@ __device__ __forceinline__ void load_plane(uint8_t* slot, const __nv_bfloat16* _
 }
 
 // G = cin / 8 channel groups, tiles of 8 x TY x 1 cells (TY / 16 accumulators
-// of 128 rows).  Persistent, 256 threads, warp-specialised:
-//  * warps 0 .. NACC-1: lane 0 issues accumulator q = warp's MMAs (27 taps x
-//    cin / 16 K steps) into one of two TMEM buffers;
-//  * warps 2, 3: copy halo planes into the ring (cp.async);
-//  * warps 4..7: epilogue (TMEM lanes 32 (warp - 4) ..): bias, ReLU or the
-//    ReLU mask, BF16 / FP32 stores.
-// mbarriers: slot full (copying threads) / empty (tcgen05.commit once no
-// later tile reads the plane); accumulator buffer full (commit) / empty
-// (epilogue warps).  The weights (packed once by conv_pack) are copied into
-// shared memory once per block.
+// of 128 rows).  Persistent, 256 threads, warp-specialised, z taps packed
+// along N:
+//  * The block's run of tiles (z fastest) splits into column segments: L
+//    consecutive tiles of one 8 x TY column at z = z0 .. z0 + L - 1.  A
+//    segment reads its input planes P = z0 - 1 .. z0 + L once each, in
+//    order.  Input plane P, shifted in-plane by one of the 9 (ky, kx)
+//    offsets, is the A operand of one MMA per 16 input channels whose B
+//    holds the weights of the three z taps side by side (N = 3 npad rows:
+//    column block j3 = the tap kz = j3 for the forward pass), so one MMA adds
+//    the contributions of plane P to the output planes P + 1, P, P - 1.
+//  * The accumulators of the output planes live in a ring of kRing slots of
+//    npad TMEM columns per 128-row accumulator, in descending order of the
+//    output plane, so the three column blocks an input plane writes are
+//    adjacent; where they cross the end of the ring the MMA splits in two.
+//    The first K step that reaches an output plane (input plane = output
+//    plane + 1 - j3 with j3 = 0) writes its block with accumulate off.
+//  * Output plane z is complete once input plane z + 1 has been added.
+// Roles: warps 0 .. NACC-1, lane 0: the MMAs of accumulator q; warps 2, 3:
+// copy input planes into the ring (cp.async); warps 4..7: epilogue of the
+// completed output planes (tcgen05.ld, bias, ReLU or the ReLU mask, BF16 /
+// FP32 stores).  mbarriers: input slot full (copying threads) / empty (a
+// tcgen05.commit after the plane's MMAs); output slot full (a commit after
+// the output plane's last MMA) / free (the epilogue warps).  The weights
+// (packed once by conv_pack) are copied into shared memory once per block.
+// Compared with one N = npad MMA per (tap, 16 channels) and tile, this reads
+// each input plane's A operand once for three output planes: about a third
+// of the shared-memory operand traffic per MAC.
+constexpr int kRing = 8;  // output-plane slots per accumulator
+
 template <int G, int TY>
 __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   using R = ConvRing<G, TY>;
@@ -162,16 +180,18 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   constexpr int NL = 64;  // copying threads
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int npad = a.npad;
   const int Kp = a.kchunks * kKC;
-  const int bBytes = a.npad * Kp * 2;
+  const int bBytes = 3 * npad * Kp * 2;
   uint8_t* sB = smem;
   uint8_t* ring = smem + ((bBytes + 1023) & ~1023);
   float* sBias = reinterpret_cast<float*>(ring + NS * R::SLOT);
   uint64_t* full = reinterpret_cast<uint64_t*>(sBias + 32);
   uint64_t* empty = full + NS;
-  uint64_t* afull = empty + NS;
-  uint64_t* aempty = afull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(aempty + 2);
+  uint64_t* ofull = empty + NS;
+  uint64_t* ofree = ofull + kRing;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ofree + kRing);
+  const uint32_t tmem_cols = (uint32_t)(NACC * kRing * npad);  // 128 .. 512, a power of two
 
   const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
   const int tiles_x = nx / kTX, tiles_y = ny / TY;
@@ -190,7 +210,7 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   if (tid < 32) sBias[tid] = (a.bias && tid < a.cout) ? __ldg(a.bias + tid) : 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                 "r"(R::TMEM_COLS)
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -199,9 +219,9 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + i)), "r"(NL) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(empty + i)), "r"(NACC) : "memory");
     }
-    for (int i = 0; i < 2; i++) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(afull + i)), "r"(NACC) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(aempty + i)) : "memory");
+    for (int i = 0; i < kRing; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(ofull + i)), "r"(NACC) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(ofree + i)) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -216,90 +236,101 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
     // ---- MMA issue: accumulator q -------------------------------------
     if (lane == 0) {
       const int q = warp;
-      const uint32_t idesc = make_idesc(kM, a.npad);
       const uint32_t sbo_b = (Kp / 8) * 128;
       const uint32_t b_addr = smem_addr(sB);
-      int e = -1;       // ring index of the newest plane of the current tile
-      int seen = -1;    // ring entries up to this one are known to have landed
-      int freed = 0;    // ring indices below this have been released
-      int issued = 0;
-      for (int i = 0; i < run.count && ok; i++) {
-        e += run.fresh(i) ? 3 : 1;
-        // the tile's planes z-1, z, z+1 are ring entries e-2, e-1, e; the
-        // entries shared with the previous tile need no second wait
-        for (int k = seen + 1; k <= e && ok; k++) ok = mbar_wait(smem_addr(full + k % NS), (k / NS) & 1);
-        seen = e;
-        const int b = i & 1;
-        if (ok && i >= 2) ok = mbar_wait(smem_addr(aempty + b), (i / 2 - 1) & 1);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // GEMM row m of accumulator q = tile cell (m % 8, 16 q + m / 8): the
-        // rows of a core matrix are 8 consecutive halo cells along x (16
-        // bytes apart), 8-row groups one halo row apart (SBO = kHX * 16); tap
-        // t reads plane kz's slot from the cell shifted by (kx, ky) (the
-        // mirrored tap for the input gradient).  Address fields count
-        // 16-byte units, so shifts add to the descriptor.
-        uint64_t a0[3];
+      const uint32_t dq = tmem + (uint32_t)(q * kRing * npad);
+      int k = 0;          // input planes consumed
+      int last_out = -1;  // last output plane committed
+      for (int i0 = 0; i0 < run.count && ok;) {
+        // the column segment of tiles i0 .. i0 + L - 1 (outputs g = i0 + u)
+        int L = 1;
+        while (i0 + L < run.count && run.col(i0 + L) == run.col(i0)) L++;
+        for (int v = 0; v < L + 2 && ok; v++, k++) {
+          const int jlo = v > L - 1 ? v - (L - 1) : 0, jhi = v < 2 ? v : 2;
+          const int gtop = i0 + v;  // output plane of block j3 = 0 (started by this input plane if v < L)
+          ok = mbar_wait(smem_addr(full + k % NS), (k / NS) & 1);
+          if (ok && jlo == 0 && gtop >= kRing)  // its slot's previous output has been read out
+            ok = mbar_wait(smem_addr(ofree + gtop % kRing), (gtop / kRing - 1) & 1);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // GEMM row m of accumulator q = tile cell (m % 8, 16 q + m / 8): the
+          // rows of a core matrix are 8 consecutive halo cells along x (16
+          // bytes apart), 8-row groups one halo row apart (SBO = kHX * 16);
+          // the (ky, kx) offset is a shift of the start address.
+          const uint64_t a0 = make_desc(smem_addr(ring + (k % NS) * R::SLOT), G == 4 ? R::PLANE : 16, kHX * 16) +
+                              (uint64_t)(q * 16 * kHX);
 #pragma unroll
-        for (int kz = 0; kz < 3; kz++)
-          a0[kz] = make_desc(smem_addr(ring + ((e - 2 + kz) % NS) * R::SLOT), G == 4 ? R::PLANE : 16, kHX * 16) +
-                   (uint64_t)(q * 16 * kHX);
-        const uint32_t d = tmem + (uint32_t)((b * NACC + q) * 32);
+          for (int j = 0; j < 9; j++) {
+            const int off = (j / 3) * kHX + j % 3;
 #pragma unroll
-        for (int t = 0; t < 27; t++) {
-          const int tt = a.flip ? 26 - t : t;
-          const int kz = tt / 9, off = ((tt / 3) % 3) * kHX + tt % 3;
-#pragma unroll
-          for (int h = 0; h < (G == 4 ? 2 : 1); h++) {
-            const uint64_t bdesc = (G == 4) ? make_desc(b_addr + (t * 4 + 2 * h) * 128, 128, sbo_b)
-                                            : make_desc(b_addr + t * 128, (27 - t) * 128, sbo_b);
-            const uint32_t acc = (t > 0 || h > 0) ? 1u : 0u;
-            // G = 4: k = 16 channels 16h..16h+15 (planes 2h, 2h+1); G = 1: the
-            // 8 channels of tap t, then 8 whose weights are the zero k-group 27
-            const uint64_t adesc =
-                (kz == 0 ? a0[0] : kz == 1 ? a0[1] : a0[2]) + (uint64_t)(off + (G == 4 ? h * (2 * R::PLANE / 16) : 0));
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-                : "memory");
+            for (int h = 0; h < (G == 4 ? 2 : 1); h++) {
+              // G = 4: k = 16 channels 16h..16h+15 (planes 2h, 2h+1); G = 1:
+              // the 8 channels of offset j, then 8 whose weights are the zero
+              // k-group 9
+              const uint32_t b_k = (G == 4) ? (uint32_t)((j * 4 + 2 * h) * 128) : (uint32_t)(j * 128);
+              const uint32_t lbo_b = (G == 4) ? 128u : (uint32_t)((9 - j) * 128);
+              const uint64_t adesc = a0 + (uint64_t)(off + (G == 4 ? h * (2 * R::PLANE / 16) : 0));
+              const bool first = (j == 0 && h == 0);
+              int j0 = jlo, nb = jhi - jlo + 1;
+              while (nb > 0) {
+                // block j0 alone when it starts its output plane (accumulate off)
+                const uint32_t acc = (first && j0 == 0) ? 0u : 1u;
+                const int g = gtop - j0;
+                const int slot = kRing - 1 - (g % kRing);
+                int len = nb < kRing - slot ? nb : kRing - slot;
+                if (acc == 0u) len = 1;
+                const uint64_t bdesc = make_desc(b_addr + b_k + (uint32_t)(j0 * npad / 8) * sbo_b, lbo_b, sbo_b);
+                const uint32_t idesc = make_idesc(kM, len * npad);
+                const uint32_t d = dq + (uint32_t)(slot * npad);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                    : "memory");
+                j0 += len;
+                nb -= len;
+              }
+            }
+          }
+          // the input plane is no longer read; output plane gtop - 2 is complete
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_addr(empty + k % NS))
+                       : "memory");
+          if (jhi == 2) {
+            last_out = gtop - 2;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(ofull + last_out % kRing))
+                         : "memory");
           }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_addr(afull + b))
-                     : "memory");
-        issued = i + 1;
-        // release the planes that no later tile reads
-        const int keep = (i + 1 < run.count) ? (run.fresh(i + 1) ? e + 1 : e - 1) : e + 1;
-        for (; freed < keep; freed++)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_addr(empty + freed % NS))
-                       : "memory");
+        i0 += L;
       }
       // nothing of this thread in flight when TMEM is freed
-      if (issued > 0) {
-        const bool done = mbar_wait(smem_addr(afull + (issued - 1) % 2), ((issued - 1) / 2) & 1);
+      if (last_out >= 0) {
+        const bool done = mbar_wait(smem_addr(ofull + last_out % kRing), (last_out / kRing) & 1);
         ok = ok && done;
       }
     }
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   } else if (warp == 2 || warp == 3) {
-    // ---- copies: ring entry k goes to slot k % NS ------------------------
+    // ---- copies: input plane k goes to slot k % NS ---------------------------
     const int lt = tid - 64;
     int k = 0;
-    for (int i = 0; i < run.count && ok; i++) {
-      const int c = run.col(i), z = run.z(i);
-      const int first = run.fresh(i) ? -1 : 1;
-      for (int dz = first; dz <= 1 && ok; dz++, k++) {
+    for (int i0 = 0; i0 < run.count && ok;) {
+      int L = 1;
+      while (i0 + L < run.count && run.col(i0 + L) == run.col(i0)) L++;
+      const int c = run.col(i0), z0 = run.z(i0);
+      for (int v = 0; v < L + 2 && ok; v++, k++) {
         if (k >= NS) ok = mbar_wait(smem_addr(empty + k % NS), (k / NS - 1) & 1);
         if (!ok) break;
-        load_plane<G, TY>(ring + (k % NS) * R::SLOT, a.x, c, wrap1(z + dz, nz), run, nx, ny, lt, NL);
-        if (k >= 1) {  // the previous entry's pieces have landed
+        load_plane<G, TY>(ring + (k % NS) * R::SLOT, a.x, c, wrap1(z0 - 1 + v, nz), run, nx, ny, lt, NL);
+        if (k >= 1) {  // the previous plane's pieces have landed
           asm volatile("cp.async.wait_group 1;" ::: "memory");
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + (k - 1) % NS)) : "memory");
         }
       }
+      i0 += L;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (ok && k > 0) {
@@ -310,22 +341,22 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
     // ---- epilogue: TMEM lanes 32 (warp - 4) + lane = GEMM row -------------
     const int ew = warp - 4, row = 32 * ew + lane;
     const int co_n = a.cout;
-    for (int i = 0; i < run.count; i++) {
-      const int b = i & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(afull + b), (i / 2) & 1));
+    for (int g = 0; g < run.count; g++) {
+      ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(ofull + g % kRing), (g / kRing) & 1));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int c = run.col(i), z0 = run.z(i);
+      const int c = run.col(g), z0 = run.z(g);
       const int x0 = (c % tiles_x) * kTX, y0 = (c / tiles_x) * TY;
+      const int slot = kRing - 1 - (g % kRing);
 #pragma unroll
       for (int q = 0; q < NACC; q++) {
         const int cell = (x0 + (row & 7)) + nx * ((y0 + 16 * q + (row >> 3)) + ny * z0);
-        const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)((b * NACC + q) * 32);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)((q * kRing + slot) * npad);
         float acc[32];
         uint32_t r[16];
 #pragma unroll
         for (int half = 0; half < 2; half++) {
-          if (half >= a.npad / 16) break;
+          if (half >= npad / 16) break;
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
               "[%16];"
@@ -366,35 +397,47 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
           }
         }
       }
-      // the buffer's TMEM has been read: the tile after next may overwrite it
+      // the slot's TMEM has been read: the output plane kRing later may start in it
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(aempty + b)) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(ofree + g % kRing)) : "memory");
     }
   }
   if (!ok) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(R::TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 // Pack conv weights w[cout][cin][27] (FP32, PyTorch order, tap = (kz*3+ky)*3+kx)
-// into the canonical K-major BF16 image of B.  Forward (transpose = 0):
-// row n = output channel, k = tap * cin + ci.  Input gradient (transpose = 1):
-// row n = input channel, k = tap * cout + co (taps applied flipped).
+// into the canonical K-major BF16 image of B with the z taps along N:
+// row n = j3 * npad + r (column block j3 = 0, 1, 2), k = j * cols + c with j =
+// ky * 3 + kx the in-plane offset of the input plane.  Forward (transpose =
+// 0): r = output channel, c = input channel, tap (kz, ky, kx) = (j3, j / 3,
+// j % 3).  Input gradient (transpose = 1): r = input channel, c = output
+// channel, and the taps mirrored, (2 - j3, 2 - j / 3, 2 - j % 3): the kernel
+// then runs unchanged.  K is padded to kchunks * 32 with zeros (for 8
+// channels the zero k-group 9 pairs with each offset's 8).
 __global__ void conv_pack_kernel(const float* __restrict__ w, int cin, int cout, int transpose, int npad,
                                  int kchunks, uint16_t* __restrict__ img) {
   const int Kp = kchunks * kKC;
-  const int total = npad * Kp;
+  const int total = 3 * npad * Kp;
   const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int n = e / Kp, k = e % Kp;
+    const int j3 = n / npad, r = n % npad;
+    const int j = k / cols, c = k % cols;
     float v = 0.f;
-    const int tap = k / cols, c = k % cols;
-    if (n < rows && tap < 27) {
-      const int co = transpose ? c : n, ci = transpose ? n : c;
-      v = w[((size_t)co * cin + ci) * 27 + tap];
+    if (r < rows && j < 9) {
+      int kz = j3, ky = j / 3, kx = j % 3;
+      if (transpose) {
+        kz = 2 - kz;
+        ky = 2 - ky;
+        kx = 2 - kx;
+      }
+      const int co = transpose ? c : r, ci = transpose ? r : c;
+      v = w[((size_t)co * cin + ci) * 27 + (kz * 3 + ky) * 3 + kx];
     }
     const size_t off = (size_t)(n / 8) * (Kp / 8) * 64 + (size_t)(k / 8) * 64 + (n % 8) * 8 + (k % 8);
     img[off] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -829,13 +872,17 @@ cudaError_t launch_conv_wgrad_cuda_cores(const __nv_bfloat16* x, const __nv_bflo
 }
 
 int conv_npad(int n) { return n <= 16 ? 16 : 32; }
-int conv_kchunks(int c) { return (27 * c + kKC - 1) / kKC; }
+// K of the packed image: the 9 in-plane offsets x the input channels
+int conv_kchunks(int c) { return (9 * c + kKC - 1) / kKC; }
+// bytes of the packed weight image (3 npad rows: the z taps along N)
+size_t conv_image_bytes(int rows, int cols) { return (size_t)3 * conv_npad(rows) * conv_kchunks(cols) * kKC * 2; }
 size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty) {
-  const size_t b = (size_t)npad * kchunks * kKC * 2;
+  const size_t b = (size_t)3 * npad * kchunks * kKC * 2;
   const size_t slot = ty == 32 ? (cin == 32 ? ConvRing<4, 32>::SLOT : ConvRing<1, 32>::SLOT)
                                : (cin == 32 ? ConvRing<4, 16>::SLOT : ConvRing<1, 16>::SLOT);
-  // weights, ring, bias, 16 mbarriers, TMEM address
-  return ((b + 1023) & ~(size_t)1023) + ConvRing<4, 32>::NSLOT * slot + 32 * sizeof(float) + 16 * 8 + 16;
+  // weights, ring, bias, the input and output slot mbarriers, TMEM address
+  return ((b + 1023) & ~(size_t)1023) + ConvRing<4, 32>::NSLOT * slot + 32 * sizeof(float) +
+         (2 * ConvRing<4, 32>::NSLOT + 2 * kRing) * 8 + 16;
 }
 
 namespace {
@@ -897,7 +944,7 @@ cudaError_t launch_variant(const ConvArgs& a, cudaStream_t s) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3d_tc_kernel<G, TY>, 256, smem);
       if (e != cudaSuccess) return e;
       // resident blocks of an SM share its 512 TMEM columns
-      const int tmem_cap = 512 / ConvRing<G, TY>::TMEM_COLS;
+      const int tmem_cap = 512 / (ConvRing<G, TY>::NACC * kRing * a.npad);
       per_sm = per_sm < tmem_cap ? per_sm : tmem_cap;
       cap = sms * (per_sm > 0 ? per_sm : 1);
       if (c.used < kCacheSizes) {
@@ -928,7 +975,7 @@ cudaError_t prepare_conv_kernels() {
 cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s) {
   const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
   const int npad = conv_npad(rows), kc = conv_kchunks(cols);
-  const int total = npad * kc * kKC;
+  const int total = 3 * npad * kc * kKC;
   conv_pack_kernel<<<(total + 255) / 256, 256, 0, s>>>(w, cin, cout, transpose, npad, kc, img);
   return cudaGetLastError();
 }

@@ -47,7 +47,7 @@ extern "C" {
 size_t mhd_conv_pack_bytes(int cin, int cout, int transpose) {
   if (!valid_channels(cin) || !valid_channels(cout)) return 0;
   const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
-  return (size_t)mhd::conv_npad(rows) * mhd::conv_kchunks(cols) * 32 * 2;
+  return mhd::conv_image_bytes(rows, cols);
 }
 
 int mhd_conv_pack(const float* w, int cin, int cout, int transpose, void* img, void* stream) {
@@ -70,8 +70,8 @@ int mhd_conv3d(int nx, int ny, int nz, int cin, int cout, const void* x, const v
   const auto mis = [](const void* p) { return ((uintptr_t)p & 15) != 0; };
   if (mis(x) || mis(img) || mis(mask) || mis(y_bf16) || mis(y_f32))
     return mhd::set_error(MHD_E_ARG, "mhd_conv3d", "buffers must be 16-byte aligned");
-  // the blocks copy npad x kchunks*32 BF16 weights: the image must be exactly that
-  if (img_bytes != (size_t)mhd::conv_npad(cout) * mhd::conv_kchunks(cin) * 32 * 2)
+  // the blocks copy the 3 npad x kchunks*32 BF16 weights: the image must be exactly that
+  if (img_bytes != mhd::conv_image_bytes(cout, cin))
     return mhd::set_error(MHD_E_ARG, "mhd_conv3d", "weight image size does not match cin/cout");
   int* err = nullptr;
   int rc = device_setup(&err);

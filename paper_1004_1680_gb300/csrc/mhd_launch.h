@@ -168,11 +168,12 @@ struct ConvArgs {
   int cout;                   // channels written per cell
   int npad, kchunks;          // MMA N and number of 32-wide k chunks
   int relu;
-  int flip;                   // 1: taps applied at -offset (input gradient)
+  int flip;                   // 1: input gradient (the mirrored taps come with the transposed pack)
   int* err;                   // set to 1 if a bounded wait gives up
 };
 int conv_npad(int n);
 int conv_kchunks(int c);
+size_t conv_image_bytes(int rows, int cols);
 size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty);
 cudaError_t prepare_conv_kernels();
 cudaError_t launch_conv_pack(const float* w, int cin, int cout, int transpose, uint16_t* img, cudaStream_t s);
