@@ -74,11 +74,12 @@ def test_conv_rejects_unsupported_shapes(lib, dims, cin, cout):
 
 
 def test_conv_pack_sizes(lib):
-    # Npad x (27 cin rounded up to 32) BF16: N = 32 for 32 outputs, 16 for 8
-    assert lib.mhd_conv_pack_bytes(32, 32, 0) == 32 * 864 * 2
-    assert lib.mhd_conv_pack_bytes(8, 32, 0) == 32 * 224 * 2
-    assert lib.mhd_conv_pack_bytes(32, 8, 0) == 16 * 864 * 2
-    assert lib.mhd_conv_pack_bytes(32, 8, 1) == 32 * 224 * 2
+    # 3 Npad rows (the three z taps side by side along N; Npad = 32 for 32
+    # outputs, 16 for 8) x (9 in-plane offsets x cin, rounded up to 32) BF16
+    assert lib.mhd_conv_pack_bytes(32, 32, 0) == 3 * 32 * 288 * 2
+    assert lib.mhd_conv_pack_bytes(8, 32, 0) == 3 * 32 * 96 * 2
+    assert lib.mhd_conv_pack_bytes(32, 8, 0) == 3 * 16 * 288 * 2
+    assert lib.mhd_conv_pack_bytes(32, 8, 1) == 3 * 32 * 96 * 2
     assert lib.mhd_conv_pack_bytes(16, 8, 0) == 0
 
 
