@@ -202,9 +202,9 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   run.nz = nz;
   run.tiles_x = tiles_x;
 
-  // weights: a straight copy of the packed image, once per block; zero pad cells
-  for (int i = tid; i < bBytes / 16; i += 256)
-    reinterpret_cast<uint4*>(sB)[i] = __ldg(reinterpret_cast<const uint4*>(a.wpack) + i);
+  // zero pad cells; the copying warps start on the input planes while the
+  // other six warps copy the weights (a straight copy of the packed image,
+  // once per block) and meet on a named barrier before the first MMA
   for (int i = tid; i < NS * G * 4; i += 256)
     *reinterpret_cast<uint4*>(ring + (i / 4) * R::PLANE + (kHX * R::HY + i % 4) * 16) = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 32) sBias[tid] = (a.bias && tid < a.cout) ? __ldg(a.bias + tid) : 0.f;
@@ -225,11 +225,19 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights and pads, for the tensor core
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // pads, for the tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  const bool copier = (warp == 2 || warp == 3);
+  if (!copier) {
+    const int wt = tid < 64 ? tid : tid - 64;  // 0..191 over warps 0, 1, 4..7
+    for (int i = wt; i < bBytes / 16; i += 192)
+      reinterpret_cast<uint4*>(sB)[i] = __ldg(reinterpret_cast<const uint4*>(a.wpack) + i);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights, for the tensor core
+    asm volatile("bar.sync 1, 192;" ::: "memory");
+  }
 
   bool ok = true;
   if (warp < NACC) {
