@@ -79,6 +79,9 @@ def parse():
                    help="time the FP64 path (mhd_create_f64, an ablation) instead of the FP32 one")
     p.add_argument("--fusion", type=int, choices=[0, 1], default=1,
                    help="1: the two middle z magnetic sweeps of a step as one launch (bitwise the same state)")
+    p.add_argument("--tma", type=int, choices=[0, 1], default=1,
+                   help="1: the y and z kernel-axis fluid sweeps stage their input with TMA tile copies "
+                        "(bitwise the same state)")
     p.add_argument("--bc", default="",
                    help="non-periodic axes, e.g. x=outflow,z=reflecting (4 ghost cells at each end "
                         "inside the box; the paper's runs are periodic)")
@@ -471,6 +474,7 @@ def run_ours(args, rank, world, local):
     if args.xpath:
         box.set_xpath(args.xpath)
     box.set_fusion(bool(args.fusion))
+    box.set_tma(bool(args.tma))
     if args.seg:
         box.set_segments(args.seg, args.seg, args.seg)
     bcs = {}
@@ -507,6 +511,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    tma0 = box.tma_sweeps()
     e0.record(stream)
     box.run(args.steps, args.cfl)
     e1.record(stream)
@@ -515,6 +520,7 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     secs = e0.elapsed_time(e1) / 1e3
+    tma_per_step = (box.tma_sweeps() - tma0) / args.steps
     box.cfl_dt(args.cfl)               # state still valid after the timed run
     # per-launch figures from a second, traced pass of the same steps from
     # the same state (CUDA events around every launch; the timed pass above
@@ -650,6 +656,7 @@ def run_ours(args, rank, world, local):
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
                           "xpath": args.xpath or "auto",
                           "fusion": bool(args.fusion),
+                          "tma_staged_fluid_sweeps_per_step": tma_per_step,
                           **({"boundaries": bcs, "interior_cells": int(np.prod([n - 8 if a in bcs else n for a in "xyz"]))}
                              if bcs else {}),
                           **({"mach": args.mach, "beta": args.beta} if (args.mach, args.beta) != (1.0, 1.0) else {}),

@@ -39,7 +39,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 struct Scalars {  // small device block
   float tau;
   unsigned rate[2];
-  unsigned pad;
+  unsigned err;  // 1: a staged chunk of a fluid sweep did not arrive within the wait bound
   double time;
   double diag[10];
 };
@@ -71,6 +71,8 @@ struct mhd_s {
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   int fuse = 1;         // 1: the two z magnetic sweeps of a step run as one launch
+  int tma = 1;          // 1: y and z kernel-axis fluid sweeps stage their chunks with TMA where they qualify
+  long long tma_sweeps = 0;  // fluid sweeps launched TMA-staged
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
   double cpl[3] = {0.0, 0.0, 0.0};  // cells per unit length per physical axis (0: n, the unit box)
   int own_lo[3] = {0, 0, 0};        // own cells [own_lo, own_hi) per physical axis (the others are
@@ -370,6 +372,10 @@ int fluid(mhd_s* m, int d, bool rate) {
   a.fast = m->fast;
   for (int p = 0; p < 3; p++)  // the fused rate covers the interior, own cells
     rate_window(m, p, &a.rate_lo[kernel_axis_of(m, p)], &a.rate_hi[kernel_axis_of(m, p)]);
+  int staged = 0;
+  a.tma = m->tma;
+  a.err = &m->sc->err;
+  a.tma_used = &staged;
   if (m->fast == 2) {  // per-pencil freezing speeds before the sweep
     a.pencil_c = m->pencil_c;
     if ((rc = traced(m, MHD_K_CONTROL, [&] {
@@ -383,6 +389,7 @@ int fluid(mhd_s* m, int d, bool rate) {
     return MHD_OK;
   });
   if (rc) return rc;
+  m->tma_sweeps += staged;
   for (int q = 0; q < 5; q++) std::swap(m->cur[q], m->spare[q]);
   return MHD_OK;
 }
@@ -793,11 +800,15 @@ int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
   if (!check_box(m) || !dt_full) return fail(MHD_E_ARG, "null argument");
   if (!(cfl > 0.0)) return fail(MHD_E_ARG, "cfl must be > 0");
   if (m->f64) return cfl_dt64(m, cfl, dt_full);
-  unsigned bits = 0;
-  CK(cudaMemcpyAsync(&bits, &m->sc->rate[m->rcur], sizeof bits, cudaMemcpyDeviceToHost, m->stream));
+  unsigned w[3] = {0, 0, 0};  // rate[0], rate[1], err
+  CK(cudaMemcpyAsync(w, &m->sc->rate[0], sizeof w, cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
+  if (w[2]) {
+    *dt_full = 0.0;
+    return fail(MHD_E_TIMEOUT, "a staged chunk of a fluid sweep did not arrive within the wait bound");
+  }
   float r;
-  std::memcpy(&r, &bits, sizeof r);
+  std::memcpy(&r, &w[m->rcur], sizeof r);
   if (!(r > 0.f) || !std::isfinite(r)) {
     *dt_full = 0.0;
     return fail(MHD_E_STATE, "invalid state: NaN, rho <= 0 or p <= 0 in some cell");
@@ -1025,6 +1036,20 @@ int mhd_set_fusion(mhd_t* m, int on) {
   if (!check_box(m)) return MHD_E_ARG;
   if (on < 0 || on > 1) return fail(MHD_E_ARG, "fusion must be 0 or 1");
   m->fuse = on;
+  return MHD_OK;
+}
+
+int mhd_set_tma(mhd_t* m, int on) {
+  if (!check_box(m)) return MHD_E_ARG;
+  if (int rc = fp32_only(m)) return rc;
+  if (on < 0 || on > 1) return fail(MHD_E_ARG, "tma must be 0 or 1");
+  m->tma = on;
+  return MHD_OK;
+}
+
+int mhd_tma_sweeps(const mhd_t* m, long long* count) {
+  if (!check_box(m) || !count) return fail(MHD_E_ARG, "null argument");
+  *count = m->tma_sweeps;
   return MHD_OK;
 }
 

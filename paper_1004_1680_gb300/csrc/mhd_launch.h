@@ -1,6 +1,7 @@
 // Kernel argument blocks and host-side launchers shared by the library's
 // translation units (internal; the public interface is include/mhd.h).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the maps are encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -52,7 +53,26 @@ struct FluidArgs {
   // interior of a box with ghost layers; every cell by default)
   int rate_lo[3] = {0, 0, 0};
   int rate_hi[3] = {1 << 30, 1 << 30, 1 << 30};
+  int tma = 0;              // 1: stage chunks with tensor-tile copies where the sweep qualifies
+  unsigned* err = nullptr;  // set to 1 (atomicOr) if a staged chunk did not arrive within the bound
+  int* tma_used = nullptr;  // host: set to 1 when the launch was TMA-staged
 };
+
+// Tensor maps of a TMA-staged fluid sweep (kernel axes 1 and 2), dimensions
+// ordered (lane axis A, row axis O, sweep axis D).  full[]: one chunk of 4
+// positions, for rho, m_d, m_t1, m_t2, e, b_A, b_O (32 x 4 x 4), b_d
+// (32 x 4 x 5), b_A of the next block's first 4 lanes (4 x 4 x 4; only its
+// row form is used) and b_O of its first row (32 x 1 x 4); row[]: the same
+// boxes one position long.
+constexpr int kFluidMaps = 10;
+struct FluidMaps {
+  CUtensorMap full[kFluidMaps];
+  CUtensorMap row[kFluidMaps];
+};
+// Encode the maps of a sweep along kernel axis 1 or 2; false if the box does
+// not qualify (lane extent not a multiple of 32, row extent not a multiple of
+// 4, unaligned fields) or the driver's encoder is unavailable.
+bool make_fluid_maps(int axis, const FluidArgs& a, FluidMaps* m);
 
 struct MagArgs {
   const float* in[8];

@@ -41,6 +41,80 @@ struct Axes {
 
 constexpr int kFluidWarps = 4;
 
+// TMA staging of the y and z kernel-axis sweeps.  One thread of the block
+// copies each 4-position chunk of the block's 32 x 4 pencils into shared
+// memory with 3-D tensor-tile copies, one chunk ahead of the chunk the warps
+// compute on (two buffers, one mbarrier each).  A chunk buffer holds, as
+// [position][row][lane] floats: rho, m_d, m_t1, m_t2, e, the face field b_A
+// of the lane axis and b_O of the row axis (4 positions each), b_d at 5
+// positions (the high face of the last cell), and the two neighbour pencils
+// one block over: b_A at lanes 32..35 (4 rows x 4 lanes per position, each
+// position in its own 128-byte slot: a tile copy lands on a 128-byte
+// boundary) and b_O at row 4 (4 x 32).  Chunks that cross the periodic wrap
+// along the pencil, and the b_A edge always, are copied one position at a
+// time (the row maps).
+constexpr int kTmaCh = 4;                                  // positions per chunk
+constexpr int kTmaField = kTmaCh * kFluidWarps * 32;       // 512 floats
+constexpr int kTmaOffBd = 7 * kTmaField;                   // b_d: 5 positions
+constexpr int kTmaOffAe = kTmaOffBd + (kTmaCh + 1) * kFluidWarps * 32;  // b_A, lanes 32..35
+constexpr int kTmaAeSlot = 32;                             // floats per position of the b_A edge
+constexpr int kTmaOffOe = kTmaOffAe + kTmaCh * kTmaAeSlot; // b_O, row 4
+constexpr int kTmaFloats = kTmaOffOe + kTmaCh * 32;        // 4480 floats = 17,920 bytes
+constexpr int kTmaBytes = (kTmaFloats - kTmaCh * (kTmaAeSlot - 4 * kFluidWarps)) * 4;  // 17,664 copied
+constexpr long long kSweepSpinLimit = 1LL << 22;          // polls of a chunk's mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool sweep_mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kSweepSpinLimit; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Copy chunk `p0 .. p0+3` (b_d to p0+4) of the block at lane x0, row y0 into
+// the buffer at `dst` and arm its mbarrier with the chunk's bytes.
+__device__ __forceinline__ void tma_issue_chunk(const FluidMaps* mp, uint32_t dst, uint32_t bar, int x0, int y0,
+                                                int xe, int ye, int p0, int nD) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaBytes) : "memory");
+  const bool whole = p0 >= 0 && p0 + kTmaCh < nD;
+  if (whole) {
+#pragma unroll
+    for (int f = 0; f < 7; f++) tma_load3(dst + f * kTmaField * 4, &mp->full[f], x0, y0, p0, bar);
+    tma_load3(dst + kTmaOffBd * 4, &mp->full[7], x0, y0, p0, bar);
+    tma_load3(dst + kTmaOffOe * 4, &mp->full[9], x0, ye, p0, bar);
+  }
+#pragma unroll
+  for (int j = 0; j < kTmaCh; j++)
+    tma_load3(dst + (kTmaOffAe + j * kTmaAeSlot) * 4, &mp->row[8], xe, y0, wrap_near<false>(p0 + j, nD), bar);
+  if (!whole) {  // across the periodic wrap: one position at a time
+    for (int j = 0; j <= kTmaCh; j++) {
+      const int q = wrap_near<false>(p0 + j, nD);
+      tma_load3(dst + (kTmaOffBd + j * kFluidWarps * 32) * 4, &mp->row[7], x0, y0, q, bar);
+      if (j == kTmaCh) break;
+#pragma unroll
+      for (int f = 0; f < 7; f++)
+        tma_load3(dst + (f * kTmaField + j * kFluidWarps * 32) * 4, &mp->row[f], x0, y0, q, bar);
+      tma_load3(dst + (kTmaOffOe + j * 32) * 4, &mp->row[9], x0, ye, q, bar);
+    }
+  }
+}
+
 // x sweeps: each warp stages 8 cells x 32 pencils of every source field in
 // shared memory (rows padded to 9 floats: conflict-free column reads), loaded
 // as 32-byte row pieces so each DRAM sector is fetched by exactly one load.
@@ -67,16 +141,19 @@ __device__ __forceinline__ void stage_rows(float* tile, const float* __restrict_
   }
 }
 
-// 4 blocks of 128 threads per SM, so at most 128 registers per thread: the
-// RATE variant spills a few words at that limit (it needs about 160), which
-// measured faster than 3 blocks per SM without spills (1.77 against 1.85 ms
-// at 512^3).
-template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, int FRZ>
-__global__ void __launch_bounds__(32 * kFluidWarps, 4)
-fluid_sweep_kernel(FluidArgs a) {
+// The sweep of one block.  TMA = true (kernel axes 1 and 2, single boxes
+// whose lane extent is a multiple of 32 and row extent a multiple of 4): the
+// chunks come from the shared-memory ring the block's first thread fills with
+// tensor-tile copies (`mp`); the arithmetic is the same as with register loads.
+template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, int FRZ, bool TMA>
+__device__ __forceinline__ void fluid_sweep_body(const FluidArgs& a, const FluidMaps* mp) {
   using X = Axes<D>;
+  static_assert(!TMA || (D != 0 && !SMALL), "TMA staging: kernel axes 1 and 2, long pencils");
   constexpr int CH = (D == 0) ? kXChunk : 4;  // positions per chunk
+  static_assert(!TMA || CH == kTmaCh, "chunk of the staged layout");
   __shared__ float xs[(D == 0) ? kFluidWarps * kXTiles * kXTile : 1];
+  __shared__ alignas(128) float tb[TMA ? 2 * kTmaFloats : 1];
+  __shared__ alignas(8) unsigned long long tbar[2];
   const int lane = threadIdx.x;
   const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, a.rate);
   const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
@@ -119,6 +196,28 @@ fluid_sweep_kernel(FluidArgs a) {
   // warm-up cell so that x chunks start 16-byte aligned)
   const int nchunk = (G.seg + 7 + CH - 1) / CH;
 
+  // staged chunks: this thread's element of a field, and the element of its
+  // neighbour pencil along A (lane 31: the b_A edge columns) and along O
+  // (row 3: the b_O edge row); per-position strides of those two
+  const int w = threadIdx.y;
+  const int t0 = w * 32 + lane;
+  const int nbA = lane < 31 ? 5 * kTmaField + t0 + 1 : kTmaOffAe + w * 4;
+  const int nbA_step = lane < 31 ? kFluidWarps * 32 : kTmaAeSlot;
+  const int nbO = w < kFluidWarps - 1 ? 6 * kTmaField + t0 + 32 : kTmaOffOe + lane;
+  const int nbO_step = w < kFluidWarps - 1 ? kFluidWarps * 32 : 32;
+  const int tid = w * 32 + lane;
+  const int x0 = G.bx * 32, y0 = G.by * kFluidWarps;
+  const int xe = wrapi(x0 + 32, nA), ye = wrapi(y0 + kFluidWarps, nO);  // neighbour blocks' first lane / row
+  if constexpr (TMA) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[0])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[1])) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) tma_issue_chunk(mp, smem_u32(tb), smem_u32(&tbar[0]), x0, y0, xe, ye, s0 - 4, nD);
+  }
+
   FluidPipe<LIM, FRZ> pipe;
   pipe.init();
   if constexpr (FRZ == 2) {  // the pencil's freezing speeds (two reduction passes before the sweep)
@@ -130,14 +229,27 @@ fluid_sweep_kernel(FluidArgs a) {
   float rmax = 0.f;
   const bool rate_pencil = RATE && pa >= a.rate_lo[X::A] && pa < a.rate_hi[X::A] && pb >= a.rate_lo[X::O] &&
                            pb < a.rate_hi[X::O];
+  bool gave_up = false;  // TMA: a chunk's copies did not arrive within the bound
+  int issued = 1;        // TMA: chunks issued so far (the same count in every thread)
 
   for (int c = 0; c < nchunk; c++) {
     const int p0 = s0 - 4 + CH * c;  // first position of this chunk
-    // D != 0: the chunk's planes in registers; D == 0: staged rows in shared memory
-    float U[(D == 0) ? 1 : CH][5], B[(D == 0) ? 1 : CH][3];
+    // D != 0: the chunk's planes in registers or staged; D == 0: staged rows
+    float U[(D == 0 || TMA) ? 1 : CH][5], B[(D == 0 || TMA) ? 1 : CH][3];
     const float* row = xw + lane * kXPad;
+    const float* sb = tb + (TMA ? (c & 1) * kTmaFloats : 0);
     float bd_next = 0.f;
-    if constexpr (D == 0) {
+    if constexpr (TMA) {
+      // every warp is done with chunk c-1, whose buffer receives chunk c+1
+      if (__syncthreads_or(gave_up)) break;
+      if (c + 1 < nchunk) {
+        if (tid == 0)
+          tma_issue_chunk(mp, smem_u32(tb + ((c + 1) & 1) * kTmaFloats), smem_u32(&tbar[(c + 1) & 1]), x0, y0, xe,
+                          ye, p0 + CH, nD);
+        issued++;
+      }
+      if (!sweep_mbar_wait(smem_u32(&tbar[c & 1]), (c >> 1) & 1)) gave_up = true;
+    } else if constexpr (D == 0) {
       __syncwarp();
       stage_rows<SMALL>(xw + 0 * kXTile, rho, base, p0, nD, lane);
       stage_rows<SMALL>(xw + 1 * kXTile, md, base, p0, nD, lane);
@@ -191,7 +303,17 @@ fluid_sweep_kernel(FluidArgs a) {
 #pragma unroll
     for (int j = 0; j < CH; j++) {
       float o[5], Uj[5], Bj[3];
-      if constexpr (D == 0) {
+      if constexpr (TMA) {
+        const int e = t0 + j * kFluidWarps * 32;  // [position j][row w][lane]
+#pragma unroll
+        for (int q = 0; q < 5; q++) Uj[q] = sb[q * kTmaField + e];
+        const float bA = sb[5 * kTmaField + e], bO = sb[6 * kTmaField + e];
+        const float bA1 = sb[nbA + j * nbA_step], bO1 = sb[nbO + j * nbO_step];
+        // cell-centred field: mean of the low and high face of the cell
+        Bj[0] = face_mean(sb[kTmaOffBd + e], sb[kTmaOffBd + e + kFluidWarps * 32]);
+        Bj[1] = (X::T1 == X::A) ? face_mean(bA, bA1) : face_mean(bO, bO1);
+        Bj[2] = (X::T2 == X::A) ? face_mean(bA, bA1) : face_mean(bO, bO1);
+      } else if constexpr (D == 0) {
 #pragma unroll
         for (int q = 0; q < 5; q++) Uj[q] = row[q * kXTile + j];
         const float hi = (j + 1 < CH) ? row[5 * kXTile + j + 1] : bd_next;
@@ -233,10 +355,38 @@ fluid_sweep_kernel(FluidArgs a) {
       }
     }
   }
+  if constexpr (TMA) {
+    if (__syncthreads_or(gave_up)) {
+      // record the failure, then let the copies still in flight (the last
+      // two chunks issued) land before the block's shared memory is released
+      if (tid == 0) {
+        atomicOr(a.err, 1u);
+        for (int q = max(0, issued - 2); q < issued; q++) sweep_mbar_wait(smem_u32(&tbar[q & 1]), (q >> 1) & 1);
+      }
+      return;
+    }
+  }
   if (RATE) {
     for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     if (lane == 0) atomicMax(G.rate, __float_as_uint(rmax));
   }
+}
+
+// 4 blocks of 128 threads per SM, so at most 128 registers per thread: the
+// RATE variant spills a few words at that limit (it needs about 160), which
+// measured faster than 3 blocks per SM without spills (1.77 against 1.85 ms
+// at 512^3).
+template <int D, bool RATE, bool SMALL, bool FLOOR, int LIM, int FRZ>
+__global__ void __launch_bounds__(32 * kFluidWarps, 4)
+fluid_sweep_kernel(FluidArgs a) {
+  fluid_sweep_body<D, RATE, SMALL, FLOOR, LIM, FRZ, false>(a, nullptr);
+}
+
+// The TMA-staged sweep (kernel axes 1 and 2, the paper's scheme).
+template <int D, bool RATE, bool FLOOR>
+__global__ void __launch_bounds__(32 * kFluidWarps, 4)
+fluid_sweep_tma_kernel(const __grid_constant__ FluidArgs a, const __grid_constant__ FluidMaps mp) {
+  fluid_sweep_body<D, RATE, false, FLOOR, 0, 0, true>(a, &mp);
 }
 
 // Launch of one fluid sweep with scheme (LIM, FRZ): kernel axis, fused CFL
@@ -252,6 +402,19 @@ cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
   const bool small = a.box.n[axis] < 16;
   const bool floor = a.p_floor > 0.f;
+  if constexpr (LIM == 0 && FRZ == 0) {  // the paper's scheme: TMA-staged y and z kernel-axis sweeps
+    FluidMaps mp;
+    if (a.tma && !a.ens.items && axis != 0 && !small && make_fluid_maps(axis, a, &mp)) {
+      if (a.tma_used) *a.tma_used = 1;
+#define FLUID_TMA_CASE(DD, RR, FF) \
+  if (axis == DD && rate == RR && floor == FF) fluid_sweep_tma_kernel<DD, RR, FF><<<grid, block, 0, s>>>(a, mp);
+      FLUID_TMA_CASE(1, false, false) FLUID_TMA_CASE(1, true, false) FLUID_TMA_CASE(2, false, false)
+      FLUID_TMA_CASE(2, true, false) FLUID_TMA_CASE(1, false, true) FLUID_TMA_CASE(1, true, true)
+      FLUID_TMA_CASE(2, false, true) FLUID_TMA_CASE(2, true, true)
+#undef FLUID_TMA_CASE
+      return cudaGetLastError();
+    }
+  }
 #define FLUID_CASE(DD, RR)                                                                            \
   if (axis == DD && rate == RR) {                                                                     \
     if (floor) {                                                                                      \

@@ -47,6 +47,8 @@ SIGNATURES = {
     "mhd_set_segments": (_I, [_P, _I, _I, _I]),
     "mhd_set_xpath": (_I, [_P, _I]),
     "mhd_set_fusion": (_I, [_P, _I]),
+    "mhd_set_tma": (_I, [_P, _I]),
+    "mhd_tma_sweeps": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "mhd_create_f64": (_P, [_I, _I, _I, _D]),
     "mhd_set_state_f64": (_I, [_P, _PP, _I]),
     "mhd_get_state_f64": (_I, [_P, _PP, _I]),
@@ -290,6 +292,18 @@ class Box:
         """Run the two middle z magnetic sweeps of a step as one launch (on,
         the default) or as two (off); the state is bitwise the same."""
         _check(self.lib.mhd_set_fusion(self.h, int(bool(on))))
+
+    def set_tma(self, on: bool):
+        """Stage the y and z kernel-axis fluid sweeps' input with TMA tile
+        copies where the box qualifies (on, the default) or use register
+        loads (off); the state is bitwise the same."""
+        _check(self.lib.mhd_set_tma(self.h, int(bool(on))))
+
+    def tma_sweeps(self) -> int:
+        """Fluid sweeps this box has launched TMA-staged so far."""
+        n = ctypes.c_longlong(0)
+        _check(self.lib.mhd_tma_sweeps(self.h, ctypes.byref(n)))
+        return int(n.value)
 
     def set_xpath(self, mode: int):
         """x sweeps: 1 direct, 2 through the x<->y exchanged layout, 0 automatic;
