@@ -39,7 +39,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 struct Scalars {  // small device block
   float tau;
   unsigned rate[2];
-  unsigned err;  // 1: a staged chunk of a fluid sweep did not arrive within the wait bound
+  unsigned err;  // 1: a staged chunk of a sweep did not arrive within the wait bound
   double time;
   double diag[10];
 };
@@ -71,8 +71,8 @@ struct mhd_s {
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   int fuse = 1;         // 1: the two z magnetic sweeps of a step run as one launch
-  int tma = 1;          // 1: y and z kernel-axis fluid sweeps stage their chunks with TMA where they qualify
-  long long tma_sweeps = 0;  // fluid sweeps launched TMA-staged
+  int tma = 1;          // 1: y and z kernel-axis sweeps stage their chunks with TMA where they qualify
+  long long tma_sweeps = 0;  // sweeps launched TMA-staged
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
   double cpl[3] = {0.0, 0.0, 0.0};  // cells per unit length per physical axis (0: n, the unit box)
   int own_lo[3] = {0, 0, 0};        // own cells [own_lo, own_hi) per physical axis (the others are
@@ -410,11 +410,16 @@ int magnetic(mhd_s* m, int d, int passes = 1) {
   a.seg = m->seg[d];
   a.lim = m->lim;
   a.passes = passes;
+  int staged = 0;
+  a.tma = m->tma;
+  a.err = &m->sc->err;
+  a.tma_used = &staged;
   rc = traced(m, MHD_K_MAG_X + d, [&] {
     CK(mhd::launch_mag(ka, a, m->stream));
     return MHD_OK;
   });
   if (rc) return rc;
+  m->tma_sweeps += staged;
   for (int q = 5; q < 8; q++) std::swap(m->cur[q], m->spare[q]);
   return MHD_OK;
 }
@@ -805,7 +810,7 @@ int mhd_cfl_dt(mhd_t* m, double cfl, double* dt_full) {
   CK(cudaStreamSynchronize(m->stream));
   if (w[2]) {
     *dt_full = 0.0;
-    return fail(MHD_E_TIMEOUT, "a staged chunk of a fluid sweep did not arrive within the wait bound");
+    return fail(MHD_E_TIMEOUT, "a staged chunk of a sweep did not arrive within the wait bound");
   }
   float r;
   std::memcpy(&r, &w[m->rcur], sizeof r);

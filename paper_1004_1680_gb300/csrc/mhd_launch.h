@@ -64,6 +64,13 @@ struct FluidArgs {
 // (32 x 4 x 5), b_A of the next block's first 4 lanes (4 x 4 x 4; only its
 // row form is used) and b_O of its first row (32 x 1 x 4); row[]: the same
 // boxes one position long.
+// A 3-D tensor map of FP32 elements: tensor extents dim (the first
+// contiguous), byte strides st of dimensions 1 and 2, box b0 x b1 x b2;
+// out-of-range elements read as zero.  False if the driver's encoder is
+// unavailable or rejects the map (tma_maps.cu).
+bool tma_encode_f32(CUtensorMap* m, const float* p, const cuuint64_t dim[3], const cuuint64_t st[2], cuuint32_t b0,
+                    cuuint32_t b1, cuuint32_t b2);
+
 constexpr int kFluidMaps = 10;
 struct FluidMaps {
   CUtensorMap full[kFluidMaps];
@@ -84,6 +91,9 @@ struct MagArgs {
   int nblocks = 0;
   int lim = 0;         // slope limiter (as FluidArgs::lim)
   int passes = 1;      // 2: two sweeps with the same step in one launch (kernel axis 2 only)
+  int tma = 0;              // 1: stage chunks with tensor-tile copies where the sweep qualifies
+  unsigned* err = nullptr;  // set to 1 (atomicOr) if a staged chunk did not arrive within the bound
+  int* tma_used = nullptr;  // host: set to 1 when the launch was TMA-staged
 };
 
 // Ghost layers of a non-periodic axis (boundary.cu): kernel axis `axis` of
@@ -258,6 +268,19 @@ extern template cudaError_t prepare_mag_t<1>();
 extern template cudaError_t prepare_mag_t<2>();
 // one-time per-device kernel attributes (call on the current device before launching)
 cudaError_t prepare_mag_kernels();
+// Tensor maps of a TMA-staged magnetic sweep (kernel axes 1 and 2), dimensions
+// ordered (lane axis A, row axis O, sweep axis D): rho, m_D, b_A, b_O, b_D
+// over the 32 x 8 tile (32 x 8 x 4), rho, m_D, b_O one row (32 x 1 x 4) and
+// rho, m_D, b_A four columns (4 x 8 x 4) of the neighbouring pencils; row[]:
+// the same boxes one position long.
+constexpr int kMagMaps = 11;
+struct MagMaps {
+  CUtensorMap full[kMagMaps];
+  CUtensorMap row[kMagMaps];
+};
+// false if the box does not qualify (lane extent not a multiple of 32, row
+// extent not a multiple of 8, unaligned fields) or the encoder is unavailable
+bool make_mag_maps(int axis, const MagArgs& a, MagMaps* m);
 // cells [lo, hi) per kernel axis (the interior of a box with ghost layers)
 struct CellRange {
   int lo[3], hi[3];

@@ -8,37 +8,6 @@ namespace mhd {
 
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, looked up once through the runtime.
-EncodeTiled encoder() {
-  static const EncodeTiled fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return (EncodeTiled) nullptr;
-    }
-    return reinterpret_cast<EncodeTiled>(p);
-  }();
-  return fn;
-}
-
-// A box of b0 x b1 x b2 FP32 elements of a tensor of extents dim (the first
-// contiguous) and byte strides st of dimensions 1 and 2; out-of-range
-// elements read as zero.
-bool encode(CUtensorMap* m, const float* p, const cuuint64_t dim[3], const cuuint64_t st[2], cuuint32_t b0,
-            cuuint32_t b1, cuuint32_t b2) {
-  const cuuint32_t box[3] = {b0, b1, b2}, es[3] = {1, 1, 1};
-  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(p), dim, st, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // The fields of one sweep and the box: a step cycles through a few such sets
 // (the fields alternate between two arrays), so the encoded maps are kept.
 struct MapKey {
@@ -79,21 +48,20 @@ bool make_fluid_maps(int axis, const FluidArgs& a, FluidMaps* out) {
       *out = e.maps;
       return true;
     }
-  if (!encoder()) return false;
   const cuuint64_t dim[3] = {(cuuint64_t)b.n[A], (cuuint64_t)b.n[O], (cuuint64_t)b.n[D]};
   const cuuint64_t st[2] = {(cuuint64_t)b.stride[O] * 4, (cuuint64_t)b.stride[D] * 4};
   const float* f[7] = {a.in[RHO], a.in[MX + D], a.in[MX + T1], a.in[MX + T2], a.in[EN], a.in[BX + A], a.in[BX + O]};
   FluidMaps m;
   bool ok = true;
   for (int k = 0; k < 7; k++)
-    ok = ok && encode(&m.full[k], f[k], dim, st, 32, kFluidWarps, kTmaCh) &&
-         encode(&m.row[k], f[k], dim, st, 32, kFluidWarps, 1);
-  ok = ok && encode(&m.full[7], a.in[BX + D], dim, st, 32, kFluidWarps, kTmaCh + 1) &&
-       encode(&m.row[7], a.in[BX + D], dim, st, 32, kFluidWarps, 1);
-  ok = ok && encode(&m.full[8], a.in[BX + A], dim, st, 4, kFluidWarps, kTmaCh) &&
-       encode(&m.row[8], a.in[BX + A], dim, st, 4, kFluidWarps, 1);
-  ok = ok && encode(&m.full[9], a.in[BX + O], dim, st, 32, 1, kTmaCh) &&
-       encode(&m.row[9], a.in[BX + O], dim, st, 32, 1, 1);
+    ok = ok && tma_encode_f32(&m.full[k], f[k], dim, st, 32, kFluidWarps, kTmaCh) &&
+         tma_encode_f32(&m.row[k], f[k], dim, st, 32, kFluidWarps, 1);
+  ok = ok && tma_encode_f32(&m.full[7], a.in[BX + D], dim, st, 32, kFluidWarps, kTmaCh + 1) &&
+       tma_encode_f32(&m.row[7], a.in[BX + D], dim, st, 32, kFluidWarps, 1);
+  ok = ok && tma_encode_f32(&m.full[8], a.in[BX + A], dim, st, 4, kFluidWarps, kTmaCh) &&
+       tma_encode_f32(&m.row[8], a.in[BX + A], dim, st, 4, kFluidWarps, 1);
+  ok = ok && tma_encode_f32(&m.full[9], a.in[BX + O], dim, st, 32, 1, kTmaCh) &&
+       tma_encode_f32(&m.row[9], a.in[BX + O], dim, st, 32, 1, 1);
   if (!ok) return false;
   MapEntry& e = cache[next];
   next = (next + 1) % kMapCache;

@@ -26,6 +26,7 @@
 #pragma once
 #include "mhd_device.cuh"
 #include "mhd_launch.h"
+#include "tma.cuh"
 
 namespace mhd {
 
@@ -61,32 +62,6 @@ constexpr int kTmaAeSlot = 32;                             // floats per positio
 constexpr int kTmaOffOe = kTmaOffAe + kTmaCh * kTmaAeSlot; // b_O, row 4
 constexpr int kTmaFloats = kTmaOffOe + kTmaCh * 32;        // 4480 floats = 17,920 bytes
 constexpr int kTmaBytes = (kTmaFloats - kTmaCh * (kTmaAeSlot - 4 * kFluidWarps)) * 4;  // 17,664 copied
-constexpr long long kSweepSpinLimit = 1LL << 22;          // polls of a chunk's mbarrier
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-          "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ bool sweep_mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kSweepSpinLimit; i++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 // Copy chunk `p0 .. p0+3` (b_d to p0+4) of the block at lane x0, row y0 into
 // the buffer at `dst` and arm its mbarrier with the chunk's bytes.
 __device__ __forceinline__ void tma_issue_chunk(const FluidMaps* mp, uint32_t dst, uint32_t bar, int x0, int y0,

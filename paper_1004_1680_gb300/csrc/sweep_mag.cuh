@@ -26,6 +26,7 @@
 #pragma once
 #include "mhd_device.cuh"
 #include "mhd_launch.h"
+#include "tma.cuh"
 
 namespace mhd {
 
@@ -268,8 +269,50 @@ struct MagShared {
 
 enum { kRoleInterior = 0, kRoleHaloRow = 1, kRoleHaloCol = 2 };
 
-template <int D, bool SMALL, int LIM, int NP, int ROLE>
-__device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom& G, MagShared<NP>& sh) {
+// TMA staging (mag_sweep_tma_kernel): thread 0 copies chunk c+2 into shared
+// memory while the block computes chunk c and reads chunk c+1 (two buffers,
+// one mbarrier each; a buffer is read only while its chunk's v_D is
+// published, before that chunk's barrier).  A chunk buffer holds, as
+// [position][row][lane] floats, rho, m_D, b_A, b_O, b_D of the 32 x 8 tile;
+// rho and m_D of the row below it and rho, m_D, b_O of the row above it
+// (32 lanes); rho, m_D of the four columns left of it and rho, m_D, b_A of
+// the four columns right of it (only the nearest column is read).
+constexpr int kMRho = 0, kMMd = 1024, kMBA = 2048, kMBO = 3072, kMBD = 4096;  // 4 x 8 x 32
+constexpr int kMRhoDn = 5120, kMMdDn = 5248, kMRhoUp = 5376, kMMdUp = 5504, kMBOUp = 5632;  // 4 x 32
+constexpr int kMRhoL = 5760, kMMdL = 5888, kMRhoR = 6016, kMMdR = 6144, kMBAR = 6272;      // 4 x 8 x 4
+constexpr int kMagTmaFloats = 6400;  // 25,600 bytes per chunk
+constexpr size_t kMagTmaSmem = 2 * kMagTmaFloats * 4 + 128;  // dynamic, plus alignment to 128 bytes
+
+// Copy chunk p0 .. p0+3 of the tile at lane x0, row y0 (neighbour rows ydn,
+// yup, neighbour columns from xl and xr) into the buffer at `dst`.
+__device__ __forceinline__ void mag_issue_chunk(const MagMaps* mp, uint32_t dst, uint32_t bar, int x0, int y0,
+                                                int ydn, int yup, int xl, int xr, int p0, int nD) {
+  mbar_expect_tx(bar, kMagTmaFloats * 4);
+  const bool whole = p0 >= 0 && p0 + kMagCH <= nD;
+  const int npos = whole ? 1 : kMagCH;  // across the periodic wrap: one position at a time
+  for (int j = 0; j < npos; j++) {
+    const CUtensorMap* m = whole ? mp->full : mp->row;
+    const int q = whole ? p0 : wrap_near<false>(p0 + j, nD);
+    const uint32_t d = dst + 4 * j * 256, r = dst + 4 * j * 32;  // main boxes / row and column boxes
+#pragma unroll
+    for (int f = 0; f < 5; f++) tma_load3(d + 4 * f * 1024, &m[f], x0, y0, q, bar);
+    tma_load3(r + 4 * kMRhoDn, &m[5], x0, ydn, q, bar);
+    tma_load3(r + 4 * kMMdDn, &m[6], x0, ydn, q, bar);
+    tma_load3(r + 4 * kMRhoUp, &m[5], x0, yup, q, bar);
+    tma_load3(r + 4 * kMMdUp, &m[6], x0, yup, q, bar);
+    tma_load3(r + 4 * kMBOUp, &m[7], x0, yup, q, bar);
+    tma_load3(r + 4 * kMRhoL, &m[8], xl, y0, q, bar);
+    tma_load3(r + 4 * kMMdL, &m[9], xl, y0, q, bar);
+    tma_load3(r + 4 * kMRhoR, &m[8], xr, y0, q, bar);
+    tma_load3(r + 4 * kMMdR, &m[9], xr, y0, q, bar);
+    tma_load3(r + 4 * kMBAR, &m[10], xr, y0, q, bar);
+  }
+}
+
+template <int D, bool SMALL, int LIM, int NP, int ROLE, bool TMA = false>
+__device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom& G, MagShared<NP>& sh,
+                                              const MagMaps* mp = nullptr, const float* tb = nullptr,
+                                              unsigned long long* tfull = nullptr) {
   constexpr bool kEarly = D == 1;  // next chunk's loads before the current chunk's arithmetic
   using X = MagAxes<D>;
   constexpr int CH = kMagCH;
@@ -383,6 +426,47 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
   float bP1 = 0.f, bP2 = 0.f, bP3 = 0.f;  // b_D after the first pass at faces t-3, t-4, t-5
 
   float cv[CH], cq2[CH], cq4[CH];  // own v_D; the advected value(s) of the current chunk
+  // TMA: the same five values per position from the staged chunk at sb
+  auto load_staged = [&](const float* sb, float (&r0)[CH], float (&r1)[CH], float (&r2)[CH], float (&r3)[CH],
+                         float (&r4)[CH]) {
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+      if constexpr (ROLE == kRoleInterior) {
+        const int e = j * 256 + w * 32 + lane;
+        r0[j] = sb[kMRho + e];
+        r1[j] = sb[kMMd + e];
+        r2[j] = sb[kMBA + e];
+        r3[j] = sb[kMBO + e];
+        r4[j] = sb[kMBD + e];
+      } else if constexpr (ROLE == kRoleHaloRow) {
+        const int e = j * 32 + lane;
+        r0[j] = sb[kMRhoUp + e];
+        r1[j] = sb[kMMdUp + e];
+        r2[j] = sb[kMBOUp + e];
+        r3[j] = sb[kMRhoDn + e];
+        r4[j] = sb[kMMdDn + e];
+      } else {
+        const int e = j * 32 + min(lane, kMagWarps - 1) * 4;
+        r0[j] = sb[kMRhoR + e];
+        r1[j] = sb[kMMdR + e];
+        r2[j] = sb[kMBAR + e];
+        r3[j] = sb[kMRhoL + e + 3];
+        r4[j] = sb[kMMdL + e + 3];
+      }
+    }
+  };
+  const int tid = w * 32 + lane;
+  bool gave_up = false;  // TMA: a bounded wait ran out (block-uniform after each barrier)
+  int issued = 0;        // TMA: chunks issued so far (the same count in every thread)
+  const int ydn = wrapi(b0 - 1, nO), yup = wrapi(b0 + kMagWarps, nO);
+  const int xl = wrapi(a0 - 4, nA), xr = wrapi(a0 + 32, nA);
+  if constexpr (TMA) {
+    if (tid == 0)
+      for (int k = 0; k < 2 && k < nchunk; k++)
+        mag_issue_chunk(mp, smem_u32(tb + k * kMagTmaFloats), smem_u32(&tfull[k]), a0, b0, ydn, yup, xl, xr,
+                        s0 - 4 * NP + CH * k, nD);
+    issued = min(2, nchunk);
+  }
   auto load_chunk = [&](int p0, float (&r0)[CH], float (&r1)[CH], float (&r2)[CH], float (&r3)[CH],
                         float (&r4)[CH]) {
 #pragma unroll
@@ -416,18 +500,36 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
   };
   {
     float r0[CH], r1[CH], r2[CH], r3[CH], r4[CH];
-    load_chunk(s0 - 4 * NP, r0, r1, r2, r3, r4);
+    if constexpr (TMA) {
+      if (!sweep_mbar_wait(smem_u32(&tfull[0]), 0)) gave_up = true;
+      load_staged(tb, r0, r1, r2, r3, r4);
+    } else {
+      load_chunk(s0 - 4 * NP, r0, r1, r2, r3, r4);
+    }
     publish(0, r0, r1, r2, r3, r4);
   }
-  __syncthreads();
+  if constexpr (TMA) {
+    if (__syncthreads_or(gave_up)) gave_up = true;
+  } else {
+    __syncthreads();
+  }
 
-  for (int c = 0; c < nchunk; c++) {
+  for (int c = 0; c < nchunk && !gave_up; c++) {
     const int p0 = s0 - 4 * NP + CH * c;
     const bool more = c + 1 < nchunk;
     const int buf = c & 1;
     float n0[CH], n1[CH], n2[CH], n3[CH], n4[CH];
-    if (kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
-    if (!kEarly && more) {  // the next chunk's lines into L2 during the arithmetic
+    if constexpr (TMA) {
+      // chunk c+2 into the buffer chunk c was read from (before the last barrier)
+      if (c + 2 < nchunk) {
+        if (tid == 0)
+          mag_issue_chunk(mp, smem_u32(tb + buf * kMagTmaFloats), smem_u32(&tfull[buf]), a0, b0, ydn, yup, xl, xr,
+                          p0 + 2 * CH, nD);
+        issued++;
+      }
+    }
+    if (!TMA && kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
+    if (!TMA && !kEarly && more) {  // the next chunk's lines into L2 during the arithmetic
 #pragma unroll
       for (int j = 0; j < CH; j++) {
         const unsigned off = (unsigned)(wrap_near<SMALL>(p0 + CH + j, nD) * sD);
@@ -484,9 +586,23 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
         }
       }
     }
-    if (!kEarly && more) load_chunk(p0 + CH, n0, n1, n2, n3, n4);
+    if constexpr (TMA) {
+      if (more) {
+        if (!sweep_mbar_wait(smem_u32(&tfull[(c + 1) & 1]), ((c + 1) >> 1) & 1)) gave_up = true;
+        load_staged(tb + ((c + 1) & 1) * kMagTmaFloats, n0, n1, n2, n3, n4);
+      }
+    } else if (!kEarly && more) {
+      load_chunk(p0 + CH, n0, n1, n2, n3, n4);
+    }
     if (more) publish((c + 1) & 1, n0, n1, n2, n3, n4);
-    __syncthreads();
+    if constexpr (TMA) {
+      if (__syncthreads_or(gave_up)) {
+        gave_up = true;
+        break;
+      }
+    } else {
+      __syncthreads();
+    }
     if constexpr (ROLE == kRoleInterior) {
       if (interior) {
 #pragma unroll
@@ -511,6 +627,14 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
       }
     }
   }
+  if constexpr (TMA) {
+    if (gave_up && tid == 0) {
+      // record the failure and let the copies still in flight (at most the
+      // last two chunks issued) land before the shared memory is released
+      atomicOr(a.err, 1u);
+      for (int q = max(0, issued - 2); q < issued; q++) sweep_mbar_wait(smem_u32(&tfull[q & 1]), (q >> 1) & 1);
+    }
+  }
 }
 
 template <int D, bool SMALL, int LIM, int NP>
@@ -525,6 +649,28 @@ mag_sweep_pipe_kernel(MagArgs a) {
   else mag_pipe_role<D, SMALL, LIM, NP, kRoleHaloCol>(a, G, sh);
 }
 
+// The TMA-staged sweep along y and z (the paper's scheme, long pencils, tiles
+// that divide the box): kMagTmaSmem bytes of dynamic shared memory.
+template <int D, int NP>
+__global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
+mag_sweep_tma_kernel(const __grid_constant__ MagArgs a, const __grid_constant__ MagMaps mp) {
+  __shared__ MagShared<NP> sh;
+  extern __shared__ float mag_dyn[];
+  __shared__ alignas(8) unsigned long long tfull[2];
+  const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, nullptr);
+  // the buffers start at the first 128-byte boundary (a tile copy lands on one)
+  const float* tb = mag_dyn + ((128u - (smem_u32(mag_dyn) & 127u)) & 127u) / 4;
+  if (threadIdx.y == 0 && threadIdx.x == 0) {
+    mbar_init(smem_u32(&tfull[0]), 1);
+    mbar_init(smem_u32(&tfull[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.y < kMagWarps) mag_pipe_role<D, false, 0, NP, kRoleInterior, true>(a, G, sh, &mp, tb, tfull);
+  else if (threadIdx.y == kMagWarps) mag_pipe_role<D, false, 0, NP, kRoleHaloRow, true>(a, G, sh, &mp, tb, tfull);
+  else mag_pipe_role<D, false, 0, NP, kRoleHaloCol, true>(a, G, sh, &mp, tb, tfull);
+}
+
 // The x sweep stages rows in more than 48 KB of shared memory; the limit is
 // raised once per device before any launch (never during a graph capture).
 template <int LIM>
@@ -534,6 +680,17 @@ cudaError_t prepare_mag_t() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mag_sweep_kernel<0, false, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kMagXSmem);
+  if constexpr (LIM == 0) {  // the staged sweeps of the paper's scheme
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMagTmaSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMagTmaSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMagTmaSmem);
+  }
   return e;
 }
 
@@ -552,6 +709,16 @@ cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
   MAG_CASE(0, kMagXSmem)
 #undef MAG_CASE
   if (a.passes == 2 && axis == 0) return cudaErrorInvalidValue;  // the staged x kernel runs one pass
+  if constexpr (LIM == 0) {
+    MagMaps mp;
+    if (a.tma && !a.ens.items && !small && axis != 0 && make_mag_maps(axis, a, &mp)) {
+      if (a.tma_used) *a.tma_used = 1;
+      if (axis == 1) mag_sweep_tma_kernel<1, 1><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      else if (a.passes == 2) mag_sweep_tma_kernel<2, 2><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      else mag_sweep_tma_kernel<2, 1><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      return cudaGetLastError();
+    }
+  }
   if (axis == 1) {
     if (small) mag_sweep_pipe_kernel<1, true, LIM, 1><<<grid, block, 0, s>>>(a);
     else mag_sweep_pipe_kernel<1, false, LIM, 1><<<grid, block, 0, s>>>(a);

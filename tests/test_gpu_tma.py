@@ -1,14 +1,15 @@
-"""TMA-staged fluid sweeps (kernel axes 1 and 2) against the register-load
-sweeps and against the FP64 oracle.
+"""TMA-staged sweeps (kernel axes 1 and 2) against the register-load sweeps
+and against the FP64 oracle.
 
-The staged sweep reads the same values and does the same arithmetic, so the
-state must be bitwise that of the register-load sweep: after single sweeps,
-full steps with the fused CFL rate, the optional pressure floor, segmented
-pencils (interior segments never cross the periodic wrap, the end segments
-do) and the x sweeps through the exchanged layout (kernel axis 1 with the
-lanes along y).  Boxes qualify when the contiguous axis is a multiple of 32
-and the row axis a multiple of 4; `tma_sweeps` shows that the staged kernel
-ran.
+A staged sweep reads the same values and does the same arithmetic, so the
+state must be bitwise that of the register-load sweep: after single fluid and
+magnetic sweeps, full steps with the fused CFL rate and the fused pair of z
+magnetic sweeps, the optional pressure floor, segmented pencils (interior
+segments never cross the periodic wrap, the end segments do) and the x
+sweeps through the exchanged layout (kernel axis 1 with the lanes along y).
+Boxes qualify when the contiguous axis is a multiple of 32 and the row axis a
+multiple of 4 (fluid) or 8 (magnetic); `tma_sweeps` shows that the staged
+kernels ran.
 """
 import numpy as np
 import pytest
@@ -46,19 +47,20 @@ def pair(mhd, st64, **cfg):
 
 
 @pytest.mark.parametrize("axis", [1, 2])
-def test_single_staged_sweep_is_bitwise_the_register_sweep(mhd, axis):
-    st = ic.turbulence((64, 32, 20), seed=31, dtype=torch.float64, kmin=1.0, kmax=4.0)
+@pytest.mark.parametrize("kind", [0, 1])
+def test_single_staged_sweep_is_bitwise_the_register_sweep(mhd, axis, kind):
+    st = ic.turbulence((64, 32, 24), seed=31, dtype=torch.float64, kmin=1.0, kmax=4.0)
     a, b = pair(mhd, st)
     tau = 0.35 / oracle.cfl_rate(ic.as_oracle_input(st), G)
-    a.sweep(axis, 0, tau)
-    b.sweep(axis, 0, tau)
+    a.sweep(axis, kind, tau)
+    b.sweep(axis, kind, tau)
     assert a.tma_sweeps() == 1 and b.tma_sweeps() == 0
     assert torch.equal(a.get_state(), b.get_state())
 
 
 @pytest.mark.parametrize("dims, cfg", [
     ((32, 32, 32), {}),                                  # one block column, whole pencils
-    ((64, 32, 20), {"segs": (0, 16, 4)}),                # z segments of 4: wrapped chunks in every segment
+    ((64, 32, 24), {"segs": (0, 16, 4)}),                # z segments of 4: wrapped chunks in every segment
     ((32, 64, 48), {"segs": (0, 32, 16)}),               # interior segments with no wrap
     ((64, 64, 16), {"xpath": 2}),                        # x sweeps through the exchanged layout
     ((32, 32, 24), {"floor": 1e-3}),                     # the pressure-floor variant
@@ -81,23 +83,27 @@ def test_staged_steps_are_bitwise_the_register_steps(mhd, dims, cfg):
 
 
 @pytest.mark.parametrize("axis", [1, 2])
-def test_staged_sweep_parity_with_oracle(mhd, axis):
+@pytest.mark.parametrize("kind", [0, 1])
+def test_staged_sweep_parity_with_oracle(mhd, axis, kind):
     st = ic.turbulence((64, 32, 24), seed=41, dtype=torch.float64, kmin=1.0, kmax=4.0)
     s = ic.as_oracle_input(st)
     tau = 0.35 / oracle.cfl_rate(s, G)
     nz, ny, nx = st.shape[1:]
     box = mhd.Box(nx, ny, nz, gamma=G)
     box.set_state(to_gpu(st))
-    box.sweep(axis, 0, tau)
+    box.sweep(axis, kind, tau)
     assert box.tma_sweeps() == 1
-    oracle.fluid_sweep(s, axis, tau, G)
+    if kind == 0:
+        oracle.fluid_sweep(s, axis, tau, G)
+    else:
+        oracle.mag_sweep(s, axis, tau)
     err = rel_err(from_gpu(box.get_state()), s, field_scales(s))
     assert np.all(err < 1e-5), err
 
 
 def test_staged_full_step_parity_with_oracle(mhd):
-    """One full step of 64 x 32 x 24 turbulence, every y and z fluid sweep
-    staged: within the non-smooth one-step bound (1e-4) of the oracle."""
+    """One full step of 64 x 32 x 24 turbulence, every y and z sweep staged:
+    within the non-smooth one-step bound (1e-4) of the oracle."""
     st = ic.turbulence((64, 32, 24), seed=43, dtype=torch.float64, kmin=1.0, kmax=4.0)
     s = ic.as_oracle_input(st)
     nz, ny, nx = st.shape[1:]
@@ -105,7 +111,7 @@ def test_staged_full_step_parity_with_oracle(mhd):
     box.set_state(to_gpu(st))
     dt = oracle.cfl_dt(s, G, 0.7)
     box.step(dt)
-    assert box.tma_sweeps() >= 4
+    assert box.tma_sweeps() >= 7  # 4 fluid sweeps, 2 magnetic y sweeps, the fused z pair
     oracle.step(s, dt, G)
     err = rel_err(from_gpu(box.get_state()), s, field_scales(s))
     assert np.all(err < 1e-4), err
