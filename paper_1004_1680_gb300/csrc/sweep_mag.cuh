@@ -283,10 +283,14 @@ constexpr int kMRhoL = 5760, kMMdL = 5888, kMRhoR = 6016, kMMdR = 6144, kMBAR = 
 constexpr int kMagTmaFloats = 6400;  // 25,600 bytes per chunk
 constexpr size_t kMagTmaSmem = 2 * kMagTmaFloats * 4 + 128;  // dynamic, plus alignment to 128 bytes
 
-// Copy chunk p0 .. p0+3 of the tile at lane x0, row y0 (neighbour rows ydn,
-// yup, neighbour columns from xl and xr) into the buffer at `dst`.
+// Copy chunk p0 .. p0+3 of the tile at lane x0, row y0 and of its periodic
+// neighbour rows and columns into the buffer at `dst`.  The neighbours'
+// coordinates are formed here by compare and select (x0, y0 lie inside the
+// box) rather than kept in every thread's registers.
 __device__ __forceinline__ void mag_issue_chunk(const MagMaps* mp, uint32_t dst, uint32_t bar, int x0, int y0,
-                                                int ydn, int yup, int xl, int xr, int p0, int nD) {
+                                                int nA, int nO, int p0, int nD) {
+  const int ydn = y0 == 0 ? nO - 1 : y0 - 1, yup = y0 + kMagWarps == nO ? 0 : y0 + kMagWarps;
+  const int xl = x0 == 0 ? nA - 4 : x0 - 4, xr = x0 + 32 == nA ? 0 : x0 + 32;
   mbar_expect_tx(bar, kMagTmaFloats * 4);
   const bool whole = p0 >= 0 && p0 + kMagCH <= nD;
   const int npos = whole ? 1 : kMagCH;  // across the periodic wrap: one position at a time
@@ -458,12 +462,10 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
   const int tid = w * 32 + lane;
   bool gave_up = false;  // TMA: a bounded wait ran out (block-uniform after each barrier)
   int issued = 0;        // TMA: chunks issued so far (the same count in every thread)
-  const int ydn = wrapi(b0 - 1, nO), yup = wrapi(b0 + kMagWarps, nO);
-  const int xl = wrapi(a0 - 4, nA), xr = wrapi(a0 + 32, nA);
   if constexpr (TMA) {
     if (tid == 0)
       for (int k = 0; k < 2 && k < nchunk; k++)
-        mag_issue_chunk(mp, smem_u32(tb + k * kMagTmaFloats), smem_u32(&tfull[k]), a0, b0, ydn, yup, xl, xr,
+        mag_issue_chunk(mp, smem_u32(tb + k * kMagTmaFloats), smem_u32(&tfull[k]), a0, b0, nA, nO,
                         s0 - 4 * NP + CH * k, nD);
     issued = min(2, nchunk);
   }
@@ -523,7 +525,7 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
       // chunk c+2 into the buffer chunk c was read from (before the last barrier)
       if (c + 2 < nchunk) {
         if (tid == 0)
-          mag_issue_chunk(mp, smem_u32(tb + buf * kMagTmaFloats), smem_u32(&tfull[buf]), a0, b0, ydn, yup, xl, xr,
+          mag_issue_chunk(mp, smem_u32(tb + buf * kMagTmaFloats), smem_u32(&tfull[buf]), a0, b0, nA, nO,
                           p0 + 2 * CH, nD);
         issued++;
       }
