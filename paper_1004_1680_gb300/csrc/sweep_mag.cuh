@@ -543,51 +543,62 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
       }
     }
     float bDold[CH];  // raw b_D at the face each position's constraint updates
+    // Every cell and face the chunk finishes lies in this segment: the
+    // interior warps of the staged single-pass sweep then store without
+    // per-position tests (`all`, a literal at each call; the fused pair
+    // would spill with the second copy of its loops).
+    const bool steady = TMA && NP == 1 && ROLE == kRoleInterior && p0 - kLag >= s0 && p0 + CH - kLag < s1;
+    auto advect = [&](const bool all) {
 #pragma unroll
-    for (int j = 0; j < CH; j++) {
-      const float vj = cv[j];
-      float nA_new = 0.f, nO_new = 0.f;
-      if constexpr (kA_) {  // flux along A: interior and halo column
-        const float uA = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vAr][vAc]));
-        const float fa = pA.step(cq2[j], uA, c_half, c_full, nA_new);
-        if (wr_col) sh.fA[0][buf][j][row][col] = fa;
-        if constexpr (NP == 2) {
-          float q2;
-          const float fa2 = qA.step(nA_new, uA3, c_half, c_full, q2);
-          if (wr_col) sh.fA[1][buf][j][row][col] = fa2;
-          nA_new = q2;
-          uA3 = uA2;
-          uA2 = uA1;
-          uA1 = uA;
+      for (int j = 0; j < CH; j++) {
+        const float vj = cv[j];
+        float nA_new = 0.f, nO_new = 0.f;
+        if constexpr (kA_) {  // flux along A: interior and halo column
+          const float uA = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vAr][vAc]));
+          const float fa = pA.step(cq2[j], uA, c_half, c_full, nA_new);
+          if (wr_col) sh.fA[0][buf][j][row][col] = fa;
+          if constexpr (NP == 2) {
+            float q2;
+            const float fa2 = qA.step(nA_new, uA3, c_half, c_full, q2);
+            if (wr_col) sh.fA[1][buf][j][row][col] = fa2;
+            nA_new = q2;
+            uA3 = uA2;
+            uA2 = uA1;
+            uA1 = uA;
+          }
+        }
+        if constexpr (kO_) {  // flux along O: interior and halo row
+          const float qin = (ROLE == kRoleInterior) ? cq3[j] : cq2[j];
+          const float uO = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vOr][vOc]));
+          const float fo = pO.step(qin, uO, c_half, c_full, nO_new);
+          if (wr_row) sh.fO[0][buf][j][row][col] = fo;
+          if constexpr (NP == 2) {
+            float q2;
+            const float fo2 = qO.step(nO_new, uO3, c_half, c_full, q2);
+            if (wr_row) sh.fO[1][buf][j][row][col] = fo2;
+            nO_new = q2;
+            uO3 = uO2;
+            uO2 = uO1;
+            uO1 = uO;
+          }
+        }
+        if constexpr (ROLE == kRoleInterior) {
+          bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
+          bD2 = bD1;
+          bD1 = cq4[j];
+          const int po = p0 + j - kLag;
+          if (all || (interior && po >= s0 && po < s1)) {
+            const unsigned cell = ib + (unsigned)(po * sD);  // po is inside [s0, s1)
+            o_bA[cell] = nA_new;
+            o_bO[cell] = nO_new;
+          }
         }
       }
-      if constexpr (kO_) {  // flux along O: interior and halo row
-        const float qin = (ROLE == kRoleInterior) ? cq3[j] : cq2[j];
-        const float uO = __fmul_rn(0.5f, __fadd_rn(vj, sh.v[buf][j][vOr][vOc]));
-        const float fo = pO.step(qin, uO, c_half, c_full, nO_new);
-        if (wr_row) sh.fO[0][buf][j][row][col] = fo;
-        if constexpr (NP == 2) {
-          float q2;
-          const float fo2 = qO.step(nO_new, uO3, c_half, c_full, q2);
-          if (wr_row) sh.fO[1][buf][j][row][col] = fo2;
-          nO_new = q2;
-          uO3 = uO2;
-          uO2 = uO1;
-          uO1 = uO;
-        }
-      }
-      if constexpr (ROLE == kRoleInterior) {
-        bDold[j] = bD2;  // b_D at position t-2, the face of edge t-5/2
-        bD2 = bD1;
-        bD1 = cq4[j];
-        const int po = p0 + j - kLag;
-        if (interior && po >= s0 && po < s1) {
-          const unsigned cell = ib + (unsigned)(po * sD);  // po is inside [s0, s1)
-          o_bA[cell] = nA_new;
-          o_bO[cell] = nO_new;
-        }
-      }
-    }
+    };
+    if (steady)
+      advect(true);
+    else
+      advect(false);
     if constexpr (TMA) {
       if (more) {
         if (!sweep_mbar_wait(smem_u32(&tfull[(c + 1) & 1]), ((c + 1) >> 1) & 1)) gave_up = true;
@@ -606,7 +617,7 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
       __syncthreads();
     }
     if constexpr (ROLE == kRoleInterior) {
-      if (interior) {
+      auto constraint = [&](const bool all) {
 #pragma unroll
         for (int j = 0; j < CH; j++) {
           const int t = p0 + j;
@@ -624,9 +635,13 @@ __device__ __forceinline__ void mag_pipe_role(const MagArgs& a, const BlockGeom&
             b = b2;
           }
           const int pf = t - kLag + 1;
-          if (pf >= s0 && pf < s1) o_bD[ib + (unsigned)(pf * sD)] = b;  // pf is inside [s0, s1)
+          if (all || (pf >= s0 && pf < s1)) o_bD[ib + (unsigned)(pf * sD)] = b;  // pf is inside [s0, s1)
         }
-      }
+      };
+      if (steady)
+        constraint(true);
+      else if (interior)
+        constraint(false);
     }
   }
   if constexpr (TMA) {
