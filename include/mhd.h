@@ -190,9 +190,11 @@ int mhd_set_fusion(mhd_t *m, int on);
  * is a multiple of 4 reads its input through the Tensor Memory Accelerator:
  * one thread per block copies the next 4 positions of the block's 32 x 4
  * pencils into shared memory while the block computes the current ones.
- * The values and their arithmetic are those of the register-load sweep, so
- * the state is bitwise the same either way; on = 0 always uses register
- * loads.  Ensembles, ablations and boxes that do not qualify use register
+ * The values and their arithmetic are those of the register-load sweep,
+ * except that the staged fluid sweep takes the freezing speeds' square
+ * roots from the hardware approximation (a few ulp; the faster choice on
+ * each path), so the two paths agree to FP32 rounding, not bitwise (the
+ * magnetic sweeps bitwise); on = 0 always uses register loads.  Ensembles, ablations and boxes that do not qualify use register
  * loads.  If a staged chunk does not arrive within the bounded wait (about
  * half a second), the block records the failure and stops; mhd_cfl_dt then
  * returns MHD_E_TIMEOUT until the next mhd_set_state.  MHD_E_ARG unless on

@@ -95,14 +95,16 @@ __device__ __forceinline__ float v_sub(float a, float b) { return __fsub_rn(a, b
 __device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float v_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float v_div(float a, float b) { return __fmul_rn(a, rcp_ftz(b)); }
-// Square root of the freezing speeds: the multi-function unit's
-// approximation with subnormals flushed (relative error of a few ulp, one
-// instruction; the IEEE sqrtf adds a refinement and a slow-path branch per
-// call).  Its arguments are squared signal speeds of valid cells, far from
-// the subnormal range.  With the sweeps' input staged by TMA it took the
-// fluid sweep 1.225 -> 1.135 ms at 512^3 (the plain approximation 1.144);
-// with register loads it had measured slower.
-__device__ __forceinline__ float v_sqrt(float a) {
+__device__ __forceinline__ float v_sqrt(float a) { return sqrtf(a); }
+// The freezing speeds' square root of the TMA-staged fluid sweeps: the
+// multi-function unit's approximation with subnormals flushed (relative
+// error of a few ulp, one instruction; sqrtf adds a refinement and a
+// slow-path branch).  Its arguments are squared signal speeds of valid
+// cells, far from the subnormal range.  Measured at 512^3: the staged fluid
+// sweep 1.225 -> 1.135 ms with it, but the register-load sweep 1.35 -> 1.70
+// ms, so each path keeps the faster one (the two then agree to FP32
+// rounding rather than bitwise).
+__device__ __forceinline__ float v_sqrt_fast(float a) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
   return r;
@@ -180,9 +182,12 @@ __device__ __forceinline__ V5 half_limited5(const V5& a, const V5& b) {
 // s = a^2 + v_A^2 (an ablation: the smallest freezing speed the relaxation
 // allows); 2 the given speed c_given (one value per pencil and stage: the
 // largest bound along the pencil, another ablation).
-template <int FRZ = 0>
+// FSQ: the freezing speed's square root from v_sqrt_fast (the TMA-staged
+// sweeps) instead of v_sqrt.
+template <int FRZ = 0, bool FSQ = false>
 __device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, float gamma, V5& FR, V5& FL,
                                            float c_given = 0.f) {
+  auto root = [](float x) { return FSQ ? v_sqrt_fast(x) : v_sqrt(x); };
   const float md = u.p0.y;
   const float rinv = v_div(1.f, u.p0.x);
   const float vd = v_mul(md, rinv);
@@ -202,11 +207,11 @@ __device__ __forceinline__ void split_flux(const V5& u, float bd, float2 bt, flo
     const float vad2 = v_mul(v_mul(bd, bd), rinv);
     const float sum = v_add(a2, va2);
     const float disc = v_fma(v_mul(-4.f, a2), vad2, v_mul(sum, sum));
-    hc = v_mul(0.5f, v_add(v_abs(vd), v_sqrt(v_mul(0.5f, v_add(sum, v_sqrt(fmaxf(disc, 0.f)))))));
+    hc = v_mul(0.5f, v_add(v_abs(vd), root(v_mul(0.5f, v_add(sum, root(fmaxf(disc, 0.f)))))));
   } else if constexpr (FRZ == 2) {
     hc = v_mul(0.5f, c_given);
   } else {
-    hc = v_mul(0.5f, v_add(v_abs(vd), v_sqrt(v_mul(v_fma(gamma, p, b2), rinv))));
+    hc = v_mul(0.5f, v_add(v_abs(vd), root(v_mul(v_fma(gamma, p, b2), rinv))));
   }
   FR.p0 = __ffma2_rn(f2(hc), u.p0, __fmul2_rn(f2(0.5f), F01));
   FR.p1 = __ffma2_rn(f2(hc), u.p1, __fmul2_rn(f2(0.5f), F23));
@@ -273,7 +278,8 @@ __device__ __forceinline__ float face_mean(float lo, float hi) { return __fmul_r
 //             Unew(t-3)    = U(t-3) - tau/h (F2(t-5/2) - F2(t-7/2))
 // so Unew at position t-3 is produced at step t (the 7-point stencil of
 // Section II.B).  Every intermediate value is held in registers.
-template <int LIM = 0, int FRZ = 0>
+// FSQ: the fast square root of split_flux (the TMA-staged sweeps).
+template <int LIM = 0, int FRZ = 0, bool FSQ = false>
 struct FluidPipe {
   V5 U1, U2, U3;   // raw U at t-1, t-2, t-3
   float b1[3];     // frozen b at t-1
@@ -297,11 +303,11 @@ struct FluidPipe {
                                        float c_full, float out[5]) {
     const V5 u = {make_float2(U[0], U[1]), make_float2(U[2], U[3]), U[4]};
     V5 FR, FL;
-    split_flux<FRZ>(u, b[0], make_float2(b[1], b[2]), gamma, FR, FL, c1);
+    split_flux<FRZ, FSQ>(u, b[0], make_float2(b[1], b[2]), gamma, FR, FL, c1);
     const V5 f1 = v5_sub(FR1, FL);
     const V5 Uh = v5_fma(-c_half, v5_sub(f1, f1m), U1);
     V5 Rh, Lh;
-    split_flux<FRZ>(Uh, b1[0], make_float2(b1[1], b1[2]), gamma, Rh, Lh, c2);
+    split_flux<FRZ, FSQ>(Uh, b1[0], make_float2(b1[1], b1[2]), gamma, Rh, Lh, c2);
     // the left-hand differences were the right-hand ones one step earlier
     const V5 dR2 = v5_sub(Rh2, Rh3), dL1 = v5_sub(Lh, Lh2);
     const V5 right = v5_add(Rh3, half_limited5<LIM>(dR3, dR2));

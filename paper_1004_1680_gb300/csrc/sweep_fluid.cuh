@@ -193,7 +193,7 @@ __device__ __forceinline__ void fluid_sweep_body(const FluidArgs& a, const Fluid
     if (tid == 0) tma_issue_chunk(mp, smem_u32(tb), smem_u32(&tbar[0]), x0, y0, xe, ye, s0 - 4, nD);
   }
 
-  FluidPipe<LIM, FRZ> pipe;
+  FluidPipe<LIM, FRZ, TMA> pipe;  // the staged sweep takes the fast square root
   pipe.init();
   if constexpr (FRZ == 2) {  // the pencil's freezing speeds (two reduction passes before the sweep)
     const int pc = ib * nA + ia;

@@ -294,9 +294,10 @@ class Box:
         _check(self.lib.mhd_set_fusion(self.h, int(bool(on))))
 
     def set_tma(self, on: bool):
-        """Stage the y and z kernel-axis fluid sweeps' input with TMA tile
-        copies where the box qualifies (on, the default) or use register
-        loads (off); the state is bitwise the same."""
+        """Stage the y and z kernel-axis sweeps' input with TMA tile copies
+        where the box qualifies (on, the default) or use register loads
+        (off); the two agree to FP32 rounding (the staged fluid sweep takes
+        the hardware square root approximation)."""
         _check(self.lib.mhd_set_tma(self.h, int(bool(on))))
 
     def tma_sweeps(self) -> int:

@@ -47,6 +47,7 @@ def test_members_equal_single_boxes(mhd, xpath, segdiv):
     for b, st in enumerate(sts):
         box = mhd.Box(*DIMS[b], gamma=G)
         box.set_xpath(xpath)
+        box.set_tma(False)  # the ensemble's register-load sweeps
         box.set_state(st.to(torch.float32).contiguous().cuda())
         box.run(3, 0.7)
         assert torch.equal(ens.get_state(b), box.get_state()), b

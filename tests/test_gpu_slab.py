@@ -13,9 +13,14 @@ pytestmark = pytest.mark.gpu
 DIMS = (24, 20, 64)
 
 
+# (24, 20, 64): register-load sweeps; (32, 32, 64): every y and z sweep of
+# the whole box and of the slab boxes (16 own + 32 halo planes or more) is
+# TMA-staged, so both sides take the same arithmetic
+@pytest.mark.parametrize("dims", [DIMS, (32, 32, 64)])
 @pytest.mark.parametrize("world", [1, 2, 4])
-def test_gpu_slabs_reproduce_the_whole_box(world):
+def test_gpu_slabs_reproduce_the_whole_box(world, dims):
     from paper_1004_1680_gb300 import mhd
+    DIMS = dims
     st = ic.turbulence(DIMS, seed=12, dtype=torch.float64, kmin=1.0, kmax=4.0).to(torch.float32).cuda()
     whole = mhd.Box(*DIMS)
     whole.set_state(st)

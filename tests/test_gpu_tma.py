@@ -1,15 +1,19 @@
 """TMA-staged sweeps (kernel axes 1 and 2) against the register-load sweeps
 and against the FP64 oracle.
 
-A staged sweep reads the same values and does the same arithmetic, so the
-state must be bitwise that of the register-load sweep: after single fluid and
-magnetic sweeps, full steps with the fused CFL rate and the fused pair of z
-magnetic sweeps, the optional pressure floor, segmented pencils (interior
-segments never cross the periodic wrap, the end segments do) and the x
-sweeps through the exchanged layout (kernel axis 1 with the lanes along y).
-Boxes qualify when the contiguous axis is a multiple of 32 and the row axis a
-multiple of 4 (fluid) or 8 (magnetic); `tma_sweeps` shows that the staged
-kernels ran.
+A staged sweep reads the same values and does the same arithmetic as the
+register-load sweep, except that the staged fluid sweep takes the freezing
+speeds' square roots from the hardware approximation (a few ulp): magnetic
+sweeps must be bitwise those of the register path, and fluid sweeps and
+full steps equal to it within FP32 rounding (1e-6 of the field scales, four
+orders below the one-step parity bound against the oracle).  Covered: single
+fluid and magnetic sweeps, full steps with the fused CFL rate and the fused
+pair of z magnetic sweeps, the optional pressure floor, segmented pencils
+(interior segments never cross the periodic wrap, the end segments do) and
+the x sweeps through the exchanged layout (kernel axis 1 with the lanes
+along y).  Boxes qualify when the contiguous axis is a multiple of 32 and
+the row axis a multiple of 4 (fluid) or 8 (magnetic); `tma_sweeps` shows
+that the staged kernels ran.
 """
 import numpy as np
 import pytest
@@ -46,16 +50,27 @@ def pair(mhd, st64, **cfg):
     return boxes
 
 
+def close_to(a, b, tol=1e-6):
+    """max per-field |a - b| / field scale, the scales of the FP64 state a"""
+    sa = a.to(torch.float64).cpu().numpy()
+    err = rel_err(b.to(torch.float64).cpu().numpy(), sa, field_scales(sa))
+    return bool(np.all(err < tol)), err
+
+
 @pytest.mark.parametrize("axis", [1, 2])
 @pytest.mark.parametrize("kind", [0, 1])
-def test_single_staged_sweep_is_bitwise_the_register_sweep(mhd, axis, kind):
+def test_single_staged_sweep_matches_the_register_sweep(mhd, axis, kind):
     st = ic.turbulence((64, 32, 24), seed=31, dtype=torch.float64, kmin=1.0, kmax=4.0)
     a, b = pair(mhd, st)
     tau = 0.35 / oracle.cfl_rate(ic.as_oracle_input(st), G)
     a.sweep(axis, kind, tau)
     b.sweep(axis, kind, tau)
     assert a.tma_sweeps() == 1 and b.tma_sweeps() == 0
-    assert torch.equal(a.get_state(), b.get_state())
+    if kind == 1:  # the magnetic sweeps share all of their arithmetic
+        assert torch.equal(a.get_state(), b.get_state())
+    else:
+        ok, err = close_to(a.get_state(), b.get_state())
+        assert ok, err
 
 
 @pytest.mark.parametrize("dims, cfg", [
@@ -66,19 +81,21 @@ def test_single_staged_sweep_is_bitwise_the_register_sweep(mhd, axis, kind):
     ((32, 32, 24), {"floor": 1e-3}),                     # the pressure-floor variant
     ((96, 32, 28), {"segs": (0, 8, 0), "xpath": 2}),     # 3 block columns, ragged z chunking
 ])
-def test_staged_steps_are_bitwise_the_register_steps(mhd, dims, cfg):
+def test_staged_steps_match_the_register_steps(mhd, dims, cfg):
     st = ic.turbulence(dims, seed=37, dtype=torch.float64, kmin=1.0, kmax=3.0, mach=0.8)
     a, b = pair(mhd, st, **cfg)
     for _ in range(2):
         dt = a.cfl_dt(0.7)
-        assert dt == b.cfl_dt(0.7)
+        assert abs(dt - b.cfl_dt(0.7)) <= 1e-6 * dt
         a.step(dt)
         b.step(dt)
-        assert torch.equal(a.get_state(), b.get_state())
+        ok, err = close_to(a.get_state(), b.get_state())
+        assert ok, err
     a.run(3, 0.7)
     b.run(3, 0.7)
-    assert torch.equal(a.get_state(), b.get_state())
-    assert a.time() == b.time()
+    ok, err = close_to(a.get_state(), b.get_state(), 5e-6)
+    assert ok, err
+    assert abs(a.time() - b.time()) <= 1e-6 * a.time()
     assert a.tma_sweeps() > 0 and b.tma_sweeps() == 0
 
 
