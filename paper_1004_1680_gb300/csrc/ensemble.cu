@@ -141,7 +141,11 @@ int build_lists(mhd_ens_s* e) {
         const mhd::EnsBox& b = e->boxes[bi];
         int n[3] = {L ? b.n[1] : b.n[0], L ? b.n[0] : b.n[1], b.n[2]};
         minext = std::min(minext, n[ka]);
-        const int gx = (n[A] + 31) / 32, gy = (n[O] + W - 1) / W, gz = n[ka] / b.seg[d];
+        // fluid y and z kernel axes: runs of 32 W consecutive pencils (the
+        // kernel's row-order mapping); otherwise tiles of 32 x W pencils
+        const bool runs = kind == 0 && ka != 0;
+        const int gx = runs ? (n[A] * n[O] + 32 * W - 1) / (32 * W) : (n[A] + 31) / 32;
+        const int gy = runs ? 1 : (n[O] + W - 1) / W, gz = n[ka] / b.seg[d];
         for (int z = 0; z < gz; z++)
           for (int y = 0; y < gy; y++)
             for (int x = 0; x < gx; x++) items.push_back(make_int4(bi, x, y, z));

@@ -132,8 +132,22 @@ __device__ __forceinline__ void fluid_sweep_body(const FluidArgs& a, const Fluid
   const int lane = threadIdx.x;
   const BlockGeom G = block_geom(a.ens, a.box, a.seg, a.tau, a.rate);
   const int nA = G.box.n[X::A], nO = G.box.n[X::O], nD = G.box.n[D];
-  const int pa = G.bx * 32 + lane;
-  const int pb = G.by * kFluidWarps + threadIdx.y;
+  // Pencils of the block: the TMA-staged and x sweeps take a tile of 32
+  // lanes x kFluidWarps rows; the register-load y and z sweeps take 32 x
+  // kFluidWarps consecutive pencils in row order (lane axis fastest), so a
+  // lane extent that is not a multiple of 32 (48 in the ensemble's boxes)
+  // leaves no lane idle: a warp then spans at most two rows, each a
+  // contiguous piece.
+  constexpr bool kLinear = !TMA && D != 0;
+  int pa, pb;
+  if constexpr (kLinear) {
+    const int P = G.bx * (32 * kFluidWarps) + threadIdx.y * 32 + lane;
+    pb = P / nA;
+    pa = P - pb * nA;
+  } else {
+    pa = G.bx * 32 + lane;
+    pb = G.by * kFluidWarps + threadIdx.y;
+  }
   const bool active = (pa < nA) && (pb < nO);
   const int ia = min(pa, nA - 1), ib = min(pb, nO - 1);
   const int sA = (int)G.box.stride[X::A], sO = (int)G.box.stride[X::O], sD = (int)G.box.stride[D];
@@ -381,8 +395,13 @@ template <int LIM, int FRZ>
 cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t s) {
   const int A = (axis == 0) ? 1 : 0, O = (axis == 2) ? 1 : 2;
   dim3 block(32, kFluidWarps);
-  dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kFluidWarps - 1) / kFluidWarps,
-            a.box.n[axis] / a.seg);
+  // tiles of 32 x kFluidWarps pencils (TMA-staged and x sweeps) or runs of
+  // 32 kFluidWarps consecutive pencils (register-load y and z sweeps)
+  const dim3 tiles((a.box.n[A] + 31) / 32, (a.box.n[O] + kFluidWarps - 1) / kFluidWarps, a.box.n[axis] / a.seg);
+  dim3 grid = axis == 0 ? tiles
+                        : dim3((unsigned)(((long long)a.box.n[A] * a.box.n[O] + 32 * kFluidWarps - 1) /
+                                          (32 * kFluidWarps)),
+                               1, a.box.n[axis] / a.seg);
   // ensemble launches: one block per work item; `small` must hold for every
   // box of the launch (the host passes the smallest extent in a.box)
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
@@ -393,7 +412,7 @@ cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t
     if (a.tma && !a.ens.items && axis != 0 && !small && make_fluid_maps(axis, a, &mp)) {
       if (a.tma_used) *a.tma_used = 1;
 #define FLUID_TMA_CASE(DD, RR, FF) \
-  if (axis == DD && rate == RR && floor == FF) fluid_sweep_tma_kernel<DD, RR, FF><<<grid, block, 0, s>>>(a, mp);
+  if (axis == DD && rate == RR && floor == FF) fluid_sweep_tma_kernel<DD, RR, FF><<<tiles, block, 0, s>>>(a, mp);
       FLUID_TMA_CASE(1, false, false) FLUID_TMA_CASE(1, true, false) FLUID_TMA_CASE(2, false, false)
       FLUID_TMA_CASE(2, true, false) FLUID_TMA_CASE(1, false, true) FLUID_TMA_CASE(1, true, true)
       FLUID_TMA_CASE(2, false, true) FLUID_TMA_CASE(2, true, true)
