@@ -190,21 +190,52 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   uint64_t* empty = full + NS;
   uint64_t* ofull = empty + NS;
   uint64_t* ofree = ofull + kRing;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ofree + kRing);
+  uint64_t* wfull = ofree + kRing;  // the weight image has landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wfull + 1);
   const uint32_t tmem_cols = (uint32_t)(NACC * kRing * npad);  // 128 .. 512, a power of two
 
   const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
   const int tiles_x = nx / kTX, tiles_y = ny / TY;
   const int ntiles = tiles_x * tiles_y * nz;
+  // The block's run of tiles.  With at least one block per column the runs
+  // stay inside one column (a run that crosses into the next column copies
+  // two more halo planes, and the slowest block sets the launch's time):
+  // column c gets blocks b with b C / B = c and splits its nz tiles evenly.
+  // Otherwise blocks take equal contiguous ranges of whole-column order.
+  const int ncol = tiles_x * tiles_y, nblk = gridDim.x;
   TileRun run;
-  run.t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-  run.count = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x) - run.t0;
+  if (ncol <= nblk) {
+    const int c = (int)((long long)blockIdx.x * ncol / nblk);
+    const int b0 = (int)(((long long)c * nblk + ncol - 1) / ncol);
+    const int b1 = (int)(((long long)(c + 1) * nblk + ncol - 1) / ncol);
+    const int kc = b1 - b0, r = blockIdx.x - b0;  // kc <= nz: the grid has at most ncol * nz blocks
+    const int lo = r * nz / kc, hi = (r + 1) * nz / kc;
+    run.t0 = c * nz + lo;
+    run.count = hi - lo;
+  } else {
+    run.t0 = (int)((long long)blockIdx.x * ntiles / nblk);
+    run.count = (int)((long long)(blockIdx.x + 1) * ntiles / nblk) - run.t0;
+  }
   run.nz = nz;
   run.tiles_x = tiles_x;
 
-  // zero pad cells; the copying warps start on the input planes while the
-  // other six warps copy the weights (a straight copy of the packed image,
-  // once per block) and meet on a named barrier before the first MMA
+  // the weights first: bBytes (a multiple of 16) from a 16-byte aligned
+  // image, in flight while the block sets up (the barrier's initialisation
+  // is ordered before any wait on it by the block barrier below)
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(wfull)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(wfull)), "r"(bBytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(sB)),
+                 "l"(a.wpack), "r"(bBytes), "r"(smem_addr(wfull))
+                 : "memory");
+  }
+
+  // zero pad cells; the packed weight image (once per block) comes in one
+  // bulk asynchronous copy that the MMA threads wait for, while the copying
+  // warps start on the input planes
   for (int i = tid; i < NS * G * 4; i += 256)
     *reinterpret_cast<uint4*>(ring + (i / 4) * R::PLANE + (kHX * R::HY + i % 4) * 16) = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 32) sBias[tid] = (a.bias && tid < a.cout) ? __ldg(a.bias + tid) : 0.f;
@@ -230,14 +261,6 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const bool copier = (warp == 2 || warp == 3);
-  if (!copier) {
-    const int wt = tid < 64 ? tid : tid - 64;  // 0..191 over warps 0, 1, 4..7
-    for (int i = wt; i < bBytes / 16; i += 192)
-      reinterpret_cast<uint4*>(sB)[i] = __ldg(reinterpret_cast<const uint4*>(a.wpack) + i);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights, for the tensor core
-    asm volatile("bar.sync 1, 192;" ::: "memory");
-  }
 
   bool ok = true;
   if (warp < NACC) {
@@ -249,6 +272,7 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
       const uint32_t dq = tmem + (uint32_t)(q * kRing * npad);
       int k = 0;          // input planes consumed
       int last_out = -1;  // last output plane committed
+      ok = mbar_wait(smem_addr(wfull), 0);
       for (int i0 = 0; i0 < run.count && ok;) {
         // the column segment of tiles i0 .. i0 + L - 1 (outputs g = i0 + u)
         int L = 1;
@@ -412,6 +436,9 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
     }
   }
   if (!ok) atomicExch(a.err, 1);
+  // the weight copy has landed before the shared memory is released (at once
+  // unless a wait above gave up)
+  if (tid == 0) mbar_wait(smem_addr(wfull), 0);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -890,7 +917,7 @@ size_t conv_smem_bytes(int npad, int kchunks, int cin, int ty) {
                                : (cin == 32 ? ConvRing<4, 16>::SLOT : ConvRing<1, 16>::SLOT);
   // weights, ring, bias, the input and output slot mbarriers, TMEM address
   return ((b + 1023) & ~(size_t)1023) + ConvRing<4, 32>::NSLOT * slot + 32 * sizeof(float) +
-         (2 * ConvRing<4, 32>::NSLOT + 2 * kRing) * 8 + 16;
+         (2 * ConvRing<4, 32>::NSLOT + 2 * kRing + 1) * 8 + 16;
 }
 
 namespace {
