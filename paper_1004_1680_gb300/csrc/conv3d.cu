@@ -67,6 +67,15 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// One tcgen05.mma (kind::f16, cta_group::1) that accumulates into D.
+__device__ __forceinline__ void mma_acc(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(1u)
+      : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long long i = 0; i < kSpinLimit; i++) {
     uint32_t done;
@@ -291,6 +300,35 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
           // the (ky, kx) offset is a shift of the start address.
           const uint64_t a0 = make_desc(smem_addr(ring + (k % NS) * R::SLOT), G == 4 ? R::PLANE : 16, kHX * 16) +
                               (uint64_t)(q * 16 * kHX);
+          // The plane's output blocks j0 = jlo .. jhi (output planes gtop - j0
+          // in ring slots kRing - 1 - (gtop - j0) % kRing, adjacent except
+          // across the end of the ring) as at most three MMA segments, found
+          // once per plane: `f` for the plane's first K step, where a block
+          // that starts its output plane (j0 = 0) goes alone with accumulate
+          // off, `r` for the other K steps.  Per segment: TMEM column (d), N
+          // of the instruction descriptor (i), B descriptor offset in 16-byte
+          // units (b).
+          auto slot_of = [&](int g) { return kRing - 1 - (g % kRing); };
+          auto seg_d = [&](int j0) { return dq + (uint32_t)(slot_of(gtop - j0) * npad); };
+          auto seg_b = [&](int j0) { return (uint64_t)(((uint32_t)(j0 * npad / 8) * sbo_b) >> 4); };
+          const int nall = jhi - jlo + 1;
+          // r: [jlo, jlo + rl0) and [jlo + rl0, jhi] (the second if the ring wraps)
+          const int rl0 = nall < kRing - slot_of(gtop - jlo) ? nall : kRing - slot_of(gtop - jlo);
+          const int nr = rl0 < nall ? 2 : 1;
+          const uint32_t rd0 = seg_d(jlo), rd1 = seg_d(jlo + rl0);
+          const uint32_t ri0 = make_idesc(kM, rl0 * npad), ri1 = make_idesc(kM, (nall - rl0) * npad);
+          const uint64_t rb0 = seg_b(jlo), rb1 = seg_b(jlo + rl0);
+          // f: as r, unless jlo = 0: block 0 alone (accumulate off), then
+          // [1, 1 + fl1) and [1 + fl1, jhi]
+          const bool fresh = jlo == 0;
+          const int rest = jhi;  // blocks 1 .. jhi after block 0
+          const int fl1 = rest < kRing - slot_of(gtop - 1) ? rest : kRing - slot_of(gtop - 1);
+          const int nf = fresh ? 1 + (rest > 0 ? 1 : 0) + (fl1 < rest ? 1 : 0) : nr;
+          const uint32_t fd0 = fresh ? seg_d(0) : rd0, fd1 = fresh ? seg_d(1) : rd1, fd2 = seg_d(1 + fl1);
+          const uint32_t fi0 = fresh ? make_idesc(kM, npad) : ri0, fi1 = fresh ? make_idesc(kM, fl1 * npad) : ri1;
+          const uint32_t fi2 = make_idesc(kM, (rest - fl1) * npad);
+          const uint64_t fb0 = fresh ? seg_b(0) : rb0, fb1 = fresh ? seg_b(1) : rb1, fb2 = seg_b(1 + fl1);
+          const uint32_t fa0 = fresh ? 0u : 1u;
 #pragma unroll
           for (int j = 0; j < 9; j++) {
             const int off = (j / 3) * kHX + j % 3;
@@ -302,25 +340,21 @@ __global__ void __launch_bounds__(256, 1) conv3d_tc_kernel(ConvArgs a) {
               const uint32_t b_k = (G == 4) ? (uint32_t)((j * 4 + 2 * h) * 128) : (uint32_t)(j * 128);
               const uint32_t lbo_b = (G == 4) ? 128u : (uint32_t)((9 - j) * 128);
               const uint64_t adesc = a0 + (uint64_t)(off + (G == 4 ? h * (2 * R::PLANE / 16) : 0));
-              const bool first = (j == 0 && h == 0);
-              int j0 = jlo, nb = jhi - jlo + 1;
-              while (nb > 0) {
-                // block j0 alone when it starts its output plane (accumulate off)
-                const uint32_t acc = (first && j0 == 0) ? 0u : 1u;
-                const int g = gtop - j0;
-                const int slot = kRing - 1 - (g % kRing);
-                int len = nb < kRing - slot ? nb : kRing - slot;
-                if (acc == 0u) len = 1;
-                const uint64_t bdesc = make_desc(b_addr + b_k + (uint32_t)(j0 * npad / 8) * sbo_b, lbo_b, sbo_b);
-                const uint32_t idesc = make_idesc(kM, len * npad);
-                const uint32_t d = dq + (uint32_t)(slot * npad);
+              const uint64_t bd = make_desc(b_addr + b_k, lbo_b, sbo_b);
+              if (j == 0 && h == 0) {
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(fd0),
+                    "l"(adesc), "l"(bd + fb0), "r"(fi0), "r"(fa0)
                     : "memory");
-                j0 += len;
-                nb -= len;
+                if (nf > 1)
+                  mma_acc(fd1, adesc, bd + fb1, fi1);
+                if (nf > 2)
+                  mma_acc(fd2, adesc, bd + fb2, fi2);
+              } else {
+                mma_acc(rd0, adesc, bd + rb0, ri0);
+                if (nr > 1)
+                  mma_acc(rd1, adesc, bd + rb1, ri1);
               }
             }
           }
