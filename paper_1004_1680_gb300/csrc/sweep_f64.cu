@@ -143,8 +143,6 @@ struct Geo {
   double ih[3];
 };
 
-__device__ __forceinline__ int cidx(const Geo& g, int i, int j, int k) { return i * g.s[0] + j * g.s[1] + k * g.s[2]; }
-
 // one thread per pencil along D (A, O: the other axes)
 template <int D>
 __global__ void __launch_bounds__(128) fluid64_kernel(Fluid64Args a) {
