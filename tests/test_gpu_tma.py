@@ -80,6 +80,8 @@ def test_single_staged_sweep_matches_the_register_sweep(mhd, axis, kind):
     ((64, 64, 16), {"xpath": 2}),                        # x sweeps through the exchanged layout
     ((32, 32, 24), {"floor": 1e-3}),                     # the pressure-floor variant
     ((96, 32, 28), {"segs": (0, 8, 0), "xpath": 2}),     # 3 block columns, ragged z chunking
+    ((32, 16, 16), {}),                                  # the shortest staged pencils (16), rows of 16
+    ((32, 8, 16), {"segs": (0, 0, 4)}),                  # rows of 8 (z sweeps staged, y pencils too short)
 ])
 def test_staged_steps_match_the_register_steps(mhd, dims, cfg):
     st = ic.turbulence(dims, seed=37, dtype=torch.float64, kmin=1.0, kmax=3.0, mach=0.8)
