@@ -78,7 +78,9 @@ int mhd_get_state(const mhd_t *m, float *const f[8], int on_device);
  *   dt_full = 2 * cfl / max_cells max_d (|v_d| + c_f*) / h_d,
  *   c_f* = sqrt((gamma p + |b_c|^2) / rho).
  * Each of the 6 sweeps of a step uses dt_full/2.  Returns MHD_E_STATE if any
- * cell has NaN, rho <= 0 or p <= 0.  Synchronises the stream. */
+ * cell has NaN, rho <= 0 or p <= 0, and MHD_E_TIMEOUT if a TMA-staged sweep
+ * since the last mhd_set_state gave up waiting for a chunk (see
+ * mhd_set_tma).  Synchronises the stream. */
 int mhd_cfl_dt(mhd_t *m, double cfl, double *dt_full);
 
 /* One full timestep of length dt_full (Section II.B): fluid_x, mag_x,
