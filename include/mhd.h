@@ -186,25 +186,28 @@ int mhd_copy_planes(mhd_t *m, int z0, int nplanes, float *const f[8], int into_b
  * MHD_E_ARG unless on is 0 or 1. */
 int mhd_set_fusion(mhd_t *m, int on);
 
-/* Staging of the fluid sweeps along the y and z kernel axes (not a change of
- * the method): with on = 1 (the default) a sweep of the paper's scheme whose
- * lane extent (the contiguous axis) is a multiple of 32 and whose row extent
- * is a multiple of 4 reads its input through the Tensor Memory Accelerator:
- * one thread per block copies the next 4 positions of the block's 32 x 4
- * pencils into shared memory while the block computes the current ones.
- * The values and their arithmetic are those of the register-load sweep,
- * except that the staged fluid sweep takes the freezing speeds' square
- * roots from the hardware approximation (a few ulp; the faster choice on
- * each path), so the two paths agree to FP32 rounding, not bitwise (the
- * magnetic sweeps bitwise); on = 0 always uses register loads.  Ensembles, ablations and boxes that do not qualify use register
- * loads.  If a staged chunk does not arrive within the bounded wait (about
- * half a second), the block records the failure and stops; mhd_cfl_dt then
- * returns MHD_E_TIMEOUT until the next mhd_set_state.  MHD_E_ARG unless on
- * is 0 or 1, or for an FP64 box. */
+/* Staging of the sweeps along the y and z kernel axes (not a change of the
+ * method): with on = 1 (the default) a fluid sweep whose lane extent (the
+ * contiguous axis) is a multiple of 32 and whose row extent is a multiple of
+ * 4, and a magnetic sweep whose row extent is a multiple of 8, read their
+ * input through the Tensor Memory Accelerator: one thread per block copies
+ * the next chunk of positions of the block's pencils (and of the
+ * neighbouring pencils it needs) into shared memory while the block
+ * computes the current one.  Every scheme variant of mhd_set_scheme is
+ * staged.  The values and their arithmetic are those of the register-load
+ * sweep, except that the staged fluid sweep takes the freezing speeds'
+ * square roots from the hardware approximation (a few ulp; the faster
+ * choice on each path), so the two paths agree to FP32 rounding, not
+ * bitwise (the magnetic sweeps bitwise); on = 0 always uses register loads.
+ * Ensembles, pencils shorter than 16 cells and boxes that do not qualify use
+ * register loads.  If a staged chunk does not arrive within the bounded
+ * wait (about half a second), the block records the failure and stops;
+ * mhd_cfl_dt then returns MHD_E_TIMEOUT until the next mhd_set_state.
+ * MHD_E_ARG unless on is 0 or 1, or for an FP64 box. */
 int mhd_set_tma(mhd_t *m, int on);
 
-/* Number of fluid sweeps this box has launched TMA-staged so far.  MHD_E_ARG
- * for NULL. */
+/* Number of sweeps (fluid and magnetic) this box has launched TMA-staged so
+ * far.  MHD_E_ARG for NULL. */
 int mhd_tma_sweeps(const mhd_t *m, long long *count);
 
 /* Optional floor on the gas pressure (not in the paper; 0 = off, the

@@ -77,8 +77,9 @@ struct FluidMaps {
   CUtensorMap row[kFluidMaps];
 };
 // Encode the maps of a sweep along kernel axis 1 or 2; false if the box does
-// not qualify (lane extent not a multiple of 32, row extent not a multiple of
-// 4, unaligned fields) or the driver's encoder is unavailable.
+// not qualify (rows not a multiple of 16 bytes, unaligned fields, pencils
+// shorter than 16 cells) or the driver's encoder is unavailable.  Lane and
+// row extents need not fill the 32 x 4 tiles.
 bool make_fluid_maps(int axis, const FluidArgs& a, FluidMaps* m);
 
 struct MagArgs {

@@ -29,7 +29,7 @@ bool make_fluid_maps(int axis, const FluidArgs& a, FluidMaps* out) {
   if (axis != 1 && axis != 2) return false;
   const Box& b = a.box;
   const int A = 0, O = (axis == 2) ? 1 : 2, D = axis, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  if (b.stride[A] != 1 || b.n[A] % 32 || b.n[O] % kFluidWarps || b.n[D] < 16) return false;
+  if (b.stride[A] != 1 || b.n[D] < 16) return false;
   if ((b.stride[O] * 4) % 16 || (b.stride[D] * 4) % 16) return false;
   for (int q = 0; q < 8; q++)
     if (reinterpret_cast<uintptr_t>(a.in[q]) % 16) return false;

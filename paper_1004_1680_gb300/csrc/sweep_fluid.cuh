@@ -186,17 +186,23 @@ __device__ __forceinline__ void fluid_sweep_body(const FluidArgs& a, const Fluid
   const int nchunk = (G.seg + 7 + CH - 1) / CH;
 
   // staged chunks: this thread's element of a field, and the element of its
-  // neighbour pencil along A (lane 31: the b_A edge columns) and along O
-  // (row 3: the b_O edge row); per-position strides of those two
+  // neighbour pencil along A and along O: the next lane / row of the block,
+  // or the edge columns / edge row copied from the next block along A / O
+  // (from lane / row 0 of the box where the next pencil wraps around; in a
+  // tile cut by the box's end the lanes and rows past it read zeros and
+  // store nothing); per-position strides of those two
   const int w = threadIdx.y;
   const int t0 = w * 32 + lane;
-  const int nbA = lane < 31 ? 5 * kTmaField + t0 + 1 : kTmaOffAe + w * 4;
-  const int nbA_step = lane < 31 ? kFluidWarps * 32 : kTmaAeSlot;
-  const int nbO = w < kFluidWarps - 1 ? 6 * kTmaField + t0 + 32 : kTmaOffOe + lane;
-  const int nbO_step = w < kFluidWarps - 1 ? kFluidWarps * 32 : 32;
-  const int tid = w * 32 + lane;
   const int x0 = G.bx * 32, y0 = G.by * kFluidWarps;
-  const int xe = wrapi(x0 + 32, nA), ye = wrapi(y0 + kFluidWarps, nO);  // neighbour blocks' first lane / row
+  const bool edgeA = lane == 31 || x0 + lane + 1 >= nA, edgeO = w == kFluidWarps - 1 || y0 + w + 1 >= nO;
+  const int nbA = edgeA ? kTmaOffAe + w * 4 : 5 * kTmaField + t0 + 1;
+  const int nbA_step = edgeA ? kTmaAeSlot : kFluidWarps * 32;
+  const int nbO = edgeO ? kTmaOffOe + lane : 6 * kTmaField + t0 + 32;
+  const int nbO_step = edgeO ? 32 : kFluidWarps * 32;
+  const int tid = w * 32 + lane;
+  // the next block's first lane / row, or lane / row 0 across the box's end
+  const int xe = x0 + 32 >= nA ? 0 : x0 + 32, ye = y0 + kFluidWarps >= nO ? 0 : y0 + kFluidWarps;
+  const bool full_tile = x0 + 32 <= nA && y0 + kFluidWarps <= nO;
   if constexpr (TMA) {
     if (tid == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[0])) : "memory");
@@ -350,7 +356,7 @@ __device__ __forceinline__ void fluid_sweep_body(const FluidArgs& a, const Fluid
       }
   
     };
-    if (TMA && p0 >= s0 + 3 && p0 < s1)
+    if (TMA && full_tile && p0 >= s0 + 3 && p0 < s1)
       positions(true);
     else
       positions(false);
@@ -382,11 +388,11 @@ fluid_sweep_kernel(FluidArgs a) {
   fluid_sweep_body<D, RATE, SMALL, FLOOR, LIM, FRZ, false>(a, nullptr);
 }
 
-// The TMA-staged sweep (kernel axes 1 and 2, the paper's scheme).
-template <int D, bool RATE, bool FLOOR>
+// The TMA-staged sweep (kernel axes 1 and 2, scheme (LIM, FRZ)).
+template <int D, bool RATE, bool FLOOR, int LIM, int FRZ>
 __global__ void __launch_bounds__(32 * kFluidWarps, 4)
 fluid_sweep_tma_kernel(const __grid_constant__ FluidArgs a, const __grid_constant__ FluidMaps mp) {
-  fluid_sweep_body<D, RATE, false, FLOOR, 0, 0, true>(a, &mp);
+  fluid_sweep_body<D, RATE, false, FLOOR, LIM, FRZ, true>(a, &mp);
 }
 
 // Launch of one fluid sweep with scheme (LIM, FRZ): kernel axis, fused CFL
@@ -407,12 +413,13 @@ cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
   const bool small = a.box.n[axis] < 16;
   const bool floor = a.p_floor > 0.f;
-  if constexpr (LIM == 0 && FRZ == 0) {  // the paper's scheme: TMA-staged y and z kernel-axis sweeps
+  {  // TMA-staged y and z kernel-axis sweeps
     FluidMaps mp;
     if (a.tma && !a.ens.items && axis != 0 && !small && make_fluid_maps(axis, a, &mp)) {
       if (a.tma_used) *a.tma_used = 1;
 #define FLUID_TMA_CASE(DD, RR, FF) \
-  if (axis == DD && rate == RR && floor == FF) fluid_sweep_tma_kernel<DD, RR, FF><<<tiles, block, 0, s>>>(a, mp);
+  if (axis == DD && rate == RR && floor == FF)                                                       \
+    fluid_sweep_tma_kernel<DD, RR, FF, LIM, FRZ><<<tiles, block, 0, s>>>(a, mp);
       FLUID_TMA_CASE(1, false, false) FLUID_TMA_CASE(1, true, false) FLUID_TMA_CASE(2, false, false)
       FLUID_TMA_CASE(2, true, false) FLUID_TMA_CASE(1, false, true) FLUID_TMA_CASE(1, true, true)
       FLUID_TMA_CASE(2, false, true) FLUID_TMA_CASE(2, true, true)

@@ -666,9 +666,9 @@ mag_sweep_pipe_kernel(MagArgs a) {
   else mag_pipe_role<D, SMALL, LIM, NP, kRoleHaloCol>(a, G, sh);
 }
 
-// The TMA-staged sweep along y and z (the paper's scheme, long pencils, tiles
-// that divide the box): kMagTmaSmem bytes of dynamic shared memory.
-template <int D, int NP>
+// The TMA-staged sweep along y and z (limiter LIM, long pencils, tiles that
+// divide the box): kMagTmaSmem bytes of dynamic shared memory.
+template <int D, int NP, int LIM>
 __global__ void __launch_bounds__(32 * (kMagWarps + 2), 2)
 mag_sweep_tma_kernel(const __grid_constant__ MagArgs a, const __grid_constant__ MagMaps mp) {
   __shared__ MagShared<NP> sh;
@@ -683,9 +683,9 @@ mag_sweep_tma_kernel(const __grid_constant__ MagArgs a, const __grid_constant__ 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.y < kMagWarps) mag_pipe_role<D, false, 0, NP, kRoleInterior, true>(a, G, sh, &mp, tb, tfull);
-  else if (threadIdx.y == kMagWarps) mag_pipe_role<D, false, 0, NP, kRoleHaloRow, true>(a, G, sh, &mp, tb, tfull);
-  else mag_pipe_role<D, false, 0, NP, kRoleHaloCol, true>(a, G, sh, &mp, tb, tfull);
+  if (threadIdx.y < kMagWarps) mag_pipe_role<D, false, LIM, NP, kRoleInterior, true>(a, G, sh, &mp, tb, tfull);
+  else if (threadIdx.y == kMagWarps) mag_pipe_role<D, false, LIM, NP, kRoleHaloRow, true>(a, G, sh, &mp, tb, tfull);
+  else mag_pipe_role<D, false, LIM, NP, kRoleHaloCol, true>(a, G, sh, &mp, tb, tfull);
 }
 
 // The x sweep stages rows in more than 48 KB of shared memory; the limit is
@@ -697,15 +697,15 @@ cudaError_t prepare_mag_t() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mag_sweep_kernel<0, false, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kMagXSmem);
-  if constexpr (LIM == 0) {  // the staged sweeps of the paper's scheme
+  {  // the staged sweeps
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<1, 1, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kMagTmaSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 1, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kMagTmaSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(mag_sweep_tma_kernel<2, 2, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kMagTmaSmem);
   }
   return e;
@@ -726,13 +726,13 @@ cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
   MAG_CASE(0, kMagXSmem)
 #undef MAG_CASE
   if (a.passes == 2 && axis == 0) return cudaErrorInvalidValue;  // the staged x kernel runs one pass
-  if constexpr (LIM == 0) {
+  {
     MagMaps mp;
     if (a.tma && !a.ens.items && !small && axis != 0 && make_mag_maps(axis, a, &mp)) {
       if (a.tma_used) *a.tma_used = 1;
-      if (axis == 1) mag_sweep_tma_kernel<1, 1><<<grid, block, kMagTmaSmem, s>>>(a, mp);
-      else if (a.passes == 2) mag_sweep_tma_kernel<2, 2><<<grid, block, kMagTmaSmem, s>>>(a, mp);
-      else mag_sweep_tma_kernel<2, 1><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      if (axis == 1) mag_sweep_tma_kernel<1, 1, LIM><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      else if (a.passes == 2) mag_sweep_tma_kernel<2, 2, LIM><<<grid, block, kMagTmaSmem, s>>>(a, mp);
+      else mag_sweep_tma_kernel<2, 1, LIM><<<grid, block, kMagTmaSmem, s>>>(a, mp);
       return cudaGetLastError();
     }
   }

@@ -301,7 +301,7 @@ class Box:
         _check(self.lib.mhd_set_tma(self.h, int(bool(on))))
 
     def tma_sweeps(self) -> int:
-        """Fluid sweeps this box has launched TMA-staged so far."""
+        """Sweeps (fluid and magnetic) this box has launched TMA-staged so far."""
         n = ctypes.c_longlong(0)
         _check(self.lib.mhd_tma_sweeps(self.h, ctypes.byref(n)))
         return int(n.value)

@@ -11,9 +11,10 @@ fluid and magnetic sweeps, full steps with the fused CFL rate and the fused
 pair of z magnetic sweeps, the optional pressure floor, segmented pencils
 (interior segments never cross the periodic wrap, the end segments do) and
 the x sweeps through the exchanged layout (kernel axis 1 with the lanes
-along y).  Boxes qualify when the contiguous axis is a multiple of 32 and
-the row axis a multiple of 4 (fluid) or 8 (magnetic); `tma_sweeps` shows
-that the staged kernels ran.
+along y).  A fluid sweep qualifies when its rows are a multiple of 16 bytes
+(tiles cut by the box's end included); a magnetic sweep when the contiguous
+axis is a multiple of 32 and the row axis a multiple of 8; `tma_sweeps`
+shows that the staged kernels ran.
 """
 import numpy as np
 import pytest
@@ -82,6 +83,8 @@ def test_single_staged_sweep_matches_the_register_sweep(mhd, axis, kind):
     ((96, 32, 28), {"segs": (0, 8, 0), "xpath": 2}),     # 3 block columns, ragged z chunking
     ((32, 16, 16), {}),                                  # the shortest staged pencils (16), rows of 16
     ((32, 8, 16), {"segs": (0, 0, 4)}),                  # rows of 8 (z sweeps staged, y pencils too short)
+    ((44, 36, 22), {}),                                  # fluid tiles cut by the box's end (lanes 12, rows 2)
+    ((52, 24, 30), {"xpath": 2, "segs": (0, 8, 0)}),     # ragged lanes along y on the exchanged layout too
 ])
 def test_staged_steps_match_the_register_steps(mhd, dims, cfg):
     st = ic.turbulence(dims, seed=37, dtype=torch.float64, kmin=1.0, kmax=3.0, mach=0.8)
