@@ -656,7 +656,7 @@ def run_ours(args, rank, world, local):
                           "scheme": {"limiter": args.limiter, "freezing": args.freezing},
                           "xpath": args.xpath or "auto",
                           "fusion": bool(args.fusion),
-                          "tma_staged_fluid_sweeps_per_step": tma_per_step,
+                          "tma_staged_sweeps_per_step": tma_per_step,
                           **({"boundaries": bcs, "interior_cells": int(np.prod([n - 8 if a in bcs else n for a in "xyz"]))}
                              if bcs else {}),
                           **({"mach": args.mach, "beta": args.beta} if (args.mach, args.beta) != (1.0, 1.0) else {}),
