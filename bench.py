@@ -180,7 +180,7 @@ def cpu_baseline(n: int, seed: int, cfl: float, budget_s: float = 15.0, min_step
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("sweep_fluid.cuh", "sweep_mag.cuh", "mhd_device.cuh", "tma.cuh"):
+    for name in ("sweep_fluid.cuh", "sweep_mag.cuh", "sweep_row.cuh", "mhd_device.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_1004_1680_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

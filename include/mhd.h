@@ -186,23 +186,27 @@ int mhd_copy_planes(mhd_t *m, int z0, int nplanes, float *const f[8], int into_b
  * MHD_E_ARG unless on is 0 or 1. */
 int mhd_set_fusion(mhd_t *m, int on);
 
-/* Staging of the sweeps along the y and z kernel axes (not a change of the
- * method): with on = 1 (the default) a fluid sweep whose lane extent (the
- * contiguous axis) is a multiple of 32 and whose row extent is a multiple of
- * 4, and a magnetic sweep whose row extent is a multiple of 8, read their
- * input through the Tensor Memory Accelerator: one thread per block copies
- * the next chunk of positions of the block's pencils (and of the
- * neighbouring pencils it needs) into shared memory while the block
- * computes the current one.  Every scheme variant of mhd_set_scheme is
- * staged.  The values and their arithmetic are those of the register-load
- * sweep, except that the staged fluid sweep takes the freezing speeds'
- * square roots from the hardware approximation (a few ulp; the faster
- * choice on each path), so the two paths agree to FP32 rounding, not
- * bitwise (the magnetic sweeps bitwise); on = 0 always uses register loads.
- * Ensembles, pencils shorter than 16 cells and boxes that do not qualify use
- * register loads.  If a staged chunk does not arrive within the bounded
- * wait (about half a second), the block records the failure and stops;
- * mhd_cfl_dt then returns MHD_E_TIMEOUT until the next mhd_set_state.
+/* Staging of the sweeps (not a change of the method): with on = 1 (the
+ * default) the sweeps read their input through the Tensor Memory
+ * Accelerator where the box qualifies.  Along the y and z kernel axes one
+ * thread per block copies the next chunk of positions of the block's pencils
+ * (and of the neighbouring pencils it needs) into shared memory while the
+ * block computes the current one: fluid sweeps whose rows are a multiple of
+ * 16 bytes, magnetic sweeps whose lane extent (the contiguous axis) is a
+ * multiple of 32 and row extent a multiple of 8.  Along x (x path 1, see
+ * mhd_set_xpath) whole x rows are copied into shared memory, each thread
+ * computing 4 consecutive cells: fluid sweeps with nx a multiple of 128 up
+ * to 2048, magnetic sweeps with nx a multiple of 128 up to 512 and ny a
+ * multiple of 4 (not with the per-pencil freezing speed).  Every other scheme
+ * variant of mhd_set_scheme is staged.  The values and their arithmetic are
+ * those of the register-load sweeps, except that the staged fluid sweeps
+ * take the freezing speeds' square roots from the hardware approximation (a
+ * few ulp; the faster choice on each path), so the two paths agree to FP32
+ * rounding, not bitwise (the magnetic sweeps bitwise); on = 0 always uses
+ * register loads.  Ensembles, pencils shorter than 16 cells and boxes that do
+ * not qualify use register loads.  If staged data does not arrive within the
+ * bounded wait (about half a second), the block records the failure and
+ * stops; mhd_cfl_dt then returns MHD_E_TIMEOUT until the next mhd_set_state.
  * MHD_E_ARG unless on is 0 or 1, or for an FP64 box. */
 int mhd_set_tma(mhd_t *m, int on);
 
@@ -268,16 +272,18 @@ int mhd_fill_ghosts(mhd_t *m);
  * segmentation, so results are bitwise independent of it. */
 int mhd_set_segments(mhd_t *m, int seg_x, int seg_y, int seg_z);
 
-/* How x sweeps read the state: 1 = directly (a warp stages 8-cell row pieces
- * of its 32 pencils in shared memory), 2 = through a copy with x and y
- * exchanged (all 8 fields transposed once before a group of x sweeps and once
- * after; consecutive steps share one group, so a run of steps costs two
- * transposes per step), 0 = automatic (2 once the state exceeds 64 MiB).
- * 3 = the paper's data flow, as an ablation: every sweep runs along the
- * contiguous axis of a copy transposed so that its axis is fastest (x<->y
- * around the y sweeps, x<->z around the z sweeps; six transposes per step);
- * needs every extent a multiple of 4.  All paths compute the same update;
- * results differ by FP32 rounding of sums taken in another order. */
+/* How x sweeps read the state: 1 = directly (over whole x rows staged in
+ * shared memory where the row sweeps of mhd_set_tma qualify; otherwise a
+ * warp stages 8-cell row pieces of its 32 pencils), 2 = through a copy with x
+ * and y exchanged (all 8 fields transposed once before a group of x sweeps
+ * and once after; consecutive steps share one group, so a run of steps costs
+ * two transposes per step), 0 = automatic: 1 where both row sweeps qualify,
+ * else 2 once the state exceeds 64 MiB, else 1.  3 = the paper's data flow,
+ * as an ablation: every sweep runs along the contiguous axis of a copy
+ * transposed so that its axis is fastest (x<->y around the y sweeps, x<->z
+ * around the z sweeps; six transposes per step); needs every extent a
+ * multiple of 4.  All paths compute the same update; results differ by FP32
+ * rounding of sums taken in another order. */
 int mhd_set_xpath(mhd_t *m, int mode);
 
 /* FP64 diagnostics of the current state, computed on the device in one pass

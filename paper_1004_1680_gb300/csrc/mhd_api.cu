@@ -71,7 +71,7 @@ struct mhd_s {
   int lim = 0;          // slope limiter (0 = van Leer, the paper's scheme)
   int fast = 0;         // freezing speed (0 = the bound, the paper's scheme)
   int fuse = 1;         // 1: the two z magnetic sweeps of a step run as one launch
-  int tma = 1;          // 1: y and z kernel-axis sweeps stage their chunks with TMA where they qualify
+  int tma = 1;          // 1: sweeps stage their data with bulk tensor copies where they qualify (y, z: chunks; x: rows)
   long long tma_sweeps = 0;  // sweeps launched TMA-staged
   int bc[3] = {0, 0, 0};  // per physical axis: 0 periodic, 1 outflow, 2 reflecting (ghost layers)
   double cpl[3] = {0.0, 0.0, 0.0};  // cells per unit length per physical axis (0: n, the unit box)
@@ -110,10 +110,18 @@ struct mhd_s {
 
 namespace {
 
-// x sweeps go through the exchanged layout once the state no longer fits in
-// L2 (direct x sweeps read 32 different lines per warp and position, which
-// only L2 can absorb).
-int auto_xpath(const mhd_s* m) { return m->N * 32LL > (64LL << 20) ? 2 : 1; }
+// x sweeps run directly along x when both row sweeps take the box (whole
+// x rows staged in shared memory: nx a multiple of 128 up to 512, ny a
+// multiple of 4, tensor-copy staging on, a freezing speed of its own per
+// cell); otherwise they go through the exchanged layout once the state no
+// longer fits in L2 (the pencil sweeps along x read 32 different lines per
+// warp and position, which only L2 can absorb).
+int auto_xpath(const mhd_s* m) {
+  const bool rows = m->tma && m->fast != 2 && m->n[0] % 128 == 0 && m->n[0] <= 512 && m->n[1] % 4 == 0 &&
+                    m->n[2] >= 2;
+  if (rows) return 1;
+  return m->N * 32LL > (64LL << 20) ? 2 : 1;
+}
 
 // Cells per unit length of each layout's axes (the exchanged layouts permute
 // the physical axes).
@@ -988,6 +996,7 @@ int mhd_set_scheme(mhd_t* m, int limiter, int freezing) {
   }
   m->lim = limiter;
   m->fast = freezing;
+  if (!m->xpath_req && !m->layout) m->xpath = auto_xpath(m);
   return MHD_OK;
 }
 
@@ -1049,6 +1058,7 @@ int mhd_set_tma(mhd_t* m, int on) {
   if (int rc = fp32_only(m)) return rc;
   if (on < 0 || on > 1) return fail(MHD_E_ARG, "tma must be 0 or 1");
   m->tma = on;
+  if (!m->xpath_req && !m->layout) m->xpath = auto_xpath(m);
   return MHD_OK;
 }
 

@@ -26,6 +26,7 @@
 #pragma once
 #include "mhd_device.cuh"
 #include "mhd_launch.h"
+#include "sweep_row.cuh"
 #include "tma.cuh"
 
 namespace mhd {
@@ -413,6 +414,10 @@ cudaError_t launch_fluid_t(int axis, bool rate, const FluidArgs& a, cudaStream_t
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);
   const bool small = a.box.n[axis] < 16;
   const bool floor = a.p_floor > 0.f;
+  if (axis == 0 && fluid_rows_qualify(a)) {  // x sweeps over whole staged rows
+    if (a.tma_used) *a.tma_used = 1;
+    return launch_fluid_rows<LIM, FRZ>(rate, a, s);
+  }
   {  // TMA-staged y and z kernel-axis sweeps
     FluidMaps mp;
     if (a.tma && !a.ens.items && axis != 0 && !small && make_fluid_maps(axis, a, &mp)) {

@@ -26,6 +26,7 @@
 #pragma once
 #include "mhd_device.cuh"
 #include "mhd_launch.h"
+#include "sweep_row.cuh"
 #include "tma.cuh"
 
 namespace mhd {
@@ -718,6 +719,10 @@ cudaError_t launch_mag_t(int axis, const MagArgs& a, cudaStream_t s) {
   dim3 grid((a.box.n[A] + 31) / 32, (a.box.n[O] + kMagWarps - 1) / kMagWarps, a.box.n[axis] / a.seg);
   if (a.ens.items) grid = dim3(a.nblocks, 1, 1);  // one block per work item
   const bool small = a.box.n[axis] < 16;
+  if (axis == 0 && mag_rows_qualify(a)) {  // x sweeps over whole staged rows
+    if (a.tma_used) *a.tma_used = 1;
+    return launch_mag_rows<LIM>(a, s);
+  }
 #define MAG_CASE(DD, SMEM)                                                       \
   if (axis == DD) {                                                              \
     if (small) mag_sweep_kernel<DD, true, LIM><<<grid, block, SMEM, s>>>(a);     \

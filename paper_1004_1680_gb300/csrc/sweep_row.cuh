@@ -1,0 +1,751 @@
+// Sweeps along the contiguous axis x over whole rows (Section II.B), FP32.
+//
+// A block holds whole x rows in shared memory: each row's fields arrive by
+// one-dimensional bulk copies (one per field row, contiguous 2 KB pieces at
+// 512 cells), and each thread owns 4 consecutive cells of the row.  The
+// stencil reaches neighbouring threads' cells only at the ends of a thread's
+// 4 cells; those values are exchanged through shared memory, with one block
+// barrier per exchange.  Every DRAM line is read whole and once, and no
+// transposed copy of the state is needed for the x sweeps.
+//
+// The arithmetic of a cell is that of the marching pipelines of
+// mhd_device.cuh (the same operations on the same operands, in the same
+// order), so a row sweep gives bitwise the result of the strided sweep of the
+// same pencil on the x <-> y exchanged copy.
+#pragma once
+#include <cmath>
+
+#include "mhd_device.cuh"
+#include "mhd_launch.h"
+#include "tma.cuh"
+
+namespace mhd {
+
+constexpr int kRowCells = 4;        // consecutive cells per thread
+constexpr int kRowMaxThreads = 128; // rows of up to 512 cells
+
+// One-dimensional bulk copy of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global memory into shared memory, completing on the
+// mbarrier at `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const float* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(__cvta_generic_to_global(src))), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ V5 v5_of(const float* s, int stride, int i) {
+  return {make_float2(s[i], s[stride + i]), make_float2(s[2 * stride + i], s[3 * stride + i]), s[4 * stride + i]};
+}
+__device__ __forceinline__ void v5_put(float* s, int stride, int i, const V5& v) {
+  s[i] = v.p0.x;
+  s[stride + i] = v.p0.y;
+  s[2 * stride + i] = v.p1.x;
+  s[3 * stride + i] = v.p1.y;
+  s[4 * stride + i] = v.e;
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour exchange along a row.  Thread l's left neighbour is l-1 and its
+// right neighbour l+1 (periodic over the row's T threads): within a warp by
+// shuffles; across warps through one shared-memory slot per warp, written by
+// lane 31 (values sent right) or lane 0 (values sent left) before a block
+// barrier and read after it.
+struct RowXch {
+  int lane, w, wl, wr;
+  float* sR;  // [slot][component][warp]: lane 31's values for the next warp's lane 0
+  float* sL;  // [slot][component][warp]: lane 0's values for the previous warp's lane 31
+  int nw;
+  __device__ __forceinline__ void send_right(int slot, const V5& v) const {
+    if (lane == 31) v5_put(sR + slot * 5 * nw, nw, w, v);
+  }
+  __device__ __forceinline__ void send_left(int slot, const V5& v) const {
+    if (lane == 0) v5_put(sL + slot * 5 * nw, nw, w, v);
+  }
+  // the left neighbour's v (call after the barrier that follows send_right)
+  __device__ __forceinline__ V5 from_left(int slot, const V5& v) const {
+    V5 x = {make_float2(__shfl_up_sync(~0u, v.p0.x, 1), __shfl_up_sync(~0u, v.p0.y, 1)),
+            make_float2(__shfl_up_sync(~0u, v.p1.x, 1), __shfl_up_sync(~0u, v.p1.y, 1)),
+            __shfl_up_sync(~0u, v.e, 1)};
+    if (lane == 0) x = v5_of(sR + slot * 5 * nw, nw, wl);
+    return x;
+  }
+  __device__ __forceinline__ V5 from_right(int slot, const V5& v) const {
+    V5 x = {make_float2(__shfl_down_sync(~0u, v.p0.x, 1), __shfl_down_sync(~0u, v.p0.y, 1)),
+            make_float2(__shfl_down_sync(~0u, v.p1.x, 1), __shfl_down_sync(~0u, v.p1.y, 1)),
+            __shfl_down_sync(~0u, v.e, 1)};
+    if (lane == 31) x = v5_of(sL + slot * 5 * nw, nw, wr);
+    return x;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Fluid sweep along x.  A row's copy set is 10 field rows of nx floats: rho,
+// m_x, m_y, m_z, e, b_x, b_y, b_y of the row +1 along y, b_z, b_z of the row
+// +1 along z (the face fields' high faces of the cell-centred field).  Three
+// buffers: the copies of the block's row after next go into the buffer of
+// the row before once every thread is done with it (at the first barrier of
+// this row), so the staged row stays readable for the whole of its
+// computation and the copies have about two rows' time to land.
+//
+// Per row, with thread l owning cells i = 4l .. 4l+3 (periodic along x):
+//   stage 1: FR, FL of U; flux1(i+1/2) = FR(i) - FL(i+1);
+//            Uh(i) = U(i) - tau/(2h) (flux1(i+1/2) - flux1(i-1/2))
+//            exchange: FR(4l+3) to the right, FL(4l) to the left
+//   stage 2: Rh, Lh of Uh; F2(i+1/2) = [Rh(i) + phi/2] - [Lh(i+1) - phi/2]
+//            exchange: Rh(4l+3) to the right, Rh(4l), Lh(4l), Lh(4l+1) to
+//            the left; then F2(4l+7/2) to the right
+//   Unew(i) = U(i) - tau/h (F2(i+1/2) - F2(i-1/2))
+constexpr int kFRowFields = 10;
+constexpr int kFRowBufs = 3;                     // rows in flight per block: copies two rows ahead
+constexpr int kFRowSlotsR = 3, kFRowSlotsL = 4;  // V5 slots per warp: FR, Rh, F2 / FL, Rh, Lh, Lh
+
+__host__ __device__ constexpr size_t fluid_row_smem(int nx) {
+  return (size_t)kFRowBufs * kFRowFields * nx * 4 +
+         (size_t)(kFRowSlotsR + kFRowSlotsL) * 5 * (nx / kRowCells / 32) * 4;
+}
+
+__device__ __forceinline__ void fluid_row_issue(const FluidArgs& a, uint32_t dst, uint32_t bar, int r, int nx,
+                                                int ny, int nz) {
+  const int y = r % ny, z = r / ny;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const long long o = y * sy + z * sz;
+  const long long oy = (y + 1 == ny ? 0 : y + 1) * sy + z * sz;
+  const long long oz = y * sy + (z + 1 == nz ? 0 : z + 1) * sz;
+  const uint32_t bytes = (uint32_t)nx * 4;
+  mbar_expect_tx(bar, kFRowFields * bytes);
+  bulk_load(dst + 0 * bytes, a.in[RHO] + o, bytes, bar);
+  bulk_load(dst + 1 * bytes, a.in[MX] + o, bytes, bar);
+  bulk_load(dst + 2 * bytes, a.in[MY] + o, bytes, bar);
+  bulk_load(dst + 3 * bytes, a.in[MZ] + o, bytes, bar);
+  bulk_load(dst + 4 * bytes, a.in[EN] + o, bytes, bar);
+  bulk_load(dst + 5 * bytes, a.in[BX] + o, bytes, bar);
+  bulk_load(dst + 6 * bytes, a.in[BY] + o, bytes, bar);
+  bulk_load(dst + 7 * bytes, a.in[BY] + oy, bytes, bar);
+  bulk_load(dst + 8 * bytes, a.in[BZ] + o, bytes, bar);
+  bulk_load(dst + 9 * bytes, a.in[BZ] + oz, bytes, bar);
+}
+
+// U of the thread's 4 cells from the staged row
+__device__ __forceinline__ void row_state(const float* sb, int nx, int x0, V5 (&U)[kRowCells]) {
+  float4 f[5];
+#pragma unroll
+  for (int q = 0; q < 5; q++) f[q] = *reinterpret_cast<const float4*>(sb + q * nx + x0);
+#pragma unroll
+  for (int j = 0; j < kRowCells; j++)
+    U[j] = {make_float2((&f[0].x)[j], (&f[1].x)[j]), make_float2((&f[2].x)[j], (&f[3].x)[j]), (&f[4].x)[j]};
+}
+// The cell-centred field of the thread's 4 cells (xn: the first cell of the
+// next thread, whose low x face is the last cell's high face): mean of the
+// low and high face along each axis.
+struct B3 {
+  float v[3];
+};
+__device__ __forceinline__ void row_fields(const float* sb, int nx, int x0, int xn, B3 (&B)[kRowCells]) {
+  const float4 bx = *reinterpret_cast<const float4*>(sb + 5 * nx + x0);
+  const float4 by0 = *reinterpret_cast<const float4*>(sb + 6 * nx + x0);
+  const float4 by1 = *reinterpret_cast<const float4*>(sb + 7 * nx + x0);
+  const float4 bz0 = *reinterpret_cast<const float4*>(sb + 8 * nx + x0);
+  const float4 bz1 = *reinterpret_cast<const float4*>(sb + 9 * nx + x0);
+  const float bxa[kRowCells + 1] = {bx.x, bx.y, bx.z, bx.w, sb[5 * nx + xn]};
+#pragma unroll
+  for (int j = 0; j < kRowCells; j++)
+    B[j] = {{face_mean(bxa[j], bxa[j + 1]), face_mean((&by0.x)[j], (&by1.x)[j]), face_mean((&bz0.x)[j], (&bz1.x)[j])}};
+}
+
+// 3 blocks of 128 threads per SM: about 170 registers, no spills (at 4
+// blocks and 128 registers the kernel spills and measured 1.77 against 1.54
+// ms at 512^3 with two buffers).
+template <bool RATE, bool FLOOR, int LIM, int FRZ>
+__global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __grid_constant__ FluidArgs a) {
+  static_assert(FRZ != 2, "the per-pencil freezing speed keeps the pencil sweeps");
+  extern __shared__ __align__(128) float rs_dyn[];
+  __shared__ alignas(8) unsigned long long rbar[kFRowBufs];
+  const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
+  const int T = nx / kRowCells, l = threadIdx.x;
+  const int rows = ny * nz;
+  RowXch X;
+  X.lane = l & 31;
+  X.w = l >> 5;
+  X.nw = T >> 5;
+  X.wl = X.w == 0 ? X.nw - 1 : X.w - 1;
+  X.wr = X.w + 1 == X.nw ? 0 : X.w + 1;
+  X.sR = rs_dyn + kFRowBufs * kFRowFields * nx;
+  X.sL = X.sR + kFRowSlotsR * 5 * X.nw;
+
+  const float gamma = a.gamma;
+  const float tau = *a.tau;
+  const float c_full = tau * a.box.ih[0];
+  const float c_half = 0.5f * c_full;
+  const int x0 = kRowCells * l;
+  const int xn = l + 1 == T ? 0 : x0 + kRowCells;  // the next thread's first cell
+  float rmax = 0.f;
+
+  if (l == 0) {
+    for (int k = 0; k < kFRowBufs; k++) mbar_init(smem_u32(&rbar[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int issued = 0;  // rows issued so far (the same count in every thread)
+  for (int k = 0; k < kFRowBufs - 1 && blockIdx.x + k * gridDim.x < rows; k++, issued++)
+    if (l == 0)
+      fluid_row_issue(a, smem_u32(rs_dyn + k * kFRowFields * nx), smem_u32(&rbar[k]), blockIdx.x + k * gridDim.x,
+                      nx, ny, nz);
+
+  bool gave_up = false;
+  int it = 0, buf = 0, use = 0;  // iteration, its buffer, and the buffer's use count (mbarrier phase)
+  for (int r = blockIdx.x; r < rows; r += gridDim.x, it++) {
+    const float* sb = rs_dyn + buf * kFRowFields * nx;
+    if (!sweep_mbar_wait(smem_u32(&rbar[buf]), use & 1)) gave_up = true;
+    // stage 1: the interface fluxes inside the thread's cells right away;
+    // FR(4l+3) and FL(4l) wait for the neighbours' halves.  The state is read
+    // again (16-byte reads: no bank conflicts) wherever it is needed, while
+    // the cell-centred field stays in registers through stage 2.
+    V5 f1[kRowCells + 1];  // flux1 at 4l-1/2 .. 4l+7/2
+    V5 FR3, FL0;
+    B3 B[kRowCells];
+    row_fields(sb, nx, x0, xn, B);
+    {
+      V5 U[kRowCells];
+      row_state(sb, nx, x0, U);
+      V5 FRp;
+#pragma unroll
+      for (int j = 0; j < kRowCells; j++) {
+        V5 FR, FL;
+        split_flux<FRZ, true>(U[j], B[j].v[0], make_float2(B[j].v[1], B[j].v[2]), gamma, FR, FL);
+        if (j == 0) FL0 = FL;
+        else f1[j] = v5_sub(FRp, FL);
+        FRp = FR;
+      }
+      FR3 = FRp;
+    }
+    X.send_right(0, FR3);
+    X.send_left(0, FL0);
+    if (__syncthreads_or(gave_up)) {
+      gave_up = true;
+      break;
+    }
+    // every thread is done with the previous row: the row after next goes into its buffer
+    if (r + (kFRowBufs - 1) * gridDim.x < rows) {
+      const int nb = issued % kFRowBufs;
+      if (l == 0)
+        fluid_row_issue(a, smem_u32(rs_dyn + nb * kFRowFields * nx), smem_u32(&rbar[nb]),
+                        r + (kFRowBufs - 1) * gridDim.x, nx, ny, nz);
+      issued++;
+    }
+    f1[0] = v5_sub(X.from_left(0, FR3), FL0);                // FR(4l-1) - FL(4l)
+    f1[kRowCells] = v5_sub(FR3, X.from_right(0, FL0));       // FR(4l+3) - FL(4l+4)
+    V5 Rh[kRowCells], Lh[kRowCells];
+    {
+      V5 U[kRowCells];
+      row_state(sb, nx, x0, U);
+#pragma unroll
+      for (int j = 0; j < kRowCells; j++) {
+        const V5 Uh = v5_fma(-c_half, v5_sub(f1[j + 1], f1[j]), U[j]);
+        // stage 2
+        split_flux<FRZ, true>(Uh, B[j].v[0], make_float2(B[j].v[1], B[j].v[2]), gamma, Rh[j], Lh[j]);
+      }
+    }
+    X.send_right(1, Rh[kRowCells - 1]);
+    X.send_left(1, Rh[0]);
+    X.send_left(2, Lh[0]);
+    X.send_left(3, Lh[1]);
+    __syncthreads();
+    V5 F2[kRowCells];
+    {
+      const V5 Rm = X.from_left(1, Rh[kRowCells - 1]);                             // Rh(4l-1)
+      const V5 Rp = X.from_right(1, Rh[0]), Lp0 = X.from_right(2, Lh[0]), Lp1 = X.from_right(3, Lh[1]);
+#pragma unroll
+      for (int j = 0; j < kRowCells; j++) {
+        // interface i+1/2, i = 4l + j: Rh(i-1..i+1), Lh(i..i+2)
+        const V5 Ri = Rh[j];
+        const V5 Rl = j == 0 ? Rm : Rh[j - 1];
+        const V5 Rr = j + 1 < kRowCells ? Rh[j + 1] : Rp;
+        const V5 Li = Lh[j];
+        const V5 L1 = j + 1 < kRowCells ? Lh[j + 1] : Lp0;
+        const V5 L2 = j + 2 < kRowCells ? Lh[j + 2] : (j + 2 == kRowCells ? Lp0 : Lp1);
+        const V5 right = v5_add(Ri, half_limited5<LIM>(v5_sub(Ri, Rl), v5_sub(Rr, Ri)));
+        const V5 left = v5_sub(L1, half_limited5<LIM>(v5_sub(L1, Li), v5_sub(L2, L1)));
+        F2[j] = v5_sub(right, left);
+      }
+    }
+    X.send_right(2, F2[kRowCells - 1]);
+    __syncthreads();
+    // the finished cells
+    const int y = r % ny, z = r / ny;
+    const long long ro = (long long)y * nx + (long long)z * nx * ny + x0;
+    const bool rate_row = RATE && y >= a.rate_lo[1] && y < a.rate_hi[1] && z >= a.rate_lo[2] && z < a.rate_hi[2];
+    float o[kRowCells][5];
+    {
+      V5 fprev = X.from_left(2, F2[kRowCells - 1]);  // F2(4l-1/2)
+      V5 U[kRowCells];
+      row_state(sb, nx, x0, U);
+      if (FLOOR || RATE) row_fields(sb, nx, x0, xn, B);
+#pragma unroll
+      for (int j = 0; j < kRowCells; j++) {
+        const V5 v = v5_fma(-c_full, v5_sub(F2[j], fprev), U[j]);
+        fprev = F2[j];
+        o[j][0] = v.p0.x;
+        o[j][1] = v.p0.y;
+        o[j][2] = v.p1.x;
+        o[j][3] = v.p1.y;
+        o[j][4] = v.e;
+        if (FLOOR) o[j][4] = floored_energy(o[j], B[j].v, gamma, a.p_floor);
+        if (RATE && rate_row && x0 + j >= a.rate_lo[0] && x0 + j < a.rate_hi[0])
+          rmax = fmaxf(rmax, cell_rate(o[j][0], &o[j][1], o[j][4], B[j].v, gamma, a.box.ih));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; q++)
+      *reinterpret_cast<float4*>(a.out[q] + ro) = make_float4(o[0][q], o[1][q], o[2][q], o[3][q]);
+    if (++buf == kFRowBufs) {
+      buf = 0;
+      use++;
+    }
+  }
+  if (__syncthreads_or(gave_up)) {
+    // record the failure, then let the copies still in flight (the last
+    // kFRowBufs issued) land before the block's shared memory is released;
+    // row q went into buffer q % kFRowBufs as its use q / kFRowBufs
+    if (l == 0) {
+      atomicOr(a.err, 1u);
+      for (int q = max(0, issued - kFRowBufs); q < issued; q++)
+        sweep_mbar_wait(smem_u32(&rbar[q % kFRowBufs]), (q / kFRowBufs) & 1);
+    }
+    return;
+  }
+  if (RATE) {
+    for (int s = 16; s > 0; s >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, s));
+    if ((l & 31) == 0) atomicMax(a.rate, __float_as_uint(rmax));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Magnetic sweep along x.  A block owns a tile of kMRowR rows along y (rows
+// j0 .. j0+R-1) and marches it along z over a segment of planes k0 .. k0+L-1,
+// one thread group (threadIdx.y) per row plus a halo group for row j0+R.
+// For each row the edge fluxes of b_y and b_z along x (MagPipe's arithmetic,
+// cell by cell) are
+//   E_y(j, k): q = b_y(j, k), face velocity (v(j, k) + v(j-1, k))/2,
+//   E_z(j, k): q = b_z(j, k), face velocity (v(j, k) + v(j, k-1))/2,
+// and plane k is finished with
+//   b_y(j, k) -= tau/h_x (E_y(i+1/2) - E_y(i-1/2)), likewise b_z with E_z,
+//   b_x(face i-1/2) += tau/h_y (E_y(j+1, k) - E_y(j, k))
+//                    + tau/h_z (E_z(j, k+1) - E_z(j, k))   (at edge i-1/2).
+// Step s of the march stages plane p = k0-1+s, forms v(p), E_z(p) and
+// E_y(p-1) and finishes plane p-1: E_z(j, p-1) is carried from the step
+// before, E_y of row j+1 comes from the neighbouring group through shared
+// memory.  Each staged plane holds rho and m_x of rows j0-1 .. j0+R, b_x and
+// b_z of the tile's rows and b_y of rows j0 .. j0+R (ten bulk copies, the
+// tile's rows in one piece each); two buffers, the copies of plane p+2 going
+// into plane p's once every thread has read it (after the step's third
+// exchange barrier).
+constexpr int kMRowR = 4;
+constexpr int kMRowRho = 0, kMRowMx = kMRowR + 2, kMRowBx = 2 * (kMRowR + 2), kMRowBy = kMRowBx + kMRowR,
+              kMRowBz = kMRowBy + kMRowR + 1, kMRowSlots = kMRowBz + kMRowR;  // row slots per plane (25)
+constexpr int kMRowXch = 6;  // scalar exchange slots per direction, per group and warp
+
+__host__ __device__ constexpr size_t mag_row_smem(int nx) {
+  return ((size_t)2 * kMRowSlots + 2 * (kMRowR + 2) + (kMRowR + 1)) * nx * 4 +
+         (size_t)2 * kMRowXch * (kMRowR + 1) * (nx / kRowCells / 32) * 4;
+}
+
+__device__ __forceinline__ void mag_row_issue(const MagArgs& a, uint32_t dst, uint32_t bar, int j0, int p, int nx,
+                                              int ny, int nz) {
+  constexpr int R = kMRowR;
+  const int k = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+  const long long sz = (long long)nx * ny;
+  const long long o = (long long)j0 * nx + k * sz;                                // row j0
+  const long long om = (long long)(j0 == 0 ? ny - 1 : j0 - 1) * nx + k * sz;      // row j0-1
+  const long long op = (long long)(j0 + R == ny ? 0 : j0 + R) * nx + k * sz;      // row j0+R
+  const uint32_t row = (uint32_t)nx * 4;
+  mbar_expect_tx(bar, kMRowSlots * row);
+  bulk_load(dst + (kMRowRho + 0) * row, a.in[RHO] + om, row, bar);
+  bulk_load(dst + (kMRowRho + 1) * row, a.in[RHO] + o, R * row, bar);
+  bulk_load(dst + (kMRowRho + R + 1) * row, a.in[RHO] + op, row, bar);
+  bulk_load(dst + (kMRowMx + 0) * row, a.in[MX] + om, row, bar);
+  bulk_load(dst + (kMRowMx + 1) * row, a.in[MX] + o, R * row, bar);
+  bulk_load(dst + (kMRowMx + R + 1) * row, a.in[MX] + op, row, bar);
+  bulk_load(dst + kMRowBx * row, a.in[BX] + o, R * row, bar);
+  bulk_load(dst + kMRowBy * row, a.in[BY] + o, R * row, bar);
+  bulk_load(dst + (kMRowBy + R) * row, a.in[BY] + op, row, bar);
+  bulk_load(dst + kMRowBz * row, a.in[BZ] + o, R * row, bar);
+}
+
+// Barrier of thread group g (threadIdx.y) alone: named barrier g + 1 over
+// its n threads (a multiple of 32).
+__device__ __forceinline__ void group_sync(int g, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(n) : "memory");
+}
+
+// Scalar neighbour exchange of one thread group (as RowXch).
+struct RowXch1 {
+  int lane, w, wl, wr, nw;
+  float* sR;  // [slot][warp]
+  float* sL;
+  __device__ __forceinline__ void send_right(int slot, float v) const {
+    if (lane == 31) sR[slot * nw + w] = v;
+  }
+  __device__ __forceinline__ void send_left(int slot, float v) const {
+    if (lane == 0) sL[slot * nw + w] = v;
+  }
+  __device__ __forceinline__ float from_left(int slot, float v) const {
+    const float x = __shfl_up_sync(~0u, v, 1);
+    return lane == 0 ? sR[slot * nw + wl] : x;
+  }
+  __device__ __forceinline__ float from_right(int slot, float v) const {
+    const float x = __shfl_down_sync(~0u, v, 1);
+    return lane == 31 ? sL[slot * nw + wr] : x;
+  }
+};
+
+// One edge-flux row of the thread's 4 cells, in three parts separated by
+// the exchange barriers.  u[0..5]: face velocity at cells 4l-1 .. 4l+4.
+template <int LIM>
+struct RowAdvect {
+  float q[kRowCells];          // advected face field at 4l .. 4l+3
+  float ub[kRowCells + 1];     // edge velocity at 4l-1/2 .. 4l+7/2
+  float qh[kRowCells];         // half-step field
+  float f[kRowCells];          // edge flux at 4l+1/2 .. 4l+7/2
+  // part 1: edge velocities; send q(4l+3) right, q(4l) left
+  __device__ __forceinline__ void part1(const float (&u)[kRowCells + 2], const RowXch1& X, int slot) {
+#pragma unroll
+    for (int e = 0; e <= kRowCells; e++) ub[e] = __fmul_rn(0.5f, __fadd_rn(u[e], u[e + 1]));
+    X.send_right(slot, q[kRowCells - 1]);
+    X.send_left(slot, q[0]);
+  }
+  // part 2 (after a barrier): first-order fluxes and the half step; send
+  // qh(4l+3) right, qh(4l), qh(4l+1) left
+  __device__ __forceinline__ void part2(float c_half, const RowXch1& X, int slot) {
+    const float qL = X.from_left(slot, q[kRowCells - 1]), qR = X.from_right(slot, q[0]);
+    float g[kRowCells + 1];  // at 4l-1/2 .. 4l+7/2
+#pragma unroll
+    for (int e = 0; e <= kRowCells; e++) {
+      const float lo = e == 0 ? qL : q[e - 1], hi = e == kRowCells ? qR : q[e];
+      g[e] = __fmul_rn(ub[e], ub[e] >= 0.f ? lo : hi);
+    }
+#pragma unroll
+    for (int i = 0; i < kRowCells; i++) qh[i] = __fmaf_rn(-c_half, __fsub_rn(g[i + 1], g[i]), q[i]);
+    X.send_right(slot + 1, qh[kRowCells - 1]);
+    X.send_left(slot + 1, qh[0]);
+    X.send_left(slot + 2, qh[1]);
+  }
+  // part 3 (after a barrier): the limited edge fluxes f(4l+1/2 .. 4l+7/2)
+  __device__ __forceinline__ void part3(const RowXch1& X, int slot) {
+    float h[kRowCells + 3];  // qh at 4l-1 .. 4l+5
+    h[0] = X.from_left(slot + 1, qh[kRowCells - 1]);
+#pragma unroll
+    for (int i = 0; i < kRowCells; i++) h[i + 1] = qh[i];
+    h[kRowCells + 1] = X.from_right(slot + 1, qh[0]);
+    h[kRowCells + 2] = X.from_right(slot + 2, qh[1]);
+    float d[kRowCells + 2];  // d(i) = qh(i) - qh(i-1), i = 4l .. 4l+5
+#pragma unroll
+    for (int i = 0; i < kRowCells + 2; i++) d[i] = __fsub_rn(h[i + 1], h[i]);
+#pragma unroll
+    for (int e = 0; e < kRowCells; e++) {  // edge 4l+e+1/2
+      const float u = ub[e + 1];
+      const bool pos = u >= 0.f;
+      const float base = pos ? h[e + 1] : h[e + 2];
+      const float sa = pos ? d[e] : d[e + 1];
+      const float sb = pos ? d[e + 1] : d[e + 2];
+      float lim;
+      if constexpr (LIM == 0) {
+        lim = vanleer_half(sa, sb);
+      } else {
+        lim = half_limited<LIM>(sa, sb);
+      }
+      f[e] = __fmul_rn(u, pos ? __fadd_rn(base, lim) : __fsub_rn(base, lim));
+    }
+  }
+};
+
+template <int LIM>
+__global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __grid_constant__ MagArgs a, int L) {
+  constexpr int R = kMRowR;
+  extern __shared__ __align__(128) float ms_dyn[];
+  __shared__ alignas(8) unsigned long long mbarr[2];
+  const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
+  const int T = nx / kRowCells, l = threadIdx.x, g = threadIdx.y;
+  const bool halo = g == R;
+  const int tiles = ny / R;
+  const int j0 = (blockIdx.x % tiles) * R, k0 = (blockIdx.x / tiles) * L;
+  const int tid = g * T + l;
+  float* P = ms_dyn;                                   // [2][slots][nx]
+  float* vring = P + 2 * kMRowSlots * nx;              // [2][R+2][nx]: v of rows j0-1 .. j0+R
+  float* ey = vring + 2 * (R + 2) * nx;                // [R+1][nx]: E_y of rows j0 .. j0+R
+  RowXch1 X;
+  X.lane = l & 31;
+  X.w = l >> 5;
+  X.nw = T >> 5;
+  X.wl = X.w == 0 ? X.nw - 1 : X.w - 1;
+  X.wr = X.w + 1 == X.nw ? 0 : X.w + 1;
+  X.sR = ey + (R + 1) * nx + g * 2 * kMRowXch * X.nw;
+  X.sL = X.sR + kMRowXch * X.nw;
+
+  const float tau = *a.tau;
+  const float c_full = tau * a.box.ih[0];
+  const float c_half = 0.5f * c_full;
+  const float kA = tau * a.box.ih[1];  // tau / h_y
+  const float kO = tau * a.box.ih[2];  // tau / h_z
+  const int x0 = kRowCells * l;
+  const int xm = l == 0 ? nx - 1 : x0 - 1, xp = l + 1 == T ? 0 : x0 + kRowCells;
+  const int vs = halo ? R + 1 : g + 1;  // this group's row in the v slots
+  const int nsteps = L + 2;
+
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbarr[0]), 1);
+    mbar_init(smem_u32(&mbarr[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < 2; s++) mag_row_issue(a, smem_u32(P + s * kMRowSlots * nx), smem_u32(&mbarr[s]), j0, k0 - 1 + s, nx, ny, nz);
+  int issued = 2;
+
+  float cbx[kRowCells], cby[kRowCells], cbz[kRowCells];  // raw b at plane p-1
+  float ezp[kRowCells + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};  // E_z(p-1) at 4l-1/2 .. 4l+7/2
+  bool gave_up = false;
+  RowAdvect<LIM> Az, Ay;
+  for (int s = 0; s < nsteps; s++) {
+    const int p = k0 - 1 + s;
+    const float* sb = P + (s & 1) * kMRowSlots * nx;
+    if (!sweep_mbar_wait(smem_u32(&mbarr[s & 1]), (s >> 1) & 1)) gave_up = true;
+    float* vcur = vring + (s & 1) * (R + 2) * nx;
+    const float* vprev = vring + ((s + 1) & 1) * (R + 2) * nx;
+    auto ld4 = [&](int slot, float (&d)[kRowCells]) {
+      const float4 v = *reinterpret_cast<const float4*>(sb + slot * nx + x0);
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
+    };
+    // part A: v(p) of this group's rows (the halo group: rows j0-1 and j0+R)
+    {
+      auto vel = [&](int slot) {
+        const float4 r = *reinterpret_cast<const float4*>(sb + (kMRowRho + slot) * nx + x0);
+        const float4 m = *reinterpret_cast<const float4*>(sb + (kMRowMx + slot) * nx + x0);
+        *reinterpret_cast<float4*>(vcur + slot * nx + x0) =
+            make_float4(v_div(m.x, r.x), v_div(m.y, r.y), v_div(m.z, r.z), v_div(m.w, r.w));
+      };
+      if (halo) {
+        vel(0);
+        vel(R + 1);
+      } else {
+        vel(g + 1);
+      }
+    }
+    if (__syncthreads_or(gave_up)) {
+      gave_up = true;
+      break;
+    }
+    const bool doz = !halo && s >= 1, doy = s >= 2;
+    // face velocities at cells 4l-1 .. 4l+4 of two v rows: (own + other) / 2
+    auto face_u = [&](const float* va, const float* vb, float (&u)[kRowCells + 2]) {
+      const float4 a4 = *reinterpret_cast<const float4*>(va + x0), b4 = *reinterpret_cast<const float4*>(vb + x0);
+      u[0] = __fmul_rn(0.5f, __fadd_rn(va[xm], vb[xm]));
+      u[1] = __fmul_rn(0.5f, __fadd_rn(a4.x, b4.x));
+      u[2] = __fmul_rn(0.5f, __fadd_rn(a4.y, b4.y));
+      u[3] = __fmul_rn(0.5f, __fadd_rn(a4.z, b4.z));
+      u[4] = __fmul_rn(0.5f, __fadd_rn(a4.w, b4.w));
+      u[5] = __fmul_rn(0.5f, __fadd_rn(va[xp], vb[xp]));
+    };
+    if (doz) {  // E_z(p): b_z(p), v of this row at planes p and p-1
+      float u[kRowCells + 2];
+      face_u(vcur + vs * nx, vprev + vs * nx, u);
+      ld4(kMRowBz + g, Az.q);  // b_z(p)
+      Az.part1(u, X, 0);
+    }
+    if (doy) {  // E_y(p-1): b_y(p-1), v of rows j and j-1 at plane p-1
+      float u[kRowCells + 2];
+      face_u(vprev + vs * nx, vprev + (vs - 1) * nx, u);
+#pragma unroll
+      for (int i = 0; i < kRowCells; i++) Ay.q[i] = cby[i];
+      Ay.part1(u, X, 3);
+    }
+    // the exchanges along a row need only the row's own warps: a named
+    // barrier per group (the block-wide ones cost 1.5x the step at 256^3)
+    group_sync(g, T);
+    if (doz) Az.part2(c_half, X, 0);
+    if (doy) Ay.part2(c_half, X, 3);
+    group_sync(g, T);
+    if (doz) {
+      Az.part3(X, 0);
+      X.send_right(0, Az.f[kRowCells - 1]);
+    }
+    if (doy) {
+      Ay.part3(X, 3);
+      *reinterpret_cast<float4*>(ey + (vs - 1) * nx + x0) = make_float4(Ay.f[0], Ay.f[1], Ay.f[2], Ay.f[3]);
+    }
+    // the raw fields of plane p for the next step (read late: fewer live registers)
+    float nbx[kRowCells] = {0.f, 0.f, 0.f, 0.f}, nby[kRowCells], nbz[kRowCells] = {0.f, 0.f, 0.f, 0.f};
+    if (halo) {
+      ld4(kMRowBy + R, nby);
+    } else {
+      ld4(kMRowBx + g, nbx);
+      ld4(kMRowBy + g, nby);
+      ld4(kMRowBz + g, nbz);
+    }
+    __syncthreads();
+    if (s + 2 < nsteps) {  // every thread has read plane p: plane p+2 goes into its buffer
+      if (tid == 0) mag_row_issue(a, smem_u32(P + (s & 1) * kMRowSlots * nx), smem_u32(&mbarr[s & 1]), j0, p + 2, nx, ny, nz);
+      issued++;
+    }
+    float ezc[kRowCells + 1];  // E_z(p) at 4l-1/2 .. 4l+7/2
+    if (doz) {
+      ezc[0] = X.from_left(0, Az.f[kRowCells - 1]);
+#pragma unroll
+      for (int e = 0; e < kRowCells; e++) ezc[e + 1] = Az.f[e];
+    }
+    if (doy && !halo) {  // finish plane p-1 of row j0+g
+      float eyo[kRowCells + 1], eyu[kRowCells];  // E_y of this row at 4l-1/2 .., of row j+1 at 4l-1/2 .. 4l+5/2
+      const float* er = ey + g * nx;
+      const float* eu = ey + (g + 1) * nx;
+      eyo[0] = er[xm];
+#pragma unroll
+      for (int e = 0; e < kRowCells; e++) eyo[e + 1] = Ay.f[e];
+      eyu[0] = eu[xm];
+      {
+        const float4 t = *reinterpret_cast<const float4*>(eu + x0);
+        eyu[1] = t.x;
+        eyu[2] = t.y;
+        eyu[3] = t.z;
+      }
+      float obx[kRowCells], oby[kRowCells], obz[kRowCells];
+#pragma unroll
+      for (int i = 0; i < kRowCells; i++) {
+        oby[i] = __fmaf_rn(-c_full, __fsub_rn(eyo[i + 1], eyo[i]), cby[i]);
+        obz[i] = __fmaf_rn(-c_full, __fsub_rn(ezp[i + 1], ezp[i]), cbz[i]);
+        // b_x on the low face of cell i: the edge fluxes at i-1/2, y first
+        float b = __fmaf_rn(kA, __fsub_rn(eyu[i], eyo[i]), cbx[i]);
+        obx[i] = __fmaf_rn(kO, __fsub_rn(ezc[i], ezp[i]), b);
+      }
+      const int kp = p - 1;  // inside [k0, k0 + L)
+      const long long ro = (long long)(j0 + g) * nx + (long long)kp * nx * ny + x0;
+      *reinterpret_cast<float4*>(a.out[0] + ro) = make_float4(obx[0], obx[1], obx[2], obx[3]);
+      *reinterpret_cast<float4*>(a.out[1] + ro) = make_float4(oby[0], oby[1], oby[2], oby[3]);
+      *reinterpret_cast<float4*>(a.out[2] + ro) = make_float4(obz[0], obz[1], obz[2], obz[3]);
+    }
+    // plane p becomes plane p-1 of the next step
+#pragma unroll
+    for (int i = 0; i < kRowCells; i++) {
+      cbx[i] = nbx[i];
+      cby[i] = nby[i];
+      cbz[i] = nbz[i];
+    }
+    if (doz)
+#pragma unroll
+      for (int e = 0; e <= kRowCells; e++) ezp[e] = ezc[e];
+  }
+  if (__syncthreads_or(gave_up)) {
+    if (tid == 0) {
+      atomicOr(a.err, 1u);
+      for (int q = max(0, issued - 2); q < issued; q++) sweep_mbar_wait(smem_u32(&mbarr[q & 1]), (q >> 1) & 1);
+    }
+  }
+}
+
+// Rows of the box qualify: x contiguous, nx a multiple of 128 (whole warps of
+// 4-cell threads) and at most 512, 16-byte aligned fields, a single box.
+inline bool fluid_rows_qualify(const FluidArgs& a) {
+  const Box& b = a.box;
+  if (a.ens.items || !a.tma || a.fast == 2) return false;
+  if (b.stride[0] != 1 || b.stride[1] != b.n[0] || b.stride[2] != (long long)b.n[0] * b.n[1]) return false;
+  if (b.n[0] % 128 || b.n[0] > kRowCells * kRowMaxThreads) return false;
+  for (int q = 0; q < 8; q++)
+    if (reinterpret_cast<uintptr_t>(a.in[q]) % 16 || reinterpret_cast<uintptr_t>(a.out[q]) % 16) return false;
+  return true;
+}
+
+// Persistent grid: as many blocks as fit on the device at once (at most one
+// per row).
+template <class K>
+inline cudaError_t row_grid(K kernel, int threads, size_t smem, long long rows, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  const long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  *grid = (int)(rows < cap ? rows : cap);
+  return cudaSuccess;
+}
+
+template <int LIM, int FRZ>
+cudaError_t launch_fluid_rows(bool rate, const FluidArgs& a, cudaStream_t s) {
+  if constexpr (FRZ == 2) {
+    return cudaErrorInvalidValue;
+  } else {
+    const int nx = a.box.n[0];
+    const int threads = nx / kRowCells;
+    const size_t smem = fluid_row_smem(nx);
+    const long long rows = (long long)a.box.n[1] * a.box.n[2];
+    const bool floor = a.p_floor > 0.f;
+    int grid = 0;
+    cudaError_t e;
+#define FLUID_ROW_CASE(RR, FF)                                                        \
+  if (rate == RR && floor == FF) {                                                    \
+    e = row_grid(fluid_row_kernel<RR, FF, LIM, FRZ>, threads, smem, rows, &grid);     \
+    if (e != cudaSuccess) return e;                                                   \
+    fluid_row_kernel<RR, FF, LIM, FRZ><<<grid, threads, smem, s>>>(a);                \
+  }
+    FLUID_ROW_CASE(false, false) FLUID_ROW_CASE(true, false) FLUID_ROW_CASE(false, true) FLUID_ROW_CASE(true, true)
+#undef FLUID_ROW_CASE
+    return cudaGetLastError();
+  }
+}
+
+}  // namespace mhd
+
+namespace mhd {
+
+// The magnetic row sweep qualifies for single boxes with x contiguous, nx a
+// multiple of 128 up to 512 (a block of 5 x nx/4 threads), ny a multiple of
+// the tile's rows and 16-byte aligned fields.
+inline bool mag_rows_qualify(const MagArgs& a) {
+  const Box& b = a.box;
+  if (a.ens.items || !a.tma || a.passes != 1) return false;
+  if (b.stride[0] != 1 || b.stride[1] != b.n[0] || b.stride[2] != (long long)b.n[0] * b.n[1]) return false;
+  if (b.n[0] % 128 || b.n[0] > 512 || b.n[1] % kMRowR || b.n[2] < 2) return false;
+  for (int q = 0; q < 8; q++)
+    if (reinterpret_cast<uintptr_t>(a.in[q]) % 16) return false;
+  for (int q = 0; q < 3; q++)
+    if (reinterpret_cast<uintptr_t>(a.out[q]) % 16) return false;
+  return true;
+}
+
+// Segment length along z: the divisor of nz (at least 8 planes where nz
+// allows) that minimises the warm-up planes per segment times the idle share
+// of the last wave (one block per SM).
+inline int mag_row_segment(int tiles, int nz, int sms) {
+  int best = nz;
+  double best_cost = 1e30;
+  for (int L = nz; L >= 1; L--) {
+    if (nz % L || (L < 8 && L != nz)) continue;
+    const double items = (double)tiles * (nz / L);
+    const double waves = items / sms;
+    const double cost = (double)(L + 2) / L * std::ceil(waves) / waves;
+    if (cost < best_cost * 0.999) {
+      best = L;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
+template <int LIM>
+cudaError_t launch_mag_rows(const MagArgs& a, cudaStream_t s) {
+  const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
+  const size_t smem = mag_row_smem(nx);
+  cudaError_t e = cudaFuncSetAttribute(mag_row_kernel<LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int tiles = ny / kMRowR;
+  const int L = mag_row_segment(tiles, nz, sms > 0 ? sms : 1);
+  mag_row_kernel<LIM><<<tiles * (nz / L), dim3(nx / kRowCells, kMRowR + 1), smem, s>>>(a, L);
+  return cudaGetLastError();
+}
+
+}  // namespace mhd
