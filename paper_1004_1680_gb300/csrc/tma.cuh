@@ -37,6 +37,13 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// One arrival on the barrier (release: this thread's earlier shared-memory
+// writes, and those of its warp after a __syncwarp, are seen by the threads
+// that observe the phase complete).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // Arm the barrier's current phase with the bytes the copies issued next will
 // bring (the issuing thread's arrival).
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
