@@ -4,14 +4,17 @@
 // one-dimensional bulk copies (one per field row, contiguous 2 KB pieces at
 // 512 cells), and each thread owns 4 consecutive cells of the row.  The
 // stencil reaches neighbouring threads' cells only at the ends of a thread's
-// 4 cells; those values are exchanged through shared memory, with one block
-// barrier per exchange.  Every DRAM line is read whole and once, and no
+// 4 cells; those values are exchanged through per-thread slots in shared
+// memory, around an mbarrier phase, a block barrier or a named barrier of
+// the row's own warps.  Every DRAM line is read whole and once, and no
 // transposed copy of the state is needed for the x sweeps.
 //
 // The arithmetic of a cell is that of the marching pipelines of
 // mhd_device.cuh (the same operations on the same operands, in the same
-// order), so a row sweep gives bitwise the result of the strided sweep of the
-// same pencil on the x <-> y exchanged copy.
+// order): the magnetic row sweep gives bitwise the result of the
+// register-load x sweep, and the fluid row sweep agrees with it to FP32
+// rounding (it takes the freezing speeds' square roots from the hardware
+// approximation, as the TMA-staged strided sweeps do).
 #pragma once
 #include <cmath>
 
@@ -46,47 +49,12 @@ __device__ __forceinline__ void v5_put(float* s, int stride, int i, const V5& v)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour exchange along a row.  Thread l's left neighbour is l-1 and its
-// right neighbour l+1 (periodic over the row's T threads): within a warp by
-// shuffles; across warps through one shared-memory slot per warp, written by
-// lane 31 (values sent right) or lane 0 (values sent left) before a block
-// barrier and read after it.
-struct RowXch {
-  int lane, w, wl, wr;
-  float* sR;  // [slot][component][warp]: lane 31's values for the next warp's lane 0
-  float* sL;  // [slot][component][warp]: lane 0's values for the previous warp's lane 31
-  int nw;
-  __device__ __forceinline__ void send_right(int slot, const V5& v) const {
-    if (lane == 31) v5_put(sR + slot * 5 * nw, nw, w, v);
-  }
-  __device__ __forceinline__ void send_left(int slot, const V5& v) const {
-    if (lane == 0) v5_put(sL + slot * 5 * nw, nw, w, v);
-  }
-  // the left neighbour's v (call after the barrier that follows send_right)
-  __device__ __forceinline__ V5 from_left(int slot, const V5& v) const {
-    V5 x = {make_float2(__shfl_up_sync(~0u, v.p0.x, 1), __shfl_up_sync(~0u, v.p0.y, 1)),
-            make_float2(__shfl_up_sync(~0u, v.p1.x, 1), __shfl_up_sync(~0u, v.p1.y, 1)),
-            __shfl_up_sync(~0u, v.e, 1)};
-    if (lane == 0) x = v5_of(sR + slot * 5 * nw, nw, wl);
-    return x;
-  }
-  __device__ __forceinline__ V5 from_right(int slot, const V5& v) const {
-    V5 x = {make_float2(__shfl_down_sync(~0u, v.p0.x, 1), __shfl_down_sync(~0u, v.p0.y, 1)),
-            make_float2(__shfl_down_sync(~0u, v.p1.x, 1), __shfl_down_sync(~0u, v.p1.y, 1)),
-            __shfl_down_sync(~0u, v.e, 1)};
-    if (lane == 31) x = v5_of(sL + slot * 5 * nw, nw, wr);
-    return x;
-  }
-};
-
-// ---------------------------------------------------------------------------
 // Fluid sweep along x.  A row's copy set is 10 field rows of nx floats: rho,
 // m_x, m_y, m_z, e, b_x, b_y, b_y of the row +1 along y, b_z, b_z of the row
-// +1 along z (the face fields' high faces of the cell-centred field).  Three
-// buffers: the copies of the block's row after next go into the buffer of
-// the row before once every thread is done with it (at the first barrier of
-// this row), so the staged row stays readable for the whole of its
-// computation and the copies have about two rows' time to land.
+// +1 along z (the face fields' high faces of the cell-centred field).  Two
+// buffers: the copies of the block's next row go into the buffer of the row
+// before once every warp is done with it (at the first exchange of this
+// row), so the staged row stays readable for the whole of its computation.
 //
 // Per row, with thread l owning cells i = 4l .. 4l+3 (periodic along x):
 //   stage 1: FR, FL of U; flux1(i+1/2) = FR(i) - FL(i+1);
@@ -97,13 +65,32 @@ struct RowXch {
 //            the left; then F2(4l+7/2) to the right
 //   Unew(i) = U(i) - tau/h (F2(i+1/2) - F2(i-1/2))
 constexpr int kFRowFields = 10;
-constexpr int kFRowBufs = 3;                     // rows in flight per block: copies two rows ahead
-constexpr int kFRowSlotsR = 3, kFRowSlotsL = 4;  // V5 slots per warp: FR, Rh, F2 / FL, Rh, Lh, Lh
+constexpr int kFRowBufs = 2;   // rows in flight per block (three measured the same, and leave no room for the slots)
+constexpr int kFRowSlots = 7;  // exchanged V5 values per thread: FR(4l+3), FL(4l); Rh(4l+3), Rh(4l), Lh(4l), Lh(4l+1); F2
 
 __host__ __device__ constexpr size_t fluid_row_smem(int nx) {
-  return (size_t)kFRowBufs * kFRowFields * nx * 4 +
-         (size_t)(kFRowSlotsR + kFRowSlotsL) * 5 * (nx / kRowCells / 32) * 4;
+  return (size_t)kFRowBufs * kFRowFields * nx * 4 + (size_t)kFRowSlots * (nx / kRowCells) * 20;
 }
+
+// The exchange slots of the fluid row sweep: every thread stores its value
+// of a slot as one 16-byte and one 4-byte word (conflict-free, two
+// instructions) and reads its neighbour's the same way.  Through lane
+// shuffles with the warps' end lanes going through shared memory the
+// exchange cost about 20 instructions per value: 9.0 against 7.6 warp
+// instructions per cell for the strided sweep.
+struct RowSlots {
+  float4* A;  // [slot][thread]: rho, m_d, m_t1, m_t2 components
+  float* E;   // [slot][thread]: e component
+  int T;
+  __device__ __forceinline__ void put(int slot, int i, const V5& v) const {
+    A[slot * T + i] = make_float4(v.p0.x, v.p0.y, v.p1.x, v.p1.y);
+    E[slot * T + i] = v.e;
+  }
+  __device__ __forceinline__ V5 get(int slot, int i) const {
+    const float4 a = A[slot * T + i];
+    return {make_float2(a.x, a.y), make_float2(a.z, a.w), E[slot * T + i]};
+  }
+};
 
 __device__ __forceinline__ void fluid_row_issue(const FluidArgs& a, uint32_t dst, uint32_t bar, int r, int nx,
                                                 int ny, int nz) {
@@ -165,14 +152,12 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
   const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
   const int T = nx / kRowCells, l = threadIdx.x;
   const int rows = ny * nz;
-  RowXch X;
-  X.lane = l & 31;
-  X.w = l >> 5;
-  X.nw = T >> 5;
-  X.wl = X.w == 0 ? X.nw - 1 : X.w - 1;
-  X.wr = X.w + 1 == X.nw ? 0 : X.w + 1;
-  X.sR = rs_dyn + kFRowBufs * kFRowFields * nx;
-  X.sL = X.sR + kFRowSlotsR * 5 * X.nw;
+  const int lane = l & 31, nw = T >> 5;
+  const int lm = l == 0 ? T - 1 : l - 1, lp = l + 1 == T ? 0 : l + 1;  // neighbour threads (periodic)
+  RowSlots X;
+  X.A = reinterpret_cast<float4*>(rs_dyn + kFRowBufs * kFRowFields * nx);
+  X.E = reinterpret_cast<float*>(X.A + kFRowSlots * T);
+  X.T = T;
 
   const float gamma = a.gamma;
   const float tau = *a.tau;
@@ -184,8 +169,8 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
 
   if (l == 0) {
     for (int k = 0; k < kFRowBufs; k++) mbar_init(smem_u32(&rbar[k]), 1);
-    mbar_init(smem_u32(&xbar[0]), X.nw);
-    mbar_init(smem_u32(&xbar[1]), X.nw);
+    mbar_init(smem_u32(&xbar[0]), nw);
+    mbar_init(smem_u32(&xbar[1]), nw);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -222,12 +207,12 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
       }
       FR3 = FRp;
     }
-    X.send_right(0, FR3);
-    X.send_left(0, FL0);
+    X.put(0, l, FR3);
+    X.put(1, l, FL0);
     // split-phase exchange: the interior cells 1 and 2 go on while the
     // neighbours' halves arrive
     __syncwarp();
-    if (X.lane == 0) mbar_arrive(smem_u32(&xbar[0]));
+    if (lane == 0) mbar_arrive(smem_u32(&xbar[0]));
     V5 Rh[kRowCells], Lh[kRowCells];
     V5 U[kRowCells];
     row_state(sb, nx, x0, U);
@@ -246,25 +231,25 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
                         r + (kFRowBufs - 1) * gridDim.x, nx, ny, nz);
       issued++;
     }
-    f1[0] = v5_sub(X.from_left(0, FR3), FL0);                // FR(4l-1) - FL(4l)
-    f1[kRowCells] = v5_sub(FR3, X.from_right(0, FL0));       // FR(4l+3) - FL(4l+4)
+    f1[0] = v5_sub(X.get(0, lm), FL0);          // FR(4l-1) - FL(4l)
+    f1[kRowCells] = v5_sub(FR3, X.get(1, lp));  // FR(4l+3) - FL(4l+4)
 #pragma unroll
     for (int j = 0; j < kRowCells; j += kRowCells - 1) {
       const V5 Uh = v5_fma(-c_half, v5_sub(f1[j + 1], f1[j]), U[j]);
       split_flux<FRZ, true>(Uh, B[j].v[0], make_float2(B[j].v[1], B[j].v[2]), gamma, Rh[j], Lh[j]);
     }
-    X.send_right(1, Rh[kRowCells - 1]);
-    X.send_left(1, Rh[0]);
-    X.send_left(2, Lh[0]);
-    X.send_left(3, Lh[1]);
+    X.put(2, l, Rh[kRowCells - 1]);
+    X.put(3, l, Rh[0]);
+    X.put(4, l, Lh[0]);
+    X.put(5, l, Lh[1]);
     if (__syncthreads_or(gave_up)) {
       gave_up = true;
       break;
     }
     V5 F2[kRowCells];
     {
-      const V5 Rm = X.from_left(1, Rh[kRowCells - 1]);                             // Rh(4l-1)
-      const V5 Rp = X.from_right(1, Rh[0]), Lp0 = X.from_right(2, Lh[0]), Lp1 = X.from_right(3, Lh[1]);
+      const V5 Rm = X.get(2, lm);                                         // Rh(4l-1)
+      const V5 Rp = X.get(3, lp), Lp0 = X.get(4, lp), Lp1 = X.get(5, lp);  // Rh(4l+4), Lh(4l+4), Lh(4l+5)
 #pragma unroll
       for (int j = 0; j < kRowCells; j++) {
         // interface i+1/2, i = 4l + j: Rh(i-1..i+1), Lh(i..i+2)
@@ -279,9 +264,9 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
         F2[j] = v5_sub(right, left);
       }
     }
-    X.send_right(2, F2[kRowCells - 1]);
+    X.put(6, l, F2[kRowCells - 1]);
     __syncwarp();
-    if (X.lane == 0) mbar_arrive(smem_u32(&xbar[1]));
+    if (lane == 0) mbar_arrive(smem_u32(&xbar[1]));
     // the finished cells: 1 .. 3 while F2(4l-1/2) arrives, then cell 0
     const int y = r % ny, z = r / ny;
     const long long ro = (long long)y * nx + (long long)z * nx * ny + x0;
@@ -303,7 +288,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
 #pragma unroll
     for (int j = 1; j < kRowCells; j++) finish(j, F2[j - 1]);
     if (!sweep_mbar_wait(smem_u32(&xbar[1]), it & 1)) gave_up = true;
-    finish(0, X.from_left(2, F2[kRowCells - 1]));  // F2(4l-1/2)
+    finish(0, X.get(6, lm));  // F2(4l-1/2)
 #pragma unroll
     for (int q = 0; q < 5; q++)
       *reinterpret_cast<float4*>(a.out[q] + ro) = make_float4(o[0][q], o[1][q], o[2][q], o[3][q]);
@@ -352,11 +337,11 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
 constexpr int kMRowR = 4;
 constexpr int kMRowRho = 0, kMRowMx = kMRowR + 2, kMRowBx = 2 * (kMRowR + 2), kMRowBy = kMRowBx + kMRowR,
               kMRowBz = kMRowBy + kMRowR + 1, kMRowSlots = kMRowBz + kMRowR;  // row slots per plane (25)
-constexpr int kMRowXch = 6;  // scalar exchange slots per direction, per group and warp
+constexpr int kMRowXch = 12;  // scalar exchange slots per thread: 6 per advection (q, q, qh, qh, qh, f)
 
 __host__ __device__ constexpr size_t mag_row_smem(int nx) {
   return ((size_t)2 * kMRowSlots + 2 * (kMRowR + 2) + (kMRowR + 1)) * nx * 4 +
-         (size_t)2 * kMRowXch * (kMRowR + 1) * (nx / kRowCells / 32) * 4;
+         (size_t)kMRowXch * (kMRowR + 1) * (nx / kRowCells) * 4;
 }
 
 __device__ __forceinline__ void mag_row_issue(const MagArgs& a, uint32_t dst, uint32_t bar, int j0, int p, int nx,
@@ -387,25 +372,15 @@ __device__ __forceinline__ void group_sync(int g, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(n) : "memory");
 }
 
-// Scalar neighbour exchange of one thread group (as RowXch).
-struct RowXch1 {
-  int lane, w, wl, wr, nw;
-  float* sR;  // [slot][warp]
-  float* sL;
-  __device__ __forceinline__ void send_right(int slot, float v) const {
-    if (lane == 31) sR[slot * nw + w] = v;
-  }
-  __device__ __forceinline__ void send_left(int slot, float v) const {
-    if (lane == 0) sL[slot * nw + w] = v;
-  }
-  __device__ __forceinline__ float from_left(int slot, float v) const {
-    const float x = __shfl_up_sync(~0u, v, 1);
-    return lane == 0 ? sR[slot * nw + wl] : x;
-  }
-  __device__ __forceinline__ float from_right(int slot, float v) const {
-    const float x = __shfl_down_sync(~0u, v, 1);
-    return lane == 31 ? sL[slot * nw + wr] : x;
-  }
+// Scalar exchange slots of one thread group: every thread stores its value
+// of a slot at [slot][thread] and reads its neighbour's (l-1 or l+1,
+// periodic over the group's T threads).
+struct RowSlots1 {
+  float* S;
+  int T, l, lm, lp;
+  __device__ __forceinline__ void put(int slot, float v) const { S[slot * T + l] = v; }
+  __device__ __forceinline__ float left(int slot) const { return S[slot * T + lm]; }
+  __device__ __forceinline__ float right(int slot) const { return S[slot * T + lp]; }
 };
 
 // One edge-flux row of the thread's 4 cells, in three parts separated by
@@ -416,17 +391,17 @@ struct RowAdvect {
   float ub[kRowCells + 1];     // edge velocity at 4l-1/2 .. 4l+7/2
   float qh[kRowCells];         // half-step field
   float f[kRowCells];          // edge flux at 4l+1/2 .. 4l+7/2
-  // part 1: edge velocities; send q(4l+3) right, q(4l) left
-  __device__ __forceinline__ void part1(const float (&u)[kRowCells + 2], const RowXch1& X, int slot) {
+  // part 1: edge velocities; q(4l+3) and q(4l) into slots slot, slot+1
+  __device__ __forceinline__ void part1(const float (&u)[kRowCells + 2], const RowSlots1& X, int slot) {
 #pragma unroll
     for (int e = 0; e <= kRowCells; e++) ub[e] = __fmul_rn(0.5f, __fadd_rn(u[e], u[e + 1]));
-    X.send_right(slot, q[kRowCells - 1]);
-    X.send_left(slot, q[0]);
+    X.put(slot, q[kRowCells - 1]);
+    X.put(slot + 1, q[0]);
   }
-  // part 2 (after a barrier): first-order fluxes and the half step; send
-  // qh(4l+3) right, qh(4l), qh(4l+1) left
-  __device__ __forceinline__ void part2(float c_half, const RowXch1& X, int slot) {
-    const float qL = X.from_left(slot, q[kRowCells - 1]), qR = X.from_right(slot, q[0]);
+  // part 2 (after a barrier): first-order fluxes and the half step;
+  // qh(4l+3), qh(4l), qh(4l+1) into slots slot+2 .. slot+4
+  __device__ __forceinline__ void part2(float c_half, const RowSlots1& X, int slot) {
+    const float qL = X.left(slot), qR = X.right(slot + 1);
     float g[kRowCells + 1];  // at 4l-1/2 .. 4l+7/2
 #pragma unroll
     for (int e = 0; e <= kRowCells; e++) {
@@ -435,18 +410,18 @@ struct RowAdvect {
     }
 #pragma unroll
     for (int i = 0; i < kRowCells; i++) qh[i] = __fmaf_rn(-c_half, __fsub_rn(g[i + 1], g[i]), q[i]);
-    X.send_right(slot + 1, qh[kRowCells - 1]);
-    X.send_left(slot + 1, qh[0]);
-    X.send_left(slot + 2, qh[1]);
+    X.put(slot + 2, qh[kRowCells - 1]);
+    X.put(slot + 3, qh[0]);
+    X.put(slot + 4, qh[1]);
   }
   // part 3 (after a barrier): the limited edge fluxes f(4l+1/2 .. 4l+7/2)
-  __device__ __forceinline__ void part3(const RowXch1& X, int slot) {
+  __device__ __forceinline__ void part3(const RowSlots1& X, int slot) {
     float h[kRowCells + 3];  // qh at 4l-1 .. 4l+5
-    h[0] = X.from_left(slot + 1, qh[kRowCells - 1]);
+    h[0] = X.left(slot + 2);
 #pragma unroll
     for (int i = 0; i < kRowCells; i++) h[i + 1] = qh[i];
-    h[kRowCells + 1] = X.from_right(slot + 1, qh[0]);
-    h[kRowCells + 2] = X.from_right(slot + 2, qh[1]);
+    h[kRowCells + 1] = X.right(slot + 3);
+    h[kRowCells + 2] = X.right(slot + 4);
     float d[kRowCells + 2];  // d(i) = qh(i) - qh(i-1), i = 4l .. 4l+5
 #pragma unroll
     for (int i = 0; i < kRowCells + 2; i++) d[i] = __fsub_rn(h[i + 1], h[i]);
@@ -482,14 +457,12 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
   float* P = ms_dyn;                                   // [2][slots][nx]
   float* vring = P + 2 * kMRowSlots * nx;              // [2][R+2][nx]: v of rows j0-1 .. j0+R
   float* ey = vring + 2 * (R + 2) * nx;                // [R+1][nx]: E_y of rows j0 .. j0+R
-  RowXch1 X;
-  X.lane = l & 31;
-  X.w = l >> 5;
-  X.nw = T >> 5;
-  X.wl = X.w == 0 ? X.nw - 1 : X.w - 1;
-  X.wr = X.w + 1 == X.nw ? 0 : X.w + 1;
-  X.sR = ey + (R + 1) * nx + g * 2 * kMRowXch * X.nw;
-  X.sL = X.sR + kMRowXch * X.nw;
+  RowSlots1 X;
+  X.T = T;
+  X.l = l;
+  X.lm = l == 0 ? T - 1 : l - 1;
+  X.lp = l + 1 == T ? 0 : l + 1;
+  X.S = ey + (R + 1) * nx + g * kMRowXch * T;
 
   const float tau = *a.tau;
   const float c_full = tau * a.box.ih[0];
@@ -569,20 +542,20 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
       face_u(vprev + vs * nx, vprev + (vs - 1) * nx, u);
 #pragma unroll
       for (int i = 0; i < kRowCells; i++) Ay.q[i] = cby[i];
-      Ay.part1(u, X, 3);
+      Ay.part1(u, X, 6);
     }
     // the exchanges along a row need only the row's own warps: a named
     // barrier per group (the block-wide ones cost 1.5x the step at 256^3)
     group_sync(g, T);
     if (doz) Az.part2(c_half, X, 0);
-    if (doy) Ay.part2(c_half, X, 3);
+    if (doy) Ay.part2(c_half, X, 6);
     group_sync(g, T);
     if (doz) {
       Az.part3(X, 0);
-      X.send_right(0, Az.f[kRowCells - 1]);
+      X.put(5, Az.f[kRowCells - 1]);
     }
     if (doy) {
-      Ay.part3(X, 3);
+      Ay.part3(X, 6);
       *reinterpret_cast<float4*>(ey + (vs - 1) * nx + x0) = make_float4(Ay.f[0], Ay.f[1], Ay.f[2], Ay.f[3]);
     }
     // the raw fields of plane p for the next step (read late: fewer live registers)
@@ -601,7 +574,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
     }
     float ezc[kRowCells + 1];  // E_z(p) at 4l-1/2 .. 4l+7/2
     if (doz) {
-      ezc[0] = X.from_left(0, Az.f[kRowCells - 1]);
+      ezc[0] = X.left(5);
 #pragma unroll
       for (int e = 0; e < kRowCells; e++) ezc[e + 1] = Az.f[e];
     }
