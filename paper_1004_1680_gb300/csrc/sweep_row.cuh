@@ -340,7 +340,7 @@ constexpr int kMRowRho = 0, kMRowMx = kMRowR + 2, kMRowBx = 2 * (kMRowR + 2), kM
 constexpr int kMRowXch = 12;  // scalar exchange slots per thread: 6 per advection (q, q, qh, qh, qh, f)
 
 __host__ __device__ constexpr size_t mag_row_smem(int nx) {
-  return ((size_t)2 * kMRowSlots + 2 * (kMRowR + 2) + (kMRowR + 1)) * nx * 4 +
+  return ((size_t)2 * kMRowSlots + 2 * (kMRowR + 2) + 2 * (kMRowR + 1)) * nx * 4 +
          (size_t)kMRowXch * (kMRowR + 1) * (nx / kRowCells) * 4;
 }
 
@@ -456,13 +456,15 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
   const int tid = g * T + l;
   float* P = ms_dyn;                                   // [2][slots][nx]
   float* vring = P + 2 * kMRowSlots * nx;              // [2][R+2][nx]: v of rows j0-1 .. j0+R
-  float* ey = vring + 2 * (R + 2) * nx;                // [R+1][nx]: E_y of rows j0 .. j0+R
+  // [2][R+1][nx]: E_y of rows j0 .. j0+R, by step parity (a group may run a
+  // step ahead of the one below it, which still reads its E_y row)
+  float* ey2 = vring + 2 * (R + 2) * nx;
   RowSlots1 X;
   X.T = T;
   X.l = l;
   X.lm = l == 0 ? T - 1 : l - 1;
   X.lp = l + 1 == T ? 0 : l + 1;
-  X.S = ey + (R + 1) * nx + g * kMRowXch * T;
+  X.S = ey2 + 2 * (R + 1) * nx + g * kMRowXch * T;
 
   const float tau = *a.tau;
   const float c_full = tau * a.box.ih[0];
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
     const float* sb = P + (s & 1) * kMRowSlots * nx;
     if (!sweep_mbar_wait(smem_u32(&mbarr[s & 1]), (s >> 1) & 1)) gave_up = true;
     float* vcur = vring + (s & 1) * (R + 2) * nx;
+    float* ey = ey2 + (s & 1) * (R + 1) * nx;
     const float* vprev = vring + ((s + 1) & 1) * (R + 2) * nx;
     auto ld4 = [&](int slot, float (&d)[kRowCells]) {
       const float4 v = *reinterpret_cast<const float4*>(sb + slot * nx + x0);
@@ -516,10 +519,9 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
         vel(g + 1);
       }
     }
-    if (__syncthreads_or(gave_up)) {
-      gave_up = true;
-      break;
-    }
+    // v(p) of a row is read at this step by its own group only; the other
+    // groups read it at the next step, after this step's block barrier
+    group_sync(g, T);
     const bool doz = !halo && s >= 1, doy = s >= 2;
     // face velocities at cells 4l-1 .. 4l+4 of two v rows: (own + other) / 2
     auto face_u = [&](const float* va, const float* vb, float (&u)[kRowCells + 2]) {
@@ -567,7 +569,12 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
       ld4(kMRowBy + g, nby);
       ld4(kMRowBz + g, nbz);
     }
-    __syncthreads();
+    // the step's one block barrier: E_y rows and v(p) published, plane p
+    // read by every thread; it also carries a failed wait
+    if (__syncthreads_or(gave_up)) {
+      gave_up = true;
+      break;
+    }
     if (s + 2 < nsteps) {  // every thread has read plane p: plane p+2 goes into its buffer
       if (tid == 0) mag_row_issue(a, smem_u32(P + (s & 1) * kMRowSlots * nx), smem_u32(&mbarr[s & 1]), j0, p + 2, nx, ny, nz);
       issued++;
