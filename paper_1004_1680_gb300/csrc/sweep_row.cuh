@@ -65,11 +65,15 @@ __device__ __forceinline__ void v5_put(float* s, int stride, int i, const V5& v)
 //            the left; then F2(4l+7/2) to the right
 //   Unew(i) = U(i) - tau/h (F2(i+1/2) - F2(i-1/2))
 constexpr int kFRowFields = 10;
-constexpr int kFRowBufs = 2;   // rows in flight per block (three measured the same, and leave no room for the slots)
+constexpr int kFRowBufs = 2;   // buffers of the conserved fields' rows
 constexpr int kFRowSlots = 7;  // exchanged V5 values per thread: FR(4l+3), FL(4l); Rh(4l+3), Rh(4l), Lh(4l), Lh(4l+1); F2
 
+// Shared memory: kFRowBufs x 5 rows of rho, m, e (read until the row's last
+// phase), one set of the 5 face-field rows (read in stage 1 only: the next
+// row's copies may land on them once every warp is past stage 1), the
+// exchange slots.  47.9 KB at 512 cells: 4 blocks per SM.
 __host__ __device__ constexpr size_t fluid_row_smem(int nx) {
-  return (size_t)kFRowBufs * kFRowFields * nx * 4 + (size_t)kFRowSlots * (nx / kRowCells) * 20;
+  return (size_t)(kFRowBufs * 5 + 5) * nx * 4 + (size_t)kFRowSlots * (nx / kRowCells) * 20;
 }
 
 // The exchange slots of the fluid row sweep: every thread stores its value
@@ -92,8 +96,8 @@ struct RowSlots {
   }
 };
 
-__device__ __forceinline__ void fluid_row_issue(const FluidArgs& a, uint32_t dst, uint32_t bar, int r, int nx,
-                                                int ny, int nz) {
+__device__ __forceinline__ void fluid_row_issue(const FluidArgs& a, uint32_t dst, uint32_t dstb, uint32_t bar, int r,
+                                                int nx, int ny, int nz) {
   const int y = r % ny, z = r / ny;
   const long long sy = nx, sz = (long long)nx * ny;
   const long long o = y * sy + z * sz;
@@ -106,11 +110,11 @@ __device__ __forceinline__ void fluid_row_issue(const FluidArgs& a, uint32_t dst
   bulk_load(dst + 2 * bytes, a.in[MY] + o, bytes, bar);
   bulk_load(dst + 3 * bytes, a.in[MZ] + o, bytes, bar);
   bulk_load(dst + 4 * bytes, a.in[EN] + o, bytes, bar);
-  bulk_load(dst + 5 * bytes, a.in[BX] + o, bytes, bar);
-  bulk_load(dst + 6 * bytes, a.in[BY] + o, bytes, bar);
-  bulk_load(dst + 7 * bytes, a.in[BY] + oy, bytes, bar);
-  bulk_load(dst + 8 * bytes, a.in[BZ] + o, bytes, bar);
-  bulk_load(dst + 9 * bytes, a.in[BZ] + oz, bytes, bar);
+  bulk_load(dstb + 0 * bytes, a.in[BX] + o, bytes, bar);
+  bulk_load(dstb + 1 * bytes, a.in[BY] + o, bytes, bar);
+  bulk_load(dstb + 2 * bytes, a.in[BY] + oy, bytes, bar);
+  bulk_load(dstb + 3 * bytes, a.in[BZ] + o, bytes, bar);
+  bulk_load(dstb + 4 * bytes, a.in[BZ] + oz, bytes, bar);
 }
 
 // U of the thread's 4 cells from the staged row
@@ -128,34 +132,40 @@ __device__ __forceinline__ void row_state(const float* sb, int nx, int x0, V5 (&
 struct B3 {
   float v[3];
 };
-__device__ __forceinline__ void row_fields(const float* sb, int nx, int x0, int xn, B3 (&B)[kRowCells]) {
-  const float4 bx = *reinterpret_cast<const float4*>(sb + 5 * nx + x0);
-  const float4 by0 = *reinterpret_cast<const float4*>(sb + 6 * nx + x0);
-  const float4 by1 = *reinterpret_cast<const float4*>(sb + 7 * nx + x0);
-  const float4 bz0 = *reinterpret_cast<const float4*>(sb + 8 * nx + x0);
-  const float4 bz1 = *reinterpret_cast<const float4*>(sb + 9 * nx + x0);
-  const float bxa[kRowCells + 1] = {bx.x, bx.y, bx.z, bx.w, sb[5 * nx + xn]};
+// sbb: the staged rows b_x, b_y, b_y(+y), b_z, b_z(+z)
+__device__ __forceinline__ void row_fields(const float* sbb, int nx, int x0, int xn, B3 (&B)[kRowCells]) {
+  const float4 bx = *reinterpret_cast<const float4*>(sbb + 0 * nx + x0);
+  const float4 by0 = *reinterpret_cast<const float4*>(sbb + 1 * nx + x0);
+  const float4 by1 = *reinterpret_cast<const float4*>(sbb + 2 * nx + x0);
+  const float4 bz0 = *reinterpret_cast<const float4*>(sbb + 3 * nx + x0);
+  const float4 bz1 = *reinterpret_cast<const float4*>(sbb + 4 * nx + x0);
+  const float bxa[kRowCells + 1] = {bx.x, bx.y, bx.z, bx.w, sbb[xn]};
 #pragma unroll
   for (int j = 0; j < kRowCells; j++)
     B[j] = {{face_mean(bxa[j], bxa[j + 1]), face_mean((&by0.x)[j], (&by1.x)[j]), face_mean((&bz0.x)[j], (&bz1.x)[j])}};
 }
 
-// 3 blocks of 128 threads per SM: about 170 registers, no spills (at 4
-// blocks and 128 registers the kernel spills and measured 1.77 against 1.54
-// ms at 512^3 with two buffers).
+// 4 blocks of 128 threads per SM (128 registers, no spills since the
+// exchanges go through the slots).
 template <bool RATE, bool FLOOR, int LIM, int FRZ>
-__global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __grid_constant__ FluidArgs a) {
+__global__ void __launch_bounds__(kRowMaxThreads, 4) fluid_row_kernel(const __grid_constant__ FluidArgs a) {
   static_assert(FRZ != 2, "the per-pencil freezing speed keeps the pencil sweeps");
   extern __shared__ __align__(128) float rs_dyn[];
   __shared__ alignas(8) unsigned long long rbar[kFRowBufs];
-  __shared__ alignas(8) unsigned long long xbar[2];  // split-phase exchanges: stage 1, F2 (one arrival per warp)
+  // split-phase exchanges (stage 1, stage 2, F2; one arrival per warp) and
+  // the block's stop flag: a warp whose bounded wait ran out raises it and
+  // leaves the row loop; the others see it at their next wait (their waits
+  // on the missing warp's arrivals run out too, within the bound)
+  __shared__ alignas(8) unsigned long long xbar[3];
+  __shared__ int stop;
   const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
   const int T = nx / kRowCells, l = threadIdx.x;
   const int rows = ny * nz;
   const int lane = l & 31, nw = T >> 5;
   const int lm = l == 0 ? T - 1 : l - 1, lp = l + 1 == T ? 0 : l + 1;  // neighbour threads (periodic)
+  const float* sbb = rs_dyn + kFRowBufs * 5 * nx;  // the face-field rows
   RowSlots X;
-  X.A = reinterpret_cast<float4*>(rs_dyn + kFRowBufs * kFRowFields * nx);
+  X.A = reinterpret_cast<float4*>(rs_dyn + (kFRowBufs * 5 + 5) * nx);
   X.E = reinterpret_cast<float*>(X.A + kFRowSlots * T);
   X.T = T;
 
@@ -166,25 +176,35 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
   const int x0 = kRowCells * l;
   const int xn = l + 1 == T ? 0 : x0 + kRowCells;  // the next thread's first cell
   float rmax = 0.f;
+  bool gave_up = false;
 
   if (l == 0) {
     for (int k = 0; k < kFRowBufs; k++) mbar_init(smem_u32(&rbar[k]), 1);
-    mbar_init(smem_u32(&xbar[0]), nw);
-    mbar_init(smem_u32(&xbar[1]), nw);
+    for (int k = 0; k < 3; k++) mbar_init(smem_u32(&xbar[k]), nw);
+    stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // a bounded wait, decided for the whole warp; false: leave the row loop
+  auto wait_ok = [&](uint32_t bar, uint32_t parity) {
+    const bool ok = sweep_mbar_wait(bar, parity);
+    if (__any_sync(~0u, !ok || *reinterpret_cast<volatile int*>(&stop) != 0)) {
+      gave_up = true;
+      if (lane == 0) *reinterpret_cast<volatile int*>(&stop) = 1;
+      return false;
+    }
+    return true;
+  };
   int issued = 0;  // rows issued so far (the same count in every thread)
   for (int k = 0; k < kFRowBufs - 1 && blockIdx.x + k * gridDim.x < rows; k++, issued++)
     if (l == 0)
-      fluid_row_issue(a, smem_u32(rs_dyn + k * kFRowFields * nx), smem_u32(&rbar[k]), blockIdx.x + k * gridDim.x,
+      fluid_row_issue(a, smem_u32(rs_dyn + k * 5 * nx), smem_u32(sbb), smem_u32(&rbar[k]), blockIdx.x + k * gridDim.x,
                       nx, ny, nz);
 
-  bool gave_up = false;
   int it = 0, buf = 0, use = 0;  // iteration, its buffer, and the buffer's use count (mbarrier phase)
   for (int r = blockIdx.x; r < rows; r += gridDim.x, it++) {
-    const float* sb = rs_dyn + buf * kFRowFields * nx;
-    if (!sweep_mbar_wait(smem_u32(&rbar[buf]), use & 1)) gave_up = true;
+    const float* sb = rs_dyn + buf * 5 * nx;
+    if (!wait_ok(smem_u32(&rbar[buf]), use & 1)) break;
     // stage 1: the interface fluxes inside the thread's cells right away;
     // FR(4l+3) and FL(4l) wait for the neighbours' halves.  The state is read
     // again (16-byte reads: no bank conflicts) wherever it is needed, while
@@ -192,7 +212,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
     V5 f1[kRowCells + 1];  // flux1 at 4l-1/2 .. 4l+7/2
     V5 FR3, FL0;
     B3 B[kRowCells];
-    row_fields(sb, nx, x0, xn, B);
+    row_fields(sbb, nx, x0, xn, B);
     {
       V5 U[kRowCells];
       row_state(sb, nx, x0, U);
@@ -222,12 +242,13 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
       // stage 2
       split_flux<FRZ, true>(Uh, B[j].v[0], make_float2(B[j].v[1], B[j].v[2]), gamma, Rh[j], Lh[j]);
     }
-    if (!sweep_mbar_wait(smem_u32(&xbar[0]), it & 1)) gave_up = true;
-    // every warp is done with the previous row: the row after next goes into its buffer
+    if (!wait_ok(smem_u32(&xbar[0]), it & 1)) break;
+    // every warp is done with the previous row and past this row's stage 1:
+    // the next row goes into the other buffer and onto the face-field rows
     if (r + (kFRowBufs - 1) * gridDim.x < rows) {
       const int nb = issued % kFRowBufs;
       if (l == 0)
-        fluid_row_issue(a, smem_u32(rs_dyn + nb * kFRowFields * nx), smem_u32(&rbar[nb]),
+        fluid_row_issue(a, smem_u32(rs_dyn + nb * 5 * nx), smem_u32(sbb), smem_u32(&rbar[nb]),
                         r + (kFRowBufs - 1) * gridDim.x, nx, ny, nz);
       issued++;
     }
@@ -242,38 +263,33 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
     X.put(3, l, Rh[0]);
     X.put(4, l, Lh[0]);
     X.put(5, l, Lh[1]);
-    if (__syncthreads_or(gave_up)) {
-      gave_up = true;
-      break;
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&xbar[1]));
+    // interface i+1/2, i = 4l + j: Rh(i-1..i+1), Lh(i..i+2)
+    auto flux2 = [&](int j, const V5& Rl, const V5& Rr, const V5& L1, const V5& L2) {
+      const V5 right = v5_add(Rh[j], half_limited5<LIM>(v5_sub(Rh[j], Rl), v5_sub(Rr, Rh[j])));
+      const V5 left = v5_sub(L1, half_limited5<LIM>(v5_sub(L1, Lh[j]), v5_sub(L2, L1)));
+      return v5_sub(right, left);
+    };
     V5 F2[kRowCells];
+    F2[1] = flux2(1, Rh[0], Rh[2], Lh[2], Lh[3]);  // inside the thread's cells, while the neighbours' values arrive
+    if (!wait_ok(smem_u32(&xbar[1]), it & 1)) break;
     {
       const V5 Rm = X.get(2, lm);                                         // Rh(4l-1)
       const V5 Rp = X.get(3, lp), Lp0 = X.get(4, lp), Lp1 = X.get(5, lp);  // Rh(4l+4), Lh(4l+4), Lh(4l+5)
-#pragma unroll
-      for (int j = 0; j < kRowCells; j++) {
-        // interface i+1/2, i = 4l + j: Rh(i-1..i+1), Lh(i..i+2)
-        const V5 Ri = Rh[j];
-        const V5 Rl = j == 0 ? Rm : Rh[j - 1];
-        const V5 Rr = j + 1 < kRowCells ? Rh[j + 1] : Rp;
-        const V5 Li = Lh[j];
-        const V5 L1 = j + 1 < kRowCells ? Lh[j + 1] : Lp0;
-        const V5 L2 = j + 2 < kRowCells ? Lh[j + 2] : (j + 2 == kRowCells ? Lp0 : Lp1);
-        const V5 right = v5_add(Ri, half_limited5<LIM>(v5_sub(Ri, Rl), v5_sub(Rr, Ri)));
-        const V5 left = v5_sub(L1, half_limited5<LIM>(v5_sub(L1, Li), v5_sub(L2, L1)));
-        F2[j] = v5_sub(right, left);
-      }
+      F2[0] = flux2(0, Rm, Rh[1], Lh[1], Lh[2]);
+      F2[2] = flux2(2, Rh[1], Rh[3], Lh[3], Lp0);
+      F2[3] = flux2(3, Rh[2], Rp, Lp0, Lp1);
     }
     X.put(6, l, F2[kRowCells - 1]);
     __syncwarp();
-    if (lane == 0) mbar_arrive(smem_u32(&xbar[1]));
+    if (lane == 0) mbar_arrive(smem_u32(&xbar[2]));
     // the finished cells: 1 .. 3 while F2(4l-1/2) arrives, then cell 0
     const int y = r % ny, z = r / ny;
     const long long ro = (long long)y * nx + (long long)z * nx * ny + x0;
     const bool rate_row = RATE && y >= a.rate_lo[1] && y < a.rate_hi[1] && z >= a.rate_lo[2] && z < a.rate_hi[2];
     float o[kRowCells][5];
     row_state(sb, nx, x0, U);
-    if (FLOOR || RATE) row_fields(sb, nx, x0, xn, B);
     auto finish = [&](int j, const V5& fl) {
       const V5 v = v5_fma(-c_full, v5_sub(F2[j], fl), U[j]);
       o[j][0] = v.p0.x;
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, 3) fluid_row_kernel(const __gr
     };
 #pragma unroll
     for (int j = 1; j < kRowCells; j++) finish(j, F2[j - 1]);
-    if (!sweep_mbar_wait(smem_u32(&xbar[1]), it & 1)) gave_up = true;
+    if (!wait_ok(smem_u32(&xbar[2]), it & 1)) break;
     finish(0, X.get(6, lm));  // F2(4l-1/2)
 #pragma unroll
     for (int q = 0; q < 5; q++)
