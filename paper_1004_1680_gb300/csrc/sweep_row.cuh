@@ -37,24 +37,15 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const float* src, uint32
       : "memory");
 }
 
-__device__ __forceinline__ V5 v5_of(const float* s, int stride, int i) {
-  return {make_float2(s[i], s[stride + i]), make_float2(s[2 * stride + i], s[3 * stride + i]), s[4 * stride + i]};
-}
-__device__ __forceinline__ void v5_put(float* s, int stride, int i, const V5& v) {
-  s[i] = v.p0.x;
-  s[stride + i] = v.p0.y;
-  s[2 * stride + i] = v.p1.x;
-  s[3 * stride + i] = v.p1.y;
-  s[4 * stride + i] = v.e;
-}
-
 // ---------------------------------------------------------------------------
 // Fluid sweep along x.  A row's copy set is 10 field rows of nx floats: rho,
 // m_x, m_y, m_z, e, b_x, b_y, b_y of the row +1 along y, b_z, b_z of the row
-// +1 along z (the face fields' high faces of the cell-centred field).  Two
-// buffers: the copies of the block's next row go into the buffer of the row
-// before once every warp is done with it (at the first exchange of this
-// row), so the staged row stays readable for the whole of its computation.
+// +1 along z (the face fields' high faces of the cell-centred field).  The
+// copies of the block's next row are issued at the first exchange of this
+// row, once every warp is done with the row before and past this row's
+// stage 1: rho, m, e into the other of two buffers (this row's stay
+// readable to the end of its computation), the face fields onto the one set
+// of face-field rows (read in stage 1 only).
 //
 // Per row, with thread l owning cells i = 4l .. 4l+3 (periodic along x):
 //   stage 1: FR, FL of U; flux1(i+1/2) = FR(i) - FL(i+1);
@@ -68,10 +59,9 @@ constexpr int kFRowFields = 10;
 constexpr int kFRowBufs = 2;   // buffers of the conserved fields' rows
 constexpr int kFRowSlots = 7;  // exchanged V5 values per thread: FR(4l+3), FL(4l); Rh(4l+3), Rh(4l), Lh(4l), Lh(4l+1); F2
 
-// Shared memory: kFRowBufs x 5 rows of rho, m, e (read until the row's last
-// phase), one set of the 5 face-field rows (read in stage 1 only: the next
-// row's copies may land on them once every warp is past stage 1), the
-// exchange slots.  47.9 KB at 512 cells: 4 blocks per SM.
+// Shared memory: kFRowBufs x 5 rows of rho, m, e, one set of the 5
+// face-field rows, the exchange slots.  47.9 KB at 512 cells: 4 blocks per
+// SM.
 __host__ __device__ constexpr size_t fluid_row_smem(int nx) {
   return (size_t)(kFRowBufs * 5 + 5) * nx * 4 + (size_t)kFRowSlots * (nx / kRowCells) * 20;
 }
@@ -348,8 +338,10 @@ __global__ void __launch_bounds__(kRowMaxThreads, 4) fluid_row_kernel(const __gr
 // memory.  Each staged plane holds rho and m_x of rows j0-1 .. j0+R, b_x and
 // b_z of the tile's rows and b_y of rows j0 .. j0+R (ten bulk copies, the
 // tile's rows in one piece each); two buffers, the copies of plane p+2 going
-// into plane p's once every thread has read it (after the step's third
-// exchange barrier).
+// into plane p's once every thread has read it (after the step's block
+// barrier).  The exchanges along a row wait for the row's own warps only (a
+// named barrier per group); a group may run up to a step ahead of the
+// others, which the double-buffered v and E_y rows allow.
 constexpr int kMRowR = 4;
 constexpr int kMRowRho = 0, kMRowMx = kMRowR + 2, kMRowBx = 2 * (kMRowR + 2), kMRowBy = kMRowBx + kMRowR,
               kMRowBz = kMRowBy + kMRowR + 1, kMRowSlots = kMRowBz + kMRowR;  // row slots per plane (25)
