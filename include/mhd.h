@@ -196,8 +196,9 @@ int mhd_set_fusion(mhd_t *m, int on);
  * multiple of 32 and row extent a multiple of 8.  Along x (x path 1, see
  * mhd_set_xpath) whole x rows are copied into shared memory, each thread
  * computing 4 consecutive cells: fluid sweeps with nx a multiple of 128 up
- * to 2048, magnetic sweeps with nx a multiple of 128 up to 512 and ny a
- * multiple of 4 (not with the per-pencil freezing speed).  Every other scheme
+ * to 1024, magnetic sweeps with nx a multiple of 128 up to 1024 and ny a
+ * multiple of 4 (2 for nx above 512) (not with the per-pencil freezing
+ * speed).  Every other scheme
  * variant of mhd_set_scheme is staged.  The values and their arithmetic are
  * those of the register-load sweeps, except that the staged fluid sweeps
  * take the freezing speeds' square roots from the hardware approximation (a

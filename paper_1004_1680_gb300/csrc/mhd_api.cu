@@ -111,14 +111,15 @@ struct mhd_s {
 namespace {
 
 // x sweeps run directly along x when both row sweeps take the box (whole
-// x rows staged in shared memory: nx a multiple of 128 up to 512, ny a
-// multiple of 4, tensor-copy staging on, a freezing speed of its own per
-// cell); otherwise they go through the exchanged layout once the state no
-// longer fits in L2 (the pencil sweeps along x read 32 different lines per
-// warp and position, which only L2 can absorb).
+// x rows staged in shared memory: nx a multiple of 128 up to 1024, ny a
+// multiple of the magnetic tile's rows (4, or 2 for rows longer than 512),
+// tensor-copy staging on, a freezing speed of its own per cell); otherwise
+// they go through the exchanged layout once the state no longer fits in L2
+// (the pencil sweeps along x read 32 different lines per warp and position,
+// which only L2 can absorb).
 int auto_xpath(const mhd_s* m) {
-  const bool rows = m->tma && m->fast != 2 && m->n[0] % 128 == 0 && m->n[0] <= 512 && m->n[1] % 4 == 0 &&
-                    m->n[2] >= 2;
+  const bool rows = m->tma && m->fast != 2 && m->n[0] % 128 == 0 && m->n[0] <= 1024 &&
+                    m->n[1] % (m->n[0] <= 512 ? 4 : 2) == 0 && m->n[2] >= 2;
   if (rows) return 1;
   return m->N * 32LL > (64LL << 20) ? 2 : 1;
 }

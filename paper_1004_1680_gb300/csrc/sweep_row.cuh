@@ -25,7 +25,7 @@
 namespace mhd {
 
 constexpr int kRowCells = 4;        // consecutive cells per thread
-constexpr int kRowMaxThreads = 128; // rows of up to 512 cells
+constexpr int kRowMaxThreads = 256; // rows of up to 1024 cells
 
 // One-dimensional bulk copy of `bytes` (a multiple of 16, both addresses
 // 16-byte aligned) from global memory into shared memory, completing on the
@@ -135,10 +135,11 @@ __device__ __forceinline__ void row_fields(const float* sbb, int nx, int x0, int
     B[j] = {{face_mean(bxa[j], bxa[j + 1]), face_mean((&by0.x)[j], (&by1.x)[j]), face_mean((&bz0.x)[j], (&bz1.x)[j])}};
 }
 
-// 4 blocks of 128 threads per SM (128 registers, no spills since the
-// exchanges go through the slots).
+// 128 registers: 4 blocks of 128 threads (512-cell rows) or 2 of 256
+// (1024-cell rows) per SM; no spills since the exchanges go through the
+// slots.
 template <bool RATE, bool FLOOR, int LIM, int FRZ>
-__global__ void __launch_bounds__(kRowMaxThreads, 4) fluid_row_kernel(const __grid_constant__ FluidArgs a) {
+__global__ void __launch_bounds__(kRowMaxThreads, 2) fluid_row_kernel(const __grid_constant__ FluidArgs a) {
   static_assert(FRZ != 2, "the per-pencil freezing speed keeps the pencil sweeps");
   extern __shared__ __align__(128) float rs_dyn[];
   __shared__ alignas(8) unsigned long long rbar[kFRowBufs];
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, 4) fluid_row_kernel(const __gr
 }
 
 // ---------------------------------------------------------------------------
-// Magnetic sweep along x.  A block owns a tile of kMRowR rows along y (rows
+// Magnetic sweep along x.  A block owns a tile of R rows along y (rows
 // j0 .. j0+R-1) and marches it along z over a segment of planes k0 .. k0+L-1,
 // one thread group (threadIdx.y) per row plus a halo group for row j0+R.
 // For each row the edge fluxes of b_y and b_z along x (MagPipe's arithmetic,
@@ -342,36 +343,44 @@ __global__ void __launch_bounds__(kRowMaxThreads, 4) fluid_row_kernel(const __gr
 // barrier).  The exchanges along a row wait for the row's own warps only (a
 // named barrier per group); a group may run up to a step ahead of the
 // others, which the double-buffered v and E_y rows allow.
-constexpr int kMRowR = 4;
-constexpr int kMRowRho = 0, kMRowMx = kMRowR + 2, kMRowBx = 2 * (kMRowR + 2), kMRowBy = kMRowBx + kMRowR,
-              kMRowBz = kMRowBy + kMRowR + 1, kMRowSlots = kMRowBz + kMRowR;  // row slots per plane (25)
+// Rows per tile: 4 for rows of up to 512 cells (5 groups of nx/4 threads,
+// 640 threads), 2 for 1024 cells (3 groups of 256 threads, 768).
+__host__ __device__ constexpr int mag_row_tile(int nx) { return nx <= 512 ? 4 : 2; }
+// Row slots of a staged plane for a tile of R rows: rho and m_x of rows
+// j0-1 .. j0+R, b_x of the tile, b_y of rows j0 .. j0+R, b_z of the tile.
+template <int R>
+struct MRow {
+  static constexpr int Rho = 0, Mx = R + 2, Bx = 2 * (R + 2), By = Bx + R, Bz = By + R + 1, Slots = Bz + R;
+};
 constexpr int kMRowXch = 12;  // scalar exchange slots per thread: 6 per advection (q, q, qh, qh, qh, f)
 
+template <int R>
 __host__ __device__ constexpr size_t mag_row_smem(int nx) {
-  return ((size_t)2 * kMRowSlots + 2 * (kMRowR + 2) + 2 * (kMRowR + 1)) * nx * 4 +
-         (size_t)kMRowXch * (kMRowR + 1) * (nx / kRowCells) * 4;
+  return ((size_t)2 * MRow<R>::Slots + 2 * (R + 2) + 2 * (R + 1)) * nx * 4 +
+         (size_t)kMRowXch * (R + 1) * (nx / kRowCells) * 4;
 }
 
+template <int R>
 __device__ __forceinline__ void mag_row_issue(const MagArgs& a, uint32_t dst, uint32_t bar, int j0, int p, int nx,
                                               int ny, int nz) {
-  constexpr int R = kMRowR;
+  using M = MRow<R>;
   const int k = p < 0 ? p + nz : (p >= nz ? p - nz : p);
   const long long sz = (long long)nx * ny;
   const long long o = (long long)j0 * nx + k * sz;                                // row j0
   const long long om = (long long)(j0 == 0 ? ny - 1 : j0 - 1) * nx + k * sz;      // row j0-1
   const long long op = (long long)(j0 + R == ny ? 0 : j0 + R) * nx + k * sz;      // row j0+R
   const uint32_t row = (uint32_t)nx * 4;
-  mbar_expect_tx(bar, kMRowSlots * row);
-  bulk_load(dst + (kMRowRho + 0) * row, a.in[RHO] + om, row, bar);
-  bulk_load(dst + (kMRowRho + 1) * row, a.in[RHO] + o, R * row, bar);
-  bulk_load(dst + (kMRowRho + R + 1) * row, a.in[RHO] + op, row, bar);
-  bulk_load(dst + (kMRowMx + 0) * row, a.in[MX] + om, row, bar);
-  bulk_load(dst + (kMRowMx + 1) * row, a.in[MX] + o, R * row, bar);
-  bulk_load(dst + (kMRowMx + R + 1) * row, a.in[MX] + op, row, bar);
-  bulk_load(dst + kMRowBx * row, a.in[BX] + o, R * row, bar);
-  bulk_load(dst + kMRowBy * row, a.in[BY] + o, R * row, bar);
-  bulk_load(dst + (kMRowBy + R) * row, a.in[BY] + op, row, bar);
-  bulk_load(dst + kMRowBz * row, a.in[BZ] + o, R * row, bar);
+  mbar_expect_tx(bar, M::Slots * row);
+  bulk_load(dst + (M::Rho + 0) * row, a.in[RHO] + om, row, bar);
+  bulk_load(dst + (M::Rho + 1) * row, a.in[RHO] + o, R * row, bar);
+  bulk_load(dst + (M::Rho + R + 1) * row, a.in[RHO] + op, row, bar);
+  bulk_load(dst + (M::Mx + 0) * row, a.in[MX] + om, row, bar);
+  bulk_load(dst + (M::Mx + 1) * row, a.in[MX] + o, R * row, bar);
+  bulk_load(dst + (M::Mx + R + 1) * row, a.in[MX] + op, row, bar);
+  bulk_load(dst + M::Bx * row, a.in[BX] + o, R * row, bar);
+  bulk_load(dst + M::By * row, a.in[BY] + o, R * row, bar);
+  bulk_load(dst + (M::By + R) * row, a.in[BY] + op, row, bar);
+  bulk_load(dst + M::Bz * row, a.in[BZ] + o, R * row, bar);
 }
 
 // Barrier of thread group g (threadIdx.y) alone: named barrier g + 1 over
@@ -451,9 +460,9 @@ struct RowAdvect {
   }
 };
 
-template <int LIM>
-__global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __grid_constant__ MagArgs a, int L) {
-  constexpr int R = kMRowR;
+template <int LIM, int R>
+__global__ void __launch_bounds__(R == 4 ? 640 : 768, 1) mag_row_kernel(const __grid_constant__ MagArgs a, int L) {
+  using M = MRow<R>;
   extern __shared__ __align__(128) float ms_dyn[];
   __shared__ alignas(8) unsigned long long mbarr[2];
   const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
   const int j0 = (blockIdx.x % tiles) * R, k0 = (blockIdx.x / tiles) * L;
   const int tid = g * T + l;
   float* P = ms_dyn;                                   // [2][slots][nx]
-  float* vring = P + 2 * kMRowSlots * nx;              // [2][R+2][nx]: v of rows j0-1 .. j0+R
+  float* vring = P + 2 * M::Slots * nx;              // [2][R+2][nx]: v of rows j0-1 .. j0+R
   // [2][R+1][nx]: E_y of rows j0 .. j0+R, by step parity (a group may run a
   // step ahead of the one below it, which still reads its E_y row)
   float* ey2 = vring + 2 * (R + 2) * nx;
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
   }
   __syncthreads();
   if (tid == 0)
-    for (int s = 0; s < 2; s++) mag_row_issue(a, smem_u32(P + s * kMRowSlots * nx), smem_u32(&mbarr[s]), j0, k0 - 1 + s, nx, ny, nz);
+    for (int s = 0; s < 2; s++) mag_row_issue<R>(a, smem_u32(P + s * M::Slots * nx), smem_u32(&mbarr[s]), j0, k0 - 1 + s, nx, ny, nz);
   int issued = 2;
 
   float cbx[kRowCells], cby[kRowCells], cbz[kRowCells];  // raw b at plane p-1
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
   RowAdvect<LIM> Az, Ay;
   for (int s = 0; s < nsteps; s++) {
     const int p = k0 - 1 + s;
-    const float* sb = P + (s & 1) * kMRowSlots * nx;
+    const float* sb = P + (s & 1) * M::Slots * nx;
     if (!sweep_mbar_wait(smem_u32(&mbarr[s & 1]), (s >> 1) & 1)) gave_up = true;
     float* vcur = vring + (s & 1) * (R + 2) * nx;
     float* ey = ey2 + (s & 1) * (R + 1) * nx;
@@ -515,8 +524,8 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
     // part A: v(p) of this group's rows (the halo group: rows j0-1 and j0+R)
     {
       auto vel = [&](int slot) {
-        const float4 r = *reinterpret_cast<const float4*>(sb + (kMRowRho + slot) * nx + x0);
-        const float4 m = *reinterpret_cast<const float4*>(sb + (kMRowMx + slot) * nx + x0);
+        const float4 r = *reinterpret_cast<const float4*>(sb + (M::Rho + slot) * nx + x0);
+        const float4 m = *reinterpret_cast<const float4*>(sb + (M::Mx + slot) * nx + x0);
         *reinterpret_cast<float4*>(vcur + slot * nx + x0) =
             make_float4(v_div(m.x, r.x), v_div(m.y, r.y), v_div(m.z, r.z), v_div(m.w, r.w));
       };
@@ -544,7 +553,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
     if (doz) {  // E_z(p): b_z(p), v of this row at planes p and p-1
       float u[kRowCells + 2];
       face_u(vcur + vs * nx, vprev + vs * nx, u);
-      ld4(kMRowBz + g, Az.q);  // b_z(p)
+      ld4(M::Bz + g, Az.q);  // b_z(p)
       Az.part1(u, X, 0);
     }
     if (doy) {  // E_y(p-1): b_y(p-1), v of rows j and j-1 at plane p-1
@@ -571,11 +580,11 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
     // the raw fields of plane p for the next step (read late: fewer live registers)
     float nbx[kRowCells] = {0.f, 0.f, 0.f, 0.f}, nby[kRowCells], nbz[kRowCells] = {0.f, 0.f, 0.f, 0.f};
     if (halo) {
-      ld4(kMRowBy + R, nby);
+      ld4(M::By + R, nby);
     } else {
-      ld4(kMRowBx + g, nbx);
-      ld4(kMRowBy + g, nby);
-      ld4(kMRowBz + g, nbz);
+      ld4(M::Bx + g, nbx);
+      ld4(M::By + g, nby);
+      ld4(M::Bz + g, nbz);
     }
     // the step's one block barrier: E_y rows and v(p) published, plane p
     // read by every thread; it also carries a failed wait
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
       break;
     }
     if (s + 2 < nsteps) {  // every thread has read plane p: plane p+2 goes into its buffer
-      if (tid == 0) mag_row_issue(a, smem_u32(P + (s & 1) * kMRowSlots * nx), smem_u32(&mbarr[s & 1]), j0, p + 2, nx, ny, nz);
+      if (tid == 0) mag_row_issue<R>(a, smem_u32(P + (s & 1) * M::Slots * nx), smem_u32(&mbarr[s & 1]), j0, p + 2, nx, ny, nz);
       issued++;
     }
     float ezc[kRowCells + 1];  // E_z(p) at 4l-1/2 .. 4l+7/2
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(128 * (kMRowR + 1), 1) mag_row_kernel(const __
 }
 
 // Rows of the box qualify: x contiguous, nx a multiple of 128 (whole warps of
-// 4-cell threads) and at most 512, 16-byte aligned fields, a single box.
+// 4-cell threads) and at most 1024, 16-byte aligned fields, a single box.
 inline bool fluid_rows_qualify(const FluidArgs& a) {
   const Box& b = a.box;
   if (a.ens.items || !a.tma || a.fast == 2) return false;
@@ -700,13 +709,13 @@ cudaError_t launch_fluid_rows(bool rate, const FluidArgs& a, cudaStream_t s) {
 namespace mhd {
 
 // The magnetic row sweep qualifies for single boxes with x contiguous, nx a
-// multiple of 128 up to 512 (a block of 5 x nx/4 threads), ny a multiple of
-// the tile's rows and 16-byte aligned fields.
+// multiple of 128 up to 1024 (a block of (R + 1) x nx/4 threads), ny a
+// multiple of the tile's rows and 16-byte aligned fields.
 inline bool mag_rows_qualify(const MagArgs& a) {
   const Box& b = a.box;
   if (a.ens.items || !a.tma || a.passes != 1) return false;
   if (b.stride[0] != 1 || b.stride[1] != b.n[0] || b.stride[2] != (long long)b.n[0] * b.n[1]) return false;
-  if (b.n[0] % 128 || b.n[0] > 512 || b.n[1] % kMRowR || b.n[2] < 2) return false;
+  if (b.n[0] % 128 || b.n[0] > 1024 || b.n[1] % mag_row_tile(b.n[0]) || b.n[2] < 2) return false;
   for (int q = 0; q < 8; q++)
     if (reinterpret_cast<uintptr_t>(a.in[q]) % 16) return false;
   for (int q = 0; q < 3; q++)
@@ -733,19 +742,25 @@ inline int mag_row_segment(int tiles, int nz, int sms) {
   return best;
 }
 
-template <int LIM>
-cudaError_t launch_mag_rows(const MagArgs& a, cudaStream_t s) {
+template <int LIM, int R>
+cudaError_t launch_mag_rows_r(const MagArgs& a, cudaStream_t s) {
   const int nx = a.box.n[0], ny = a.box.n[1], nz = a.box.n[2];
-  const size_t smem = mag_row_smem(nx);
-  cudaError_t e = cudaFuncSetAttribute(mag_row_kernel<LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = mag_row_smem<R>(nx);
+  cudaError_t e =
+      cudaFuncSetAttribute(mag_row_kernel<LIM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int tiles = ny / kMRowR;
+  const int tiles = ny / R;
   const int L = mag_row_segment(tiles, nz, sms > 0 ? sms : 1);
-  mag_row_kernel<LIM><<<tiles * (nz / L), dim3(nx / kRowCells, kMRowR + 1), smem, s>>>(a, L);
+  mag_row_kernel<LIM, R><<<tiles * (nz / L), dim3(nx / kRowCells, R + 1), smem, s>>>(a, L);
   return cudaGetLastError();
+}
+
+template <int LIM>
+cudaError_t launch_mag_rows(const MagArgs& a, cudaStream_t s) {
+  return mag_row_tile(a.box.n[0]) == 4 ? launch_mag_rows_r<LIM, 4>(a, s) : launch_mag_rows_r<LIM, 2>(a, s);
 }
 
 }  // namespace mhd

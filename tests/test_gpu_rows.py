@@ -49,7 +49,7 @@ def close_to(a, b, tol=1e-6):
     return bool(np.all(err < tol)), err
 
 
-DIMS = [(128, 16, 8), (256, 12, 10), (128, 9, 7), (384, 8, 8)]
+DIMS = [(128, 16, 8), (256, 12, 10), (128, 9, 7), (384, 8, 8), (1024, 6, 4)]
 
 
 @pytest.mark.parametrize("dims", DIMS)
@@ -64,8 +64,9 @@ def test_fluid_row_sweep_matches_the_pencil_sweep(mhd, dims):
     assert ok, err
 
 
-# the magnetic row sweep needs ny a multiple of 4 and nx up to 512
-MAG_DIMS = [(128, 16, 8), (256, 12, 10), (384, 8, 8), (128, 4, 3), (512, 8, 16)]
+# the magnetic row sweep needs nx up to 1024 and ny a multiple of its tile's
+# rows (4; 2 for rows longer than 512)
+MAG_DIMS = [(128, 16, 8), (256, 12, 10), (384, 8, 8), (128, 4, 3), (512, 8, 16), (1024, 6, 4), (896, 2, 5)]
 
 
 @pytest.mark.parametrize("dims", MAG_DIMS)
